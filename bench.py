@@ -1,0 +1,316 @@
+"""Benchmark of the blended D2Q5 vectorial LBM step on GB300.
+
+Default workload: the 4096 x 4096 near-vacuum blast (rho = 1, p = 1e-6, total
+energy 1 in the 2x2 centre cells, reflective walls), second order with the PP
+limiter (eps = 1e-13), FP32 populations with FP64 theta_p solves, dynamic
+kinetic speed. One "step" is one time step of the whole grid. The metric is
+MLUPS (million cell updates per second), next to the fraction of the HBM
+roofline of the step kernel (160 algorithmic bytes per cell update: 20 FP32
+values read and 20 written).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank advances its own replica of
+the grid (the single-grid step is not sharded: "replicas only"); value is the
+sum of all ranks' cell updates over the slowest rank's time.
+
+The reference arm (--impl reference) times the FP64 CPU oracle (test
+infrastructure under oracle/) on this machine's host cores, on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MLUPS & % HBM roofline, 2nd-order+PP FP32 at 4096^2; batched vs sequential; "
+          "adjoint/forward")
+BYTES_PER_LU = 160           # 20 FP32 values read + 20 written per cell update
+N_SIDE = 4096
+EPS = 1e-13
+FALLBACK_HBM_GBS = 6800.0
+CTL_BYTES = 248              # device control block read back by vlbm_monitors
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2411_15001_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cuh", ".cu", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "step_fused_blast.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    if d.get("kernel_hash") != _kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline(n_side: int = N_SIDE, target_s: float = 15.0, max_steps: int = 50):
+    """The FP64 oracle on this host's cores, timed over whole time steps of the blast."""
+    from oracle import oracle as O
+    from paper_2411_15001_gb300 import workloads as W
+
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    mem_gb = None
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable"):
+                    mem_gb = int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    n = n_side if (mem_gb is None or mem_gb > 40 or n_side <= 2048) else 2048
+    p = W.blast(n)
+    cfg = O.Config(n, n, p.bc, O.LIM_PP, p.gamma, 0.5, EPS)
+    state = O.new_state(p.conserved())
+    a = O.kinetic_speed(O.max_speed(cfg, state), 0.5)
+    state = O.init_populations(cfg, state, a)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        state = O.step(cfg, state, a)
+        a = O.kinetic_speed(O.max_speed(cfg, state), 0.5)
+        steps += 1
+        if time.perf_counter() - t0 > target_s or steps >= max_steps:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * n * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"first {steps} time steps of the {n}x{n} blast (FP64 oracle, OpenMP over rows on "
+                      f"{cores} threads, per-step array allocation included)"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.n, target_s=min(120.0, 8.0 * max(1, args.steps)), max_steps=max(1, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"blast {args.n}x{args.n}, PP eps=1e-13, reflective walls (oracle sample)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2411_15001_gb300 import vlbm as V
+    from paper_2411_15001_gb300 import workloads as W
+
+    p = W.blast(args.n)
+    cons = torch.tensor(p.conserved(), dtype=torch.float32)
+    solver = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, gamma=p.gamma, limiter=V.LIM_PP, precision=V.FP32,
+                    eps=EPS, device=dev)
+    d = cons.to(dev)
+    solver.set_conserved(d[0].contiguous(), d[1:3].contiguous(), d[3].contiguous())
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---------------------------------------------------------- device-resident timing
+    solver.step(args.warmup)
+    barrier()
+    stream = solver.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    solver.profile(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        solver.step(args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    kernel_ms, launches = solver.profile_read()
+    solver.profile(False)
+    mon = solver.monitors()
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    cells = p.nx * p.ny
+    value = world * cells * args.steps / (ms_max / 1e3) / 1e6
+
+    # ---------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        host = cons.pin_memory()
+        out_host = torch.empty((4, p.ny, p.nx), dtype=torch.float32).pin_memory()
+        dbuf = torch.empty_like(d)
+        barrier()
+        t0 = time.perf_counter()
+        dbuf.copy_(host, non_blocking=True)
+        solver.set_conserved(dbuf[0].contiguous(), dbuf[1:3].contiguous(), dbuf[3].contiguous())
+        bad = 0
+        for _ in range(args.steps):
+            solver.step(1)
+            m = solver.monitors()           # per-step positivity check read back to the host
+            bad += m["bad_cells"]
+        rho, mom, E = solver.moments()
+        out_dev = torch.cat([rho[None], mom, E[None]])
+        out_host.copy_(out_dev, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        t_e2e = time.perf_counter() - t0
+        t_t = torch.tensor([t_e2e], device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t_t, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": world * cells * args.steps / float(t_t.item()) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": host.numel() * 4 / args.steps,
+               "d2h_bytes_per_step": (out_host.numel() * 4) / args.steps + CTL_BYTES,
+               "positivity_violations": int(bad)}
+
+    peaks, peak_src = _peaks()
+    achieved = BYTES_PER_LU * cells / (kernel_ms / launches / 1e3) / 1e9 if launches else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": _ncu_traffic(),
+            "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})",
+            "kernel": "k_step_fused<float, PP>", "kernel_ms_avg": kernel_ms / launches if launches else None}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"blast {p.nx}x{p.ny} near-vacuum (rho=1, p=1e-6, E=1 in 2x2 centre), "
+                                       "reflective walls, 2nd order + PP limiter eps=1e-13, FP32 state "
+                                       "with FP64 theta_p solve, dynamic a^n",
+                           "nx": p.nx, "ny": p.ny, "precision": "fp32", "limiter": "PP",
+                           "l2": "state 2x1.34 GB >> L2 129 MB; no flush",
+                           "parallelism": f"replicas x{world}",
+                           "steps_total": args.warmup + args.steps,
+                           "positivity_violations": mon["bad_cells"] + mon["nonfinite_cells"],
+                           "first_bad_step": mon["first_bad_step"], "status": mon["status"]},
+                "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 2 * args.steps,
+                "roofline": roof}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.n)
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1900)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_SIDE, help="grid side (default 4096)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

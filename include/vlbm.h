@@ -1,0 +1,206 @@
+/*
+ * vlbm.h -- C ABI of the GB300 (sm_103a) blended D2Q5 vectorial lattice
+ * Boltzmann library for the 2D compressible Euler equations.
+ *
+ * Method: Wissocq, Liu & Abgrall, "A positive- and bound-preserving vectorial
+ * lattice Boltzmann method in two dimensions", arXiv 2411.15001.
+ *   - problem: Sec. 1, eq. (hyperbolic_PDE) with the ideal-gas Euler fluxes and
+ *     the admissible set G of eq. (convex_G);
+ *   - D2Q5 velocity set and Maxwellians: Sec. 2, Example "Five-wave (D2Q5) model";
+ *   - blended collide-and-stream update: Sec. 3.2, eq. (blending_u1) and
+ *     eq. (blending_u) (u_5 eliminated, 20 values per cell);
+ *   - per-face blending theta = min(1, theta_rho, theta_p): Sec. 3.2-3.4
+ *     (PP / LMP / RLMP density bounds, GQL internal-energy bound);
+ *   - kinetic speed a^n = 4 lambda^n and Delta t^n = dx / a^n: Sec. 4 preamble.
+ *
+ * Conventions shared by every call
+ *   - Return value: VLBM_OK (0) or a negative VLBM_E_* code; vlbm_strerror()
+ *     names it. Nothing is thrown, nothing aborts.
+ *   - Device memory: the library never allocates device memory. The caller
+ *     passes one device workspace (vlbm_workspace_bytes) that must stay alive
+ *     and unmoved until vlbm_destroy; every other device pointer is borrowed for
+ *     the duration of the call's stream work only.
+ *   - Host memory: the opaque vlbm_state is allocated by vlbm_init and freed by
+ *     vlbm_destroy.
+ *   - Streams: every call enqueues its work on the stream given to vlbm_init
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream) and
+ *     returns without waiting, except the calls documented as synchronising.
+ *   - Field layout: a "plane" is nx*ny values, cell (i, j) at j*nx + i (x
+ *     fastest), in the state's precision (double for VLBM_FP64, float for
+ *     VLBM_FP32). Momentum arguments hold two planes back to back: m1 then m2.
+ *   - Sticky errors: a state that leaves G (rho <= 0 or E - |m|^2/(2 rho) <= 0)
+ *     or becomes non-finite is recorded on the device and reported by the next
+ *     synchronising call (vlbm_sync, vlbm_monitors, vlbm_time).
+ */
+#ifndef VLBM_H
+#define VLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Exported symbols (the library is built with hidden default visibility). */
+#if defined(__GNUC__)
+#define VLBM_API __attribute__((visibility("default")))
+#else
+#define VLBM_API
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define VLBM_OK 0
+#define VLBM_E_INVAL (-1)        /* bad argument or inadmissible initial state */
+#define VLBM_E_CUDA (-2)         /* a CUDA runtime call failed (no device, launch error) */
+#define VLBM_E_POSITIVITY (-3)   /* a cell left the admissible set G */
+#define VLBM_E_NONFINITE (-4)    /* a cell became NaN or infinite */
+#define VLBM_E_TIMEOUT (-5)      /* a bounded device wait gave up */
+#define VLBM_E_UNSUPPORTED (-6)  /* valid request this build does not implement */
+#define VLBM_E_NOMEM (-7)        /* workspace too small or misaligned */
+
+/* Density bound used by the convex limiter (Sec. 3.3). FIRST_ORDER forces
+ * theta = 0 (the first-order scheme of eq. 1st-order_kinetic), NONE forces
+ * theta = 1 (the second-order scheme of eq. 2nd-order_kinetic). PP, LMP and
+ * RLMP all add the internal-energy bound theta_p of Sec. 3.4. */
+#define VLBM_LIM_FIRST_ORDER 0
+#define VLBM_LIM_NONE 1
+#define VLBM_LIM_PP 2
+#define VLBM_LIM_LMP 3
+#define VLBM_LIM_RLMP 4
+
+/* Boundary rule per side (Sec. 4: periodic; zero gradient of all
+ * distributions; reflective (symmetry) wall). A periodic side must face a
+ * periodic side. */
+#define VLBM_BC_PERIODIC 0
+#define VLBM_BC_TRANSMISSIVE 1
+#define VLBM_BC_REFLECTIVE 2
+
+/* Arithmetic of the state. FP32: populations, collision and density bounds
+ * in float; the internal-energy bound theta_p is solved in double wherever a
+ * float evaluation cannot prove it inactive; conservation sums in double. */
+#define VLBM_FP64 0
+#define VLBM_FP32 1
+
+/* Kernel choice (VLBM_KERNEL_AUTO picks the fastest available). */
+#define VLBM_KERNEL_AUTO 0
+#define VLBM_KERNEL_SIMPLE 1    /* one thread per cell, radius-2 gather from L2 */
+#define VLBM_KERNEL_FUSED 2     /* row-marching TMA kernel, one pass per step */
+
+typedef struct vlbm_state vlbm_state;
+
+/* Uniform Cartesian grid: nx * ny cells of side dx. bc = {west, east, south, north}. */
+typedef struct {
+    int32_t nx, ny;
+    double dx;
+    int32_t bc[4];
+} vlbm_grid;
+
+/* Optional settings; pass NULL for the defaults. */
+typedef struct {
+    double alpha;     /* D2Q5 rest weight M_5 = alpha u; 1/2 <= alpha < 1 (Prop. convex
+                         preservation); default 0.5 as in Sec. 4 */
+    double eps;       /* epsilon subtracted in the PP and pressure bounds; default 1e-16 */
+    int32_t kernel;   /* VLBM_KERNEL_*; default AUTO */
+    int32_t reserved;
+} vlbm_opts;
+
+/* Host copy of the device-side step state and monitors. */
+typedef struct {
+    int64_t n;                 /* time steps taken since vlbm_set_conserved / vlbm_load */
+    double t;                  /* simulated time */
+    double a;                  /* kinetic speed the next step will use */
+    double dt;                 /* time step the next step will use */
+    double lambda;             /* max_cells |v| + sqrt(gamma p / rho) of the current state */
+    int64_t bad_cells;         /* cells outside G in the last step's output */
+    int64_t nonfinite_cells;   /* non-finite cells in the last step's output */
+    int64_t first_bad_step;    /* first step whose output left G (or went non-finite); -1 if none */
+    double min_rho;            /* min density of the current state */
+    double sum[4];             /* FP64 sums of rho, m1, m2, E over the cells of the current state */
+    int32_t done;              /* 1 once vlbm_step_to has reached its final time */
+    int32_t status;            /* sticky VLBM_OK / VLBM_E_* of the device */
+} vlbm_monitor_t;
+
+/* Bytes of device workspace for a grid and precision (two padded 20-plane
+ * states with a two-cell ghost frame, plus the device control block).
+ * Returns 0 for an invalid grid or precision. */
+VLBM_API size_t vlbm_workspace_bytes(const vlbm_grid *grid, int32_t precision);
+
+/* Create a solver on `d_workspace` (caller-owned device memory, >= the size
+ * above, 256-byte aligned) for the Euler system with heat capacity ratio
+ * gamma > 1. lambda > 0 holds the kinetic speed fixed at a = 2 lambda/(1-alpha)
+ * (= 4 lambda at alpha = 1/2; Sec. 4.1 runs a = 10.7); lambda <= 0 updates it
+ * every step from the current state (Sec. 4 preamble). `stream` is a
+ * cudaStream_t. Allocates only the host object; enqueues nothing.
+ * Errors: VLBM_E_INVAL (any argument out of range), VLBM_E_NOMEM (workspace too
+ * small or misaligned), VLBM_E_CUDA (no usable device). */
+VLBM_API int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limiter,
+              int32_t precision, const vlbm_opts *opts, void *d_workspace,
+              size_t workspace_bytes, void *stream, vlbm_state **out);
+
+/* Load initial conserved fields u_0 = (rho, m1, m2, E) from device planes and
+ * initialise the populations at equilibrium, u_k^0 = M_k(u_0) (Sec. 4
+ * preamble), with a^0 from u_0. Resets n and t to 0 and clears sticky errors.
+ * Synchronises the stream: returns VLBM_E_INVAL if a cell of u_0 is outside G
+ * or not finite. */
+VLBM_API int vlbm_set_conserved(vlbm_state *s, const void *d_rho, const void *d_mom, const void *d_E);
+
+/* Advance `nsteps` >= 0 time steps (one fused collide + limit + stream pass
+ * each, eq. blending_u1 / blending_u). Asynchronous. */
+VLBM_API int vlbm_step(vlbm_state *s, int64_t nsteps);
+
+/* Advance until t = t_end (the last step is shortened so that t lands on t_end,
+ * with a = dx / Delta t, still above the Bouchut speed of eq. Bouchut_D2Q5) or
+ * until max_steps steps, whichever comes first. Synchronises the stream once per
+ * chunk of steps to learn whether t_end was reached. */
+VLBM_API int vlbm_step_to(vlbm_state *s, double t_end, int64_t max_steps);
+
+/* Copy the conserved fields of the current state into caller-owned device
+ * planes (any pointer may be NULL to skip it). Asynchronous. */
+VLBM_API int vlbm_moments(const vlbm_state *s, void *d_rho, void *d_mom, void *d_E);
+
+/* Wait for the stream, then fill *out (host) with the step state and monitors.
+ * Returns the sticky device status (VLBM_OK, VLBM_E_POSITIVITY, ...). */
+VLBM_API int vlbm_monitors(vlbm_state *s, vlbm_monitor_t *out);
+
+/* Wait for the stream and return the sticky device status. */
+VLBM_API int vlbm_sync(vlbm_state *s);
+
+/* Wait for the stream; *t and *n (either may be NULL) get the simulated time
+ * and step count. Returns the sticky device status. */
+VLBM_API int vlbm_time(vlbm_state *s, double *t, int64_t *n);
+
+/* Bytes of a checkpoint: a 64-byte header (n, t, a, dt, done) followed by the
+ * 20 planes of the current state (u, then u_1..u_4, 4 planes each). */
+VLBM_API size_t vlbm_checkpoint_bytes(const vlbm_state *s);
+
+/* Write the current state into caller-owned device memory d_dst (>=
+ * vlbm_checkpoint_bytes). Asynchronous. */
+VLBM_API int vlbm_save(const vlbm_state *s, void *d_dst);
+
+/* Restore a checkpoint written by vlbm_save for the same grid and precision;
+ * stepping on from it reproduces the uninterrupted run bit for bit.
+ * Asynchronous. */
+VLBM_API int vlbm_load(vlbm_state *s, const void *d_src);
+
+/* Kernel timing. While enabled, every step records a CUDA event pair around its
+ * collide + limit + stream kernel (not the ghost-frame kernel) on the state's
+ * stream. vlbm_profile_read waits for the stream and returns the summed kernel
+ * time in milliseconds and the number of timed launches since the last enable. */
+VLBM_API int vlbm_profile(vlbm_state *s, int32_t enable);
+VLBM_API int vlbm_profile_read(vlbm_state *s, double *kernel_ms, int64_t *launches);
+
+/* Free the host object. Enqueues nothing and does not touch the workspace. */
+VLBM_API void vlbm_destroy(vlbm_state *s);
+
+/* Static, NUL-terminated name of a return code. */
+VLBM_API const char *vlbm_strerror(int code);
+
+/* Copy the last error message recorded for `s` (or for the thread if s is NULL)
+ * into buf (n bytes, always NUL-terminated). Returns the message length. */
+VLBM_API int vlbm_last_error_detail(const vlbm_state *s, char *buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,485 @@
+// abi.cu -- the extern "C" entry points of include/vlbm.h: argument checks,
+// workspace carving, and stream-ordered launches of the step kernels.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/vlbm.h"
+#include "vlbm_internal.h"
+
+using namespace vlbm;
+
+struct vlbm_state {
+    vlbm_grid grid;
+    int precision, limiter, kernel;
+    double gamma, lambda, alpha, eps, a_fixed;
+    Layout L;
+    void *ws;
+    cudaStream_t stream;
+    DevCtl *ctl;
+    int device;
+    CUtensorMap tmap;   // 3D view [40 planes][rows][pitch] of both state buffers
+    bool have_tmap;
+    int strips, fused_grid;
+    bool profiling;
+    std::vector<cudaEvent_t> ev;   // event pairs of timed launches
+    size_t ev_used;
+    bool loaded;        // set_conserved or load has run
+    bool tend_active;   // a final time is armed on the device
+    char err[256];
+};
+
+static thread_local char g_err[256];
+
+static int fail(vlbm_state *s, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+static int fail(vlbm_state *s, int code, const char *fmt, ...) {
+    char *dst = s ? s->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int cuda_fail(vlbm_state *s, cudaError_t e, const char *what) {
+    return fail(s, VLBM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+namespace vlbm {
+Layout make_layout(int nx, int ny, int elem) {
+    Layout L;
+    L.nx = nx;
+    L.ny = ny;
+    L.elem = elem;
+    L.pitch = ((nx + 2 * kOX + 31) / 32) * 32;
+    L.rows = ny + 2 * kOY;
+    L.plane = (((long long)L.pitch * L.rows + 63) / 64) * 64;
+    L.buf_bytes = (size_t)L.plane * kNPlane * elem;
+    L.ctl_offset = 2 * L.buf_bytes;
+    L.total = L.ctl_offset + ((sizeof(DevCtl) + 255) / 256) * 256;
+    return L;
+}
+}  // namespace vlbm
+
+static bool grid_ok(const vlbm_grid *g) {
+    if (!g || g->nx < 4 || g->ny < 4 || !(g->dx > 0.0)) return false;
+    if ((long long)g->nx * g->ny > (1ll << 31)) return false;
+    for (int k = 0; k < 4; ++k)
+        if (g->bc[k] < VLBM_BC_PERIODIC || g->bc[k] > VLBM_BC_REFLECTIVE) return false;
+    if ((g->bc[0] == VLBM_BC_PERIODIC) != (g->bc[1] == VLBM_BC_PERIODIC)) return false;
+    if ((g->bc[2] == VLBM_BC_PERIODIC) != (g->bc[3] == VLBM_BC_PERIODIC)) return false;
+    return true;
+}
+
+static int elem_of(int32_t precision) {
+    return precision == VLBM_FP64 ? 8 : precision == VLBM_FP32 ? 4 : 0;
+}
+
+// Keep the caller's current device; run the call on the state's device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+static StepArgs<T> args_of(const vlbm_state *s) {
+    StepArgs<T> A;
+    A.buf0 = (T *)s->ws;
+    A.buf1 = (T *)((char *)s->ws + s->L.buf_bytes);
+    A.plane = s->L.plane;
+    A.pitch = s->L.pitch;
+    A.nx = s->grid.nx;
+    A.ny = s->grid.ny;
+    for (int k = 0; k < 4; ++k) A.bc[k] = s->grid.bc[k];
+    A.limiter = s->limiter;
+    A.gamma = s->gamma;
+    A.alpha = s->alpha;
+    A.eps = s->eps;
+    A.ctl = s->ctl;
+    return A;
+}
+
+static bool use_fused(const vlbm_state *s) {
+    return s->have_tmap && s->kernel != VLBM_KERNEL_SIMPLE;
+}
+
+static cudaError_t step_kernel_only(vlbm_state *s) {
+    if (use_fused(s)) {
+        if (s->precision == VLBM_FP64)
+            return launch_step_fused<double>(args_of<double>(s), s->tmap, s->strips, s->fused_grid, s->stream);
+        return launch_step_fused<float>(args_of<float>(s), s->tmap, s->strips, s->fused_grid, s->stream);
+    }
+    if (s->precision == VLBM_FP64) return launch_step_simple<double>(args_of<double>(s), s->stream);
+    return launch_step_simple<float>(args_of<float>(s), s->stream);
+}
+
+static cudaError_t ghosts(vlbm_state *s) {
+    if (s->precision == VLBM_FP64) return launch_ghosts<double>(args_of<double>(s), s->stream);
+    return launch_ghosts<float>(args_of<float>(s), s->stream);
+}
+
+// One time step: the collide + limit + stream kernel, then the ghost frame of
+// the new state. With profiling on, an event pair brackets the step kernel.
+static cudaError_t step_once(vlbm_state *s) {
+    cudaError_t r;
+    if (s->profiling) {
+        if (s->ev_used + 2 > s->ev.size()) {
+            for (int k = 0; k < 2; ++k) {
+                cudaEvent_t e;
+                r = cudaEventCreate(&e);
+                if (r != cudaSuccess) return r;
+                s->ev.push_back(e);
+            }
+        }
+        r = cudaEventRecord(s->ev[s->ev_used], s->stream);
+        if (r == cudaSuccess) r = step_kernel_only(s);
+        if (r == cudaSuccess) r = cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
+        s->ev_used += 2;
+    } else {
+        r = step_kernel_only(s);
+    }
+    if (r != cudaSuccess) return r;
+    return ghosts(s);
+}
+
+// TMA descriptor of the two state buffers seen as one 3D tensor
+// [40 planes][ny + 4 rows][pitch columns]; a box is 128 columns x 1 row x 20 planes.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static bool make_tmap(vlbm_state *s) {
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        encode = (EncodeTiledFn)fn;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)s->L.pitch, (cuuint64_t)s->L.rows, (cuuint64_t)(2 * kNPlane)};
+    const cuuint64_t strides[2] = {(cuuint64_t)s->L.pitch * s->L.elem, (cuuint64_t)s->L.plane * s->L.elem};
+    const cuuint32_t box[3] = {(cuuint32_t)kFusedBox, 1u, (cuuint32_t)kNPlane};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = encode(&s->tmap, s->L.elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        3, s->ws, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+static int read_ctl(vlbm_state *s, DevCtl *h) {
+    cudaError_t e = cudaMemcpyAsync(h, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "reading the device control block");
+    return VLBM_OK;
+}
+
+extern "C" {
+
+size_t vlbm_workspace_bytes(const vlbm_grid *grid, int32_t precision) {
+    const int elem = elem_of(precision);
+    if (!grid_ok(grid) || !elem) return 0;
+    return make_layout(grid->nx, grid->ny, elem).total;
+}
+
+int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limiter,
+              int32_t precision, const vlbm_opts *opts, void *d_workspace, size_t workspace_bytes,
+              void *stream, vlbm_state **out) {
+    if (!out) return fail(nullptr, VLBM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid_ok(grid))
+        return fail(nullptr, VLBM_E_INVAL, "grid: need nx, ny >= 4, dx > 0, bc in 0..2, periodic sides paired");
+    if (!(gamma > 1.0)) return fail(nullptr, VLBM_E_INVAL, "gamma must be > 1");
+    if (limiter < VLBM_LIM_FIRST_ORDER || limiter > VLBM_LIM_RLMP)
+        return fail(nullptr, VLBM_E_INVAL, "limiter out of range");
+    const int elem = elem_of(precision);
+    if (!elem) return fail(nullptr, VLBM_E_INVAL, "precision out of range");
+    vlbm_opts o = {0.5, 1e-16, VLBM_KERNEL_AUTO, 0};
+    if (opts) o = *opts;
+    if (!(o.alpha >= 0.5 && o.alpha < 1.0)) return fail(nullptr, VLBM_E_INVAL, "alpha must be in [1/2, 1)");
+    if (!(o.eps >= 0.0 && o.eps < 1e-3)) return fail(nullptr, VLBM_E_INVAL, "eps must be in [0, 1e-3)");
+    if (o.kernel < VLBM_KERNEL_AUTO || o.kernel > VLBM_KERNEL_FUSED)
+        return fail(nullptr, VLBM_E_INVAL, "kernel out of range");
+    if (!(lambda == lambda)) return fail(nullptr, VLBM_E_INVAL, "lambda is NaN");
+    const Layout L = make_layout(grid->nx, grid->ny, elem);
+    if (!d_workspace || ((uintptr_t)d_workspace & 255))
+        return fail(nullptr, VLBM_E_NOMEM, "workspace NULL or not 256-byte aligned");
+    if (workspace_bytes < L.total)
+        return fail(nullptr, VLBM_E_NOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, L.total);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, VLBM_E_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    cudaPointerAttributes pa;
+    e = cudaPointerGetAttributes(&pa, d_workspace);
+    if (e != cudaSuccess || (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(nullptr, VLBM_E_INVAL, "workspace is not device memory");
+    }
+    vlbm_state *s = new (std::nothrow) vlbm_state();
+    if (!s) return fail(nullptr, VLBM_E_NOMEM, "host allocation failed");
+    s->grid = *grid;
+    s->precision = precision;
+    s->limiter = limiter;
+    s->kernel = o.kernel;
+    s->gamma = gamma;
+    s->lambda = lambda;
+    s->alpha = o.alpha;
+    s->eps = o.eps;
+    s->a_fixed = lambda > 0.0 ? 2.0 * lambda / (1.0 - o.alpha) : 0.0;
+    s->L = L;
+    s->ws = d_workspace;
+    s->stream = (cudaStream_t)stream;
+    s->ctl = (DevCtl *)((char *)d_workspace + L.ctl_offset);
+    s->device = pa.device;
+    {
+        DeviceGuard g(s->device);
+        s->strips = (grid->nx + kFusedOut - 1) / kFusedOut;
+        s->have_tmap = make_tmap(s);
+        if (s->have_tmap) {
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+            const int per_sm = precision == VLBM_FP64 ? fused_occupancy<double>(limiter)
+                                                      : fused_occupancy<float>(limiter);
+            long long rows = (long long)s->strips * grid->ny;
+            long long want = (long long)per_sm * (sms > 0 ? sms : 1);
+            long long cap = rows / 8 > 0 ? rows / 8 : 1;
+            s->fused_grid = (int)(want < cap ? want : cap);
+        }
+        if (o.kernel == VLBM_KERNEL_FUSED && !s->have_tmap) {
+            delete s;
+            return fail(nullptr, VLBM_E_UNSUPPORTED, "TMA descriptor unavailable for the fused kernel");
+        }
+    }
+    *out = s;
+    return VLBM_OK;
+}
+
+int vlbm_set_conserved(vlbm_state *s, const void *d_rho, const void *d_mom, const void *d_E) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    if (!d_rho || !d_mom || !d_E) return fail(s, VLBM_E_INVAL, "input plane pointer is NULL");
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_ctl_reset(s->ctl, s->grid.dx, s->alpha, s->a_fixed, s->eps, s->gamma, s->stream);
+    if (e == cudaSuccess) {
+        if (s->precision == VLBM_FP64)
+            e = launch_init<double>(args_of<double>(s), (const double *)d_rho, (const double *)d_mom,
+                                    (const double *)d_E, s->stream);
+        else
+            e = launch_init<float>(args_of<float>(s), (const float *)d_rho, (const float *)d_mom,
+                                   (const float *)d_E, s->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "initialisation launch");
+    DevCtl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    s->loaded = true;
+    s->tend_active = false;
+    if (h.invalid_init)
+        return fail(s, VLBM_E_INVAL, "initial state has cells outside G or not finite");
+    return VLBM_OK;
+}
+
+int vlbm_step(vlbm_state *s, int64_t nsteps) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    if (!s->loaded) return fail(s, VLBM_E_INVAL, "no state loaded (call vlbm_set_conserved)");
+    if (nsteps < 0) return fail(s, VLBM_E_INVAL, "nsteps < 0");
+    DeviceGuard g(s->device);
+    if (s->tend_active) {
+        cudaError_t e = launch_set_tend(s->ctl, 0.0, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "clearing the final time");
+        s->tend_active = false;
+    }
+    for (int64_t k = 0; k < nsteps; ++k) {
+        cudaError_t e = step_once(s);
+        if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+    }
+    return VLBM_OK;
+}
+
+int vlbm_step_to(vlbm_state *s, double t_end, int64_t max_steps) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    if (!s->loaded) return fail(s, VLBM_E_INVAL, "no state loaded (call vlbm_set_conserved)");
+    if (!(t_end > 0.0) || max_steps < 0) return fail(s, VLBM_E_INVAL, "need t_end > 0 and max_steps >= 0");
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_set_tend(s->ctl, t_end, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "arming the final time");
+    s->tend_active = true;
+    int64_t done_steps = 0, chunk = 64;
+    while (done_steps < max_steps) {
+        const int64_t k = chunk < max_steps - done_steps ? chunk : max_steps - done_steps;
+        for (int64_t q = 0; q < k; ++q) {
+            e = step_once(s);
+            if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+        }
+        done_steps += k;
+        DevCtl h;
+        int rc = read_ctl(s, &h);
+        if (rc) return rc;
+        if (h.done) return h.status;
+        if (chunk < 4096) chunk *= 2;
+    }
+    return VLBM_OK;
+}
+
+int vlbm_moments(const vlbm_state *s, void *d_rho, void *d_mom, void *d_E) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    vlbm_state *m = const_cast<vlbm_state *>(s);
+    if (!s->loaded) return fail(m, VLBM_E_INVAL, "no state loaded");
+    DeviceGuard g(s->device);
+    cudaError_t e;
+    if (s->precision == VLBM_FP64)
+        e = launch_moments<double>(args_of<double>(s), (double *)d_rho, (double *)d_mom, (double *)d_E, s->stream);
+    else
+        e = launch_moments<float>(args_of<float>(s), (float *)d_rho, (float *)d_mom, (float *)d_E, s->stream);
+    if (e != cudaSuccess) return cuda_fail(m, e, "moments launch");
+    return VLBM_OK;
+}
+
+int vlbm_monitors(vlbm_state *s, vlbm_monitor_t *out) {
+    if (!s || !out) return fail(s, VLBM_E_INVAL, "state or out is NULL");
+    if (!s->loaded) return fail(s, VLBM_E_INVAL, "no state loaded");
+    DeviceGuard g(s->device);
+    DevCtl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    out->n = h.n;
+    out->t = h.t;
+    out->a = h.a;
+    out->dt = h.dt;
+    out->lambda = h.lambda;
+    out->bad_cells = h.bad_last;
+    out->nonfinite_cells = h.nonfinite_last;
+    out->first_bad_step = h.first_bad_step;
+    out->min_rho = h.min_rho;
+    for (int c = 0; c < 4; ++c) out->sum[c] = h.sum_last[c];
+    out->done = h.done;
+    out->status = h.status;
+    return h.status;
+}
+
+int vlbm_sync(vlbm_state *s) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    if (!s->loaded) return fail(s, VLBM_E_INVAL, "no state loaded");
+    DeviceGuard g(s->device);
+    DevCtl h;
+    int rc = read_ctl(s, &h);
+    return rc ? rc : h.status;
+}
+
+int vlbm_time(vlbm_state *s, double *t, int64_t *n) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    if (!s->loaded) return fail(s, VLBM_E_INVAL, "no state loaded");
+    DeviceGuard g(s->device);
+    DevCtl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    if (t) *t = h.t;
+    if (n) *n = h.n;
+    return h.status;
+}
+
+size_t vlbm_checkpoint_bytes(const vlbm_state *s) {
+    if (!s) return 0;
+    return 64 + (size_t)kNPlane * s->grid.nx * s->grid.ny * s->L.elem;
+}
+
+int vlbm_save(const vlbm_state *s, void *d_dst) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    vlbm_state *m = const_cast<vlbm_state *>(s);
+    if (!d_dst || ((uintptr_t)d_dst & 15)) return fail(m, VLBM_E_INVAL, "destination NULL or not 16-byte aligned");
+    if (!s->loaded) return fail(m, VLBM_E_INVAL, "no state loaded");
+    DeviceGuard g(s->device);
+    cudaError_t e = s->precision == VLBM_FP64 ? launch_save<double>(args_of<double>(s), d_dst, s->stream)
+                                              : launch_save<float>(args_of<float>(s), d_dst, s->stream);
+    if (e != cudaSuccess) return cuda_fail(m, e, "save launch");
+    return VLBM_OK;
+}
+
+int vlbm_load(vlbm_state *s, const void *d_src) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    if (!d_src || ((uintptr_t)d_src & 15)) return fail(s, VLBM_E_INVAL, "source NULL or not 16-byte aligned");
+    DeviceGuard g(s->device);
+    cudaError_t e = launch_ctl_reset(s->ctl, s->grid.dx, s->alpha, s->a_fixed, s->eps, s->gamma, s->stream);
+    if (e == cudaSuccess)
+        e = s->precision == VLBM_FP64 ? launch_load<double>(args_of<double>(s), d_src, s->stream)
+                                      : launch_load<float>(args_of<float>(s), d_src, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "load launch");
+    s->loaded = true;
+    s->tend_active = true;  // the restored header may carry a final time
+    return VLBM_OK;
+}
+
+int vlbm_profile(vlbm_state *s, int32_t enable) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    s->profiling = enable != 0;
+    if (s->profiling) s->ev_used = 0;
+    return VLBM_OK;
+}
+
+int vlbm_profile_read(vlbm_state *s, double *kernel_ms, int64_t *launches) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    DeviceGuard g(s->device);
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "profile read");
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < s->ev_used; k += 2) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, s->ev[k], s->ev[k + 1]);
+        if (e != cudaSuccess) return cuda_fail(s, e, "event elapsed time");
+        total += ms;
+    }
+    if (kernel_ms) *kernel_ms = total;
+    if (launches) *launches = (int64_t)(s->ev_used / 2);
+    return VLBM_OK;
+}
+
+void vlbm_destroy(vlbm_state *s) {
+    if (!s) return;
+    for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    delete s;
+}
+
+const char *vlbm_strerror(int code) {
+    switch (code) {
+        case VLBM_OK: return "ok";
+        case VLBM_E_INVAL: return "invalid argument";
+        case VLBM_E_CUDA: return "CUDA error";
+        case VLBM_E_POSITIVITY: return "a cell left the admissible set";
+        case VLBM_E_NONFINITE: return "a cell became non-finite";
+        case VLBM_E_TIMEOUT: return "a device wait timed out";
+        case VLBM_E_UNSUPPORTED: return "unsupported request";
+        case VLBM_E_NOMEM: return "workspace too small or misaligned";
+        default: return "unknown error code";
+    }
+}
+
+int vlbm_last_error_detail(const vlbm_state *s, char *buf, size_t n) {
+    const char *src = s ? s->err : g_err;
+    const size_t len = strlen(src);
+    if (buf && n) {
+        const size_t k = len < n - 1 ? len : n - 1;
+        memcpy(buf, src, k);
+        buf[k] = '\0';
+    }
+    return (int)len;
+}
+
+}  // extern "C"
+

@@ -1,0 +1,397 @@
+// common.cuh -- reductions, the end-of-step finaliser, ghost frame, initial
+// state, moments and checkpoints. Shared by all step kernels.
+#pragma once
+
+#include "physics.cuh"
+#include "vlbm_internal.h"
+#include "../../include/vlbm.h"
+
+namespace vlbm {
+
+template <typename T>
+__device__ __forceinline__ long long cidx(const StepArgs<T> &A, int i, int j) {
+    return (long long)(j + kOY) * A.pitch + (i + kOX);
+}
+
+// NaN-propagating max / min.
+template <typename T> __device__ __forceinline__ T pmax(T a, T b) { return (b > a || b != b) ? b : a; }
+template <typename T> __device__ __forceinline__ T pmin(T a, T b) { return (b < a || b != b) ? b : a; }
+
+// Error-free sum of two floats (Knuth's TwoSum) and a double-float accumulator:
+// the FP32 path keeps its conservation sums as (hi, lo) float pairs (about 48
+// significant bits) and converts to double once per CTA, because FP64
+// instructions run at a small fraction of the FP32 rate on this GPU.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+struct DFloat {
+    float hi, lo;
+    __device__ __forceinline__ void add(float bh, float bl) {
+        float s, e;
+        two_sum(hi, bh, s, e);
+        e = __fadd_rn(e, __fadd_rn(lo, bl));
+        hi = __fadd_rn(s, e);
+        lo = __fsub_rn(e, __fsub_rn(hi, s));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <typename T> struct SumAcc;
+template <> struct SumAcc<float> {
+    DFloat s[4];
+    __device__ __forceinline__ void zero() { for (int c = 0; c < 4; ++c) s[c].hi = s[c].lo = 0.f; }
+    __device__ __forceinline__ void add_cell(const float u[4]) { for (int c = 0; c < 4; ++c) s[c].add(u[c], 0.f); }
+    __device__ __forceinline__ void shfl_add(int off) {
+        for (int c = 0; c < 4; ++c) {
+            const float h = __shfl_xor_sync(0xffffffffu, s[c].hi, off);
+            const float l = __shfl_xor_sync(0xffffffffu, s[c].lo, off);
+            s[c].add(h, l);
+        }
+    }
+    __device__ __forceinline__ double value(int c) const { return s[c].value(); }
+};
+template <> struct SumAcc<double> {
+    double s[4];
+    __device__ __forceinline__ void zero() { for (int c = 0; c < 4; ++c) s[c] = 0.0; }
+    __device__ __forceinline__ void add_cell(const double u[4]) { for (int c = 0; c < 4; ++c) s[c] += u[c]; }
+    __device__ __forceinline__ void shfl_add(int off) {
+        for (int c = 0; c < 4; ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+    }
+    __device__ __forceinline__ double value(int c) const { return s[c]; }
+};
+
+// Per-thread monitor of the cells a thread wrote: max lambda, min rho, sums,
+// and the counts of cells outside G / non-finite.
+template <typename T>
+struct Monitor {
+    T lam, minrho;
+    SumAcc<T> sum;
+    unsigned int bad, nonfin;
+    __device__ __forceinline__ void init() {
+        lam = T(0);
+        minrho = T(INFINITY);
+        sum.zero();
+        bad = nonfin = 0u;
+    }
+    __device__ __forceinline__ void add_cell(const T u[4], T gamma, T gm1) {
+        const T sp = cell_speed(u, gamma, gm1);
+        lam = pmax(lam, sp);
+        minrho = pmin(minrho, u[0]);
+        sum.add_cell(u);
+        const bool fin = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]);
+        if (!fin) ++nonfin;
+        else if (!in_G(u)) ++bad;
+    }
+    __device__ __forceinline__ void warp_reduce() {
+        for (int off = 16; off > 0; off >>= 1) {
+            lam = pmax(lam, __shfl_xor_sync(0xffffffffu, lam, off));
+            minrho = pmin(minrho, __shfl_xor_sync(0xffffffffu, minrho, off));
+            sum.shfl_add(off);
+            bad += __shfl_xor_sync(0xffffffffu, bad, off);
+            nonfin += __shfl_xor_sync(0xffffffffu, nonfin, off);
+        }
+    }
+};
+
+// Publish one CTA's monitor into the step's reduction slots. Must be called by
+// every thread of the CTA (uses shared memory and __syncthreads).
+template <typename T>
+__device__ void block_publish(Monitor<T> &m, DevCtl *C) {
+    __shared__ Monitor<T> part[32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
+    m.warp_reduce();
+    if (lane == 0) part[warp] = m;
+    __syncthreads();
+    if (warp == 0) {
+        if (lane < nwarp) m = part[lane];
+        else m.init();
+        m.warp_reduce();
+        if (lane == 0) {
+            atomicMax(&C->lam_key, ordered_key((double)m.lam));
+            atomicMin(&C->minrho_key, ordered_key((double)m.minrho));
+            for (int c = 0; c < 4; ++c) atomicAdd(&C->sum[c], m.sum.value(c));
+            if (m.bad) atomicAdd(&C->bad, (unsigned long long)m.bad);
+            if (m.nonfin) atomicAdd(&C->nonfinite, (unsigned long long)m.nonfin);
+        }
+    }
+}
+
+__device__ __forceinline__ void reset_slots(DevCtl *C) {
+    C->lam_key = 0ull;
+    C->minrho_key = ~0ull;
+    C->bad = 0ull;
+    C->nonfinite = 0ull;
+    for (int c = 0; c < 4; ++c) C->sum[c] = 0.0;
+    C->blocks_done = 0u;
+}
+
+// Free-running kinetic speed a = 2 lambda / (1 - alpha) (= 4 lambda at alpha = 1/2,
+// the critical Bouchut speed of Sec. 4), or the fixed one.
+__device__ __forceinline__ double next_speed(const DevCtl *C, double lam) {
+    return C->a_fixed > 0.0 ? C->a_fixed : 2.0 * lam / (1.0 - C->alpha);
+}
+
+// Step control for the next step: Delta t = dx / a, shortened to land on t_end.
+__device__ __forceinline__ void plan_next(DevCtl *C, double t, double a_free) {
+    double a = a_free, dt = C->dx / a_free;
+    int last = 0;
+    if (C->t_end > 0.0 && !C->done) {
+        if (t >= C->t_end) {
+            C->done = 1;
+        } else if (t + dt >= C->t_end) {
+            dt = C->t_end - t;
+            a = C->dx / dt;
+            last = 1;
+        }
+    }
+    C->a = a;
+    C->dt = dt;
+    C->last = last;
+}
+
+// Called by one thread of the last CTA to finish a step: the grid-wide max of
+// lambda over the new state sets a^{n+1} (Sec. 4 preamble), time advances by
+// the step's Delta t, monitors are published, sticky errors recorded.
+__device__ inline void finalize_step(DevCtl *C) {
+    volatile DevCtl *V = C;
+    const double lam = key_to_double(V->lam_key);
+    const double minrho = key_to_double(V->minrho_key);
+    const unsigned long long bad = V->bad, nonfin = V->nonfinite;
+    double s[4];
+    for (int c = 0; c < 4; ++c) s[c] = V->sum[c];
+    const long long n1 = C->n + 1;
+    const double t1 = C->t + C->dt;
+    C->lambda = lam;
+    C->min_rho = minrho;
+    C->bad_last = (long long)bad;
+    C->nonfinite_last = (long long)nonfin;
+    for (int c = 0; c < 4; ++c) C->sum_last[c] = s[c];
+    if ((bad || nonfin) && C->first_bad_step < 0) C->first_bad_step = n1;
+    if (nonfin || !isfinite(lam)) {
+        if (!C->status) C->status = VLBM_E_NONFINITE;
+        C->done = 1;
+    } else if (bad && !C->status) {
+        C->status = VLBM_E_POSITIVITY;
+    }
+    if (C->last || C->status == VLBM_E_TIMEOUT) C->done = 1;
+    double a_free = next_speed(C, lam);
+    if (!(a_free > 0.0) || !isfinite(a_free)) {
+        C->done = 1;
+        if (!C->status) C->status = VLBM_E_NONFINITE;
+        a_free = C->a;
+    }
+    C->n = n1;
+    C->t = t1;
+    C->a_free = a_free;
+    plan_next(C, t1, a_free);
+    reset_slots(C);
+    __threadfence();
+}
+
+// Last-CTA detection: returns true in every thread of the CTA that finished last.
+__device__ __forceinline__ bool last_block(DevCtl *C, unsigned int nblocks) {
+    __shared__ unsigned int ticket;
+    __threadfence();
+    __syncthreads();
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    if (tid == 0) ticket = atomicAdd(&C->blocks_done, 1u);
+    __syncthreads();
+    return ticket == nblocks - 1;
+}
+
+// ----------------------------------------------------------------- ghost frame
+
+// Source of ghost index i along an axis of n cells with the side's rule;
+// *mirror is set for a reflective wall (Sec. 4.8: symmetry wall).
+__device__ __forceinline__ int ghost_source(int i, int n, int bc_lo, int bc_hi, bool *mirror) {
+    *mirror = false;
+    if (i >= 0 && i < n) return i;
+    const int bc = i < 0 ? bc_lo : bc_hi;
+    if (bc == VLBM_BC_PERIODIC) return i < 0 ? i + n : i - n;
+    if (bc == VLBM_BC_TRANSMISSIVE) return i < 0 ? 0 : n - 1;
+    *mirror = true;
+    return i < 0 ? -1 - i : 2 * n - 1 - i;
+}
+
+// Fill the two ghost layers of buffer (n & 1): periodic wrap, zero-gradient copy
+// of u and u_1..u_4, or the mirror image (normal momentum negated in u and all
+// populations, u_1 <-> u_2 across an x-wall, u_3 <-> u_4 across a y-wall).
+// Corners take the x rule, then the y rule.
+template <typename T>
+__global__ void k_ghosts(StepArgs<T> A) {
+    const int nx = A.nx, ny = A.ny;
+    const long long rowpart = 4ll * (nx + 4);
+    const long long total = rowpart + 4ll * ny;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int gi, gj;
+    if (t < rowpart) {
+        const int r = (int)(t / (nx + 4));
+        gi = (int)(t % (nx + 4)) - 2;
+        gj = r < 2 ? r - 2 : ny + (r - 2);
+    } else {
+        const long long q = t - rowpart;
+        const int c = (int)(q / ny);
+        gj = (int)(q % ny);
+        gi = c < 2 ? c - 2 : nx + (c - 2);
+    }
+    bool mx, my;
+    const int si = ghost_source(gi, nx, A.bc[0], A.bc[1], &mx);
+    const int sj = ghost_source(gj, ny, A.bc[2], A.bc[3], &my);
+    T *buf = (A.ctl->n & 1) ? A.buf1 : A.buf0;
+    const long long src = cidx(A, si, sj), dst = cidx(A, gi, gj);
+    T v[kNPlane];
+#pragma unroll
+    for (int q = 0; q < kNPlane; ++q) v[q] = buf[q * A.plane + src];
+    if (mx) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { const T x = v[4 + c]; v[4 + c] = v[8 + c]; v[8 + c] = x; }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[4 * k + 1] = -v[4 * k + 1];
+    }
+    if (my) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { const T x = v[12 + c]; v[12 + c] = v[16 + c]; v[16 + c] = x; }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[4 * k + 2] = -v[4 * k + 2];
+    }
+#pragma unroll
+    for (int q = 0; q < kNPlane; ++q) buf[q * A.plane + dst] = v[q];
+}
+
+// ----------------------------------------------------------------- initial state
+
+// Conserved planes of u_0 into buffer 0, with lambda^0 and admissibility.
+template <typename T>
+__global__ void k_init_load(StepArgs<T> A, const T *__restrict__ rho, const T *__restrict__ mom,
+                            const T *__restrict__ E) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    DevCtl *C = A.ctl;
+    Monitor<T> m;
+    m.init();
+    const T gamma = T(A.gamma), gm1 = T(A.gamma - 1.0);
+    if (i < A.nx && j < A.ny) {
+        const long long k = (long long)j * A.nx + i, N = (long long)A.nx * A.ny;
+        T u[4] = {rho[k], mom[k], mom[N + k], E[k]};
+        const long long d = cidx(A, i, j);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) A.buf0[c * A.plane + d] = u[c];
+        m.add_cell(u, gamma, gm1);
+    }
+    block_publish(m, C);
+    if (last_block(C, gridDim.x * gridDim.y)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            volatile DevCtl *V = C;
+            const double lam = key_to_double(V->lam_key);
+            const unsigned long long bad = V->bad + V->nonfinite;
+            C->invalid_init = bad ? 1 : 0;
+            C->lambda = lam;
+            C->min_rho = key_to_double(V->minrho_key);
+            for (int c = 0; c < 4; ++c) C->sum_last[c] = V->sum[c];
+            double a_free = next_speed(C, lam);
+            if (!(a_free > 0.0) || !isfinite(a_free)) {
+                C->invalid_init = 1;
+                a_free = 1.0;
+            }
+            C->n = 0;
+            C->t = 0.0;
+            C->a_free = a_free;
+            C->done = C->invalid_init;
+            C->status = C->invalid_init ? VLBM_E_INVAL : 0;
+            plan_next(C, 0.0, a_free);
+            reset_slots(C);
+            __threadfence();
+        }
+    }
+}
+
+// Populations at equilibrium, u_k^0 = M_k(u_0) (Sec. 4 preamble), with a^0.
+template <typename T>
+__global__ void k_init_pops(StepArgs<T> A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= A.nx || j >= A.ny) return;
+    const StepConsts<T> k = make_consts<T>(A.ctl->a, A.alpha, A.gamma, A.eps);
+    const long long d = cidx(A, i, j);
+    T u[4], f[4], g[4], M1[4], M2[4], M3[4], M4[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) u[c] = A.buf0[c * A.plane + d];
+    euler_fluxes(u, k.gm1, f, g);
+    maxwell_pm(u, f, k, M1, M2);
+    maxwell_pm(u, g, k, M3, M4);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        A.buf0[(4 + c) * A.plane + d] = M1[c];
+        A.buf0[(8 + c) * A.plane + d] = M2[c];
+        A.buf0[(12 + c) * A.plane + d] = M3[c];
+        A.buf0[(16 + c) * A.plane + d] = M4[c];
+    }
+}
+
+// ----------------------------------------------------------------- outputs
+
+template <typename T>
+__global__ void k_moments(StepArgs<T> A, T *rho, T *mom, T *E) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= A.nx || j >= A.ny) return;
+    const T *buf = (A.ctl->n & 1) ? A.buf1 : A.buf0;
+    const long long d = cidx(A, i, j), k = (long long)j * A.nx + i, N = (long long)A.nx * A.ny;
+    if (rho) rho[k] = buf[d];
+    if (mom) {
+        mom[k] = buf[A.plane + d];
+        mom[N + k] = buf[2 * A.plane + d];
+    }
+    if (E) E[k] = buf[3 * A.plane + d];
+}
+
+// Checkpoint: 64-byte header {n, t, a, dt, a_free, t_end, last|done<<1, status},
+// then the 20 planes of the current state, compact.
+template <typename T>
+__global__ void k_save(StepArgs<T> A, unsigned char *dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const DevCtl *C = A.ctl;
+    if (i == 0 && j == 0) {
+        double *h = (double *)dst;
+        long long *hl = (long long *)dst;
+        hl[0] = C->n;
+        h[1] = C->t;
+        h[2] = C->a;
+        h[3] = C->dt;
+        h[4] = C->a_free;
+        h[5] = C->t_end;
+        hl[6] = (long long)C->last | ((long long)C->done << 1);
+        hl[7] = (long long)C->status;
+    }
+    if (i >= A.nx || j >= A.ny) return;
+    const T *buf = (C->n & 1) ? A.buf1 : A.buf0;
+    T *out = (T *)(dst + 64);
+    const long long d = cidx(A, i, j), k = (long long)j * A.nx + i, N = (long long)A.nx * A.ny;
+#pragma unroll
+    for (int q = 0; q < kNPlane; ++q) out[q * N + k] = buf[q * A.plane + d];
+}
+
+// Restore: the state goes into buffer (n & 1) of the stored n, so that the
+// step sequence (and its ping-pong parity) is exactly the uninterrupted one.
+template <typename T>
+__global__ void k_load(StepArgs<T> A, const unsigned char *src) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const long long n = ((const long long *)src)[0];
+    if (i < A.nx && j < A.ny) {
+        T *buf = (n & 1) ? A.buf1 : A.buf0;
+        const T *in = (const T *)(src + 64);
+        const long long d = cidx(A, i, j), k = (long long)j * A.nx + i, N = (long long)A.nx * A.ny;
+#pragma unroll
+        for (int q = 0; q < kNPlane; ++q) buf[q * A.plane + d] = in[q * N + k];
+    }
+}
+
+}  // namespace vlbm

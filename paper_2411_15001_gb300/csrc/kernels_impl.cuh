@@ -1,0 +1,125 @@
+// kernels_impl.cuh -- host launchers for one storage type VLBM_T (included by
+// kernels_f32.cu and kernels_f64.cu so that the two precisions compile in parallel).
+#include "common.cuh"
+#include "step_fused.cuh"
+#include "step_simple.cuh"
+
+namespace vlbm {
+
+namespace {
+constexpr int kBX = 32, kBY = 8;
+inline dim3 cell_grid(int nx, int ny) { return dim3((nx + kBX - 1) / kBX, (ny + kBY - 1) / kBY); }
+}  // namespace
+
+template <>
+cudaError_t launch_ghosts<VLBM_T>(const StepArgs<VLBM_T> &A, cudaStream_t s) {
+    const long long total = 4ll * (A.nx + 4) + 4ll * A.ny;
+    const int thr = 128;
+    k_ghosts<VLBM_T><<<(unsigned)((total + thr - 1) / thr), thr, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_init<VLBM_T>(const StepArgs<VLBM_T> &A, const VLBM_T *rho, const VLBM_T *mom,
+                                const VLBM_T *E, cudaStream_t s) {
+    const dim3 blk(kBX, kBY), grd = cell_grid(A.nx, A.ny);
+    k_init_load<VLBM_T><<<grd, blk, 0, s>>>(A, rho, mom, E);
+    k_init_pops<VLBM_T><<<grd, blk, 0, s>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_ghosts<VLBM_T>(A, s);
+}
+
+template <>
+cudaError_t launch_step_simple<VLBM_T>(const StepArgs<VLBM_T> &A, cudaStream_t s) {
+    const dim3 blk(kBX, kBY), grd = cell_grid(A.nx, A.ny);
+    switch (A.limiter) {
+        case VLBM_LIM_FIRST_ORDER: k_step_simple<VLBM_T, VLBM_LIM_FIRST_ORDER><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_NONE: k_step_simple<VLBM_T, VLBM_LIM_NONE><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_PP: k_step_simple<VLBM_T, VLBM_LIM_PP><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_LMP: k_step_simple<VLBM_T, VLBM_LIM_LMP><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_RLMP: k_step_simple<VLBM_T, VLBM_LIM_RLMP><<<grd, blk, 0, s>>>(A); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+template <int LIM>
+cudaError_t fused_one(const StepArgs<VLBM_T> &A, const CUtensorMap &tm, int strips, int grid,
+                      cudaStream_t s) {
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t smem = sizeof(FusedSmem<VLBM_T>);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused<VLBM_T, LIM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    k_step_fused<VLBM_T, LIM><<<grid, kFB, smem, s>>>(tm, A, strips);
+    return cudaGetLastError();
+}
+
+template <int LIM>
+int fused_blocks_per_sm() {
+    int nb = 0;
+    const size_t smem = sizeof(FusedSmem<VLBM_T>);
+    cudaFuncSetAttribute(k_step_fused<VLBM_T, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_fused<VLBM_T, LIM>, kFB, smem) != cudaSuccess)
+        nb = 1;
+    return nb > 0 ? nb : 1;
+}
+}  // namespace
+
+template <>
+int fused_occupancy<VLBM_T>(int limiter) {
+    switch (limiter) {
+        case VLBM_LIM_FIRST_ORDER: return fused_blocks_per_sm<VLBM_LIM_FIRST_ORDER>();
+        case VLBM_LIM_NONE: return fused_blocks_per_sm<VLBM_LIM_NONE>();
+        case VLBM_LIM_PP: return fused_blocks_per_sm<VLBM_LIM_PP>();
+        case VLBM_LIM_LMP: return fused_blocks_per_sm<VLBM_LIM_LMP>();
+        default: return fused_blocks_per_sm<VLBM_LIM_RLMP>();
+    }
+}
+
+template <>
+cudaError_t launch_step_fused<VLBM_T>(const StepArgs<VLBM_T> &A, const CUtensorMap &tm, int strips,
+                                      int grid, cudaStream_t s) {
+    cudaError_t e;
+    switch (A.limiter) {
+        case VLBM_LIM_FIRST_ORDER: e = fused_one<VLBM_LIM_FIRST_ORDER>(A, tm, strips, grid, s); break;
+        case VLBM_LIM_NONE: e = fused_one<VLBM_LIM_NONE>(A, tm, strips, grid, s); break;
+        case VLBM_LIM_PP: e = fused_one<VLBM_LIM_PP>(A, tm, strips, grid, s); break;
+        case VLBM_LIM_LMP: e = fused_one<VLBM_LIM_LMP>(A, tm, strips, grid, s); break;
+        case VLBM_LIM_RLMP: e = fused_one<VLBM_LIM_RLMP>(A, tm, strips, grid, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return e;
+}
+
+template <>
+cudaError_t launch_moments<VLBM_T>(const StepArgs<VLBM_T> &A, VLBM_T *rho, VLBM_T *mom, VLBM_T *E,
+                                   cudaStream_t s) {
+    k_moments<VLBM_T><<<cell_grid(A.nx, A.ny), dim3(kBX, kBY), 0, s>>>(A, rho, mom, E);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_save<VLBM_T>(const StepArgs<VLBM_T> &A, void *dst, cudaStream_t s) {
+    k_save<VLBM_T><<<cell_grid(A.nx, A.ny), dim3(kBX, kBY), 0, s>>>(A, (unsigned char *)dst);
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_load<VLBM_T>(const StepArgs<VLBM_T> &A, const void *src, cudaStream_t s) {
+    cudaError_t e0 = launch_load_header(A.ctl, src, s);
+    if (e0 != cudaSuccess) return e0;
+    k_load<VLBM_T><<<cell_grid(A.nx, A.ny), dim3(kBX, kBY), 0, s>>>(A, (const unsigned char *)src);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_ghosts<VLBM_T>(A, s);
+}
+
+}  // namespace vlbm

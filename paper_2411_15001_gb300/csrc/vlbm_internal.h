@@ -1,0 +1,129 @@
+// vlbm_internal.h -- device-side data layout and launch interfaces shared by the
+// translation units of libvlbm (not part of the public ABI; see include/vlbm.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+namespace vlbm {
+
+// Padded plane layout. Cell (i, j), -2 <= i < nx+2, -2 <= j < ny+2, of plane q
+// in a state buffer lives at q * plane + (j + kOY) * pitch + (i + kOX).
+// Columns 0, 1 and nx+2, nx+3 of a padded row hold the two ghost layers of the
+// x sides, rows 0, 1 and ny+2, ny+3 those of the y sides. With kOX = 2 the
+// row-marching kernel's TMA boxes, which start two cells left of a strip of
+// 124 output columns (interior column 124 s - 2, padded column 124 s), begin on
+// a 16-byte boundary; pitch is a multiple of 32 elements.
+constexpr int kOX = 2;
+constexpr int kOY = 2;
+constexpr int kNPlane = 20;   // u (4) and u_1..u_4 (4 each); u_5 is never stored
+
+struct Layout {
+    int nx, ny;
+    int pitch;          // elements per padded row (multiple of 32)
+    int rows;           // ny + 4
+    long long plane;    // elements per plane (multiple of 64)
+    int elem;           // bytes per element (4 or 8)
+    size_t buf_bytes;   // bytes of one 20-plane buffer
+    size_t ctl_offset;  // byte offset of the control block in the workspace
+    size_t total;       // workspace bytes
+};
+
+Layout make_layout(int nx, int ny, int elem);
+
+// Order-preserving key of a double for atomicMin/atomicMax on unsigned 64-bit
+// integers (NaN with the sign bit clear sorts above +inf).
+__host__ __device__ inline unsigned long long ordered_key(double x) {
+#ifdef __CUDA_ARCH__
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long b;
+    memcpy(&b, &x, sizeof b);
+#endif
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__host__ __device__ inline double key_to_double(unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double x;
+    memcpy(&x, &b, sizeof x);
+    return x;
+#endif
+}
+
+// Device control block: time-step state written by the last CTA of each step
+// (the grid-wide lambda^n dependency of Sec. 4 is resolved at the kernel
+// boundary), the per-step reduction slots, and the published monitors.
+struct DevCtl {
+    // step state
+    long long n;           // steps taken; the current state is buffer n & 1
+    double t;              // simulated time
+    double a;              // kinetic speed of the next step
+    double dt;             // time step of the next step
+    double a_free;         // kinetic speed before any shortening to reach t_end
+    double t_end;          // > 0: stop at this time (last step clipped)
+    int last;              // the next step is the clipped final one
+    int done;              // no further step may run
+    int status;            // sticky VLBM_E_* (0 = OK)
+    int invalid_init;      // cells of u_0 outside G at the last initialisation
+    long long first_bad_step;
+    // reduction slots of the step in flight (reset by the finaliser)
+    unsigned long long lam_key;      // ordered key of max lambda
+    unsigned long long minrho_key;   // ordered key of min rho
+    unsigned long long bad;          // cells outside G
+    unsigned long long nonfinite;    // non-finite cells
+    double sum[4];
+    unsigned int blocks_done;
+    unsigned int pad0;
+    // published monitors of the current state
+    double lambda;
+    double min_rho;
+    long long bad_last;
+    long long nonfinite_last;
+    double sum_last[4];
+    // constants
+    double dx, alpha, a_fixed, eps, gamma;
+};
+
+static_assert(sizeof(DevCtl) == 248, "bench.py reads the control block size");
+
+template <typename T>
+struct StepArgs {
+    T *buf0, *buf1;     // the two 20-plane state buffers
+    long long plane;    // plane stride (elements)
+    int pitch;
+    int nx, ny;
+    int bc[4];          // west, east, south, north
+    int limiter;
+    double gamma;
+    double alpha;
+    double eps;
+    DevCtl *ctl;
+};
+
+// Host launchers (stream-ordered; return cudaError_t of the launch).
+cudaError_t launch_ctl_reset(DevCtl *ctl, double dx, double alpha, double a_fixed, double eps,
+                             double gamma, cudaStream_t s);
+template <typename T> cudaError_t launch_init(const StepArgs<T> &a, const T *rho, const T *mom,
+                                              const T *E, cudaStream_t s);
+template <typename T> cudaError_t launch_ghosts(const StepArgs<T> &a, cudaStream_t s);
+template <typename T> cudaError_t launch_step_simple(const StepArgs<T> &a, cudaStream_t s);
+// Row-marching kernel: strips of 124 columns, `grid` persistent CTAs.
+template <typename T> cudaError_t launch_step_fused(const StepArgs<T> &a, const CUtensorMap &tm, int strips,
+                                                   int grid, cudaStream_t s);
+template <typename T> int fused_occupancy(int limiter);   // CTAs per SM of the fused kernel
+constexpr int kFusedOut = 124;                             // output columns per strip
+constexpr int kFusedBox = 128;                             // TMA box width (columns)
+template <typename T> cudaError_t launch_moments(const StepArgs<T> &a, T *rho, T *mom, T *E,
+                                                 cudaStream_t s);
+template <typename T> cudaError_t launch_save(const StepArgs<T> &a, void *dst, cudaStream_t s);
+template <typename T> cudaError_t launch_load(const StepArgs<T> &a, const void *src, cudaStream_t s);
+cudaError_t launch_set_tend(DevCtl *ctl, double t_end, cudaStream_t s);
+cudaError_t launch_load_header(DevCtl *ctl, const void *src, cudaStream_t s);
+
+}  // namespace vlbm

@@ -1,0 +1,282 @@
+"""Thin Python binding of libvlbm (include/vlbm.h).
+
+The functions below carry the C names and only marshal arguments; every step of
+the scheme runs in the CUDA library. The `VLBM` class adds PyTorch plumbing:
+torch allocates the device workspace and supplies the stream. There is no CPU
+fallback: if the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvlbm.so")
+
+OK, E_INVAL, E_CUDA, E_POSITIVITY, E_NONFINITE, E_TIMEOUT, E_UNSUPPORTED, E_NOMEM = 0, -1, -2, -3, -4, -5, -6, -7
+LIM_FIRST_ORDER, LIM_NONE, LIM_PP, LIM_LMP, LIM_RLMP = range(5)
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = range(3)
+FP64, FP32 = 0, 1
+KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_FUSED = range(3)
+
+LIMITERS = {"first": LIM_FIRST_ORDER, "none": LIM_NONE, "pp": LIM_PP, "lmp": LIM_LMP, "rlmp": LIM_RLMP}
+
+
+class vlbm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("dx", ctypes.c_double),
+                ("bc", ctypes.c_int32 * 4)]
+
+
+class vlbm_opts(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("eps", ctypes.c_double), ("kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class vlbm_monitor_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("t", ctypes.c_double), ("a", ctypes.c_double),
+                ("dt", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("bad_cells", ctypes.c_int64), ("nonfinite_cells", ctypes.c_int64),
+                ("first_bad_step", ctypes.c_int64), ("min_rho", ctypes.c_double),
+                ("sum", ctypes.c_double * 4), ("done", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class VLBMError(RuntimeError):
+    def __init__(self, code: int, detail: str = ""):
+        self.code = code
+        super().__init__(f"{vlbm_strerror(code)} ({code}): {detail}")
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_2411_15001_gb300.build` "
+                      "(or __graft_entry__.build()). There is no CPU fallback.")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P, _I32, _I64, _D, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+
+_SIGS = {
+    "vlbm_workspace_bytes": (_SZ, [ctypes.POINTER(vlbm_grid), _I32]),
+    "vlbm_init": (ctypes.c_int, [ctypes.POINTER(vlbm_grid), _D, _D, _I32, _I32, ctypes.POINTER(vlbm_opts),
+                                 _P, _SZ, _P, ctypes.POINTER(_P)]),
+    "vlbm_set_conserved": (ctypes.c_int, [_P, _P, _P, _P]),
+    "vlbm_step": (ctypes.c_int, [_P, _I64]),
+    "vlbm_step_to": (ctypes.c_int, [_P, _D, _I64]),
+    "vlbm_moments": (ctypes.c_int, [_P, _P, _P, _P]),
+    "vlbm_monitors": (ctypes.c_int, [_P, ctypes.POINTER(vlbm_monitor_t)]),
+    "vlbm_sync": (ctypes.c_int, [_P]),
+    "vlbm_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "vlbm_checkpoint_bytes": (_SZ, [_P]),
+    "vlbm_save": (ctypes.c_int, [_P, _P]),
+    "vlbm_load": (ctypes.c_int, [_P, _P]),
+    "vlbm_profile": (ctypes.c_int, [_P, _I32]),
+    "vlbm_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "vlbm_destroy": (None, [_P]),
+    "vlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "vlbm_last_error_detail": (ctypes.c_int, [_P, ctypes.c_char_p, _SZ]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def library():
+    return _lib
+
+
+# ------------------------------------------------------------------ C-named calls
+def vlbm_workspace_bytes(grid: vlbm_grid, precision: int) -> int:
+    return int(_lib.vlbm_workspace_bytes(ctypes.byref(grid), precision))
+
+
+def vlbm_init(grid, gamma, lam, limiter, precision, opts, d_workspace, workspace_bytes, stream):
+    out = _P()
+    rc = _lib.vlbm_init(ctypes.byref(grid), gamma, lam, limiter, precision,
+                        ctypes.byref(opts) if opts is not None else None,
+                        d_workspace, workspace_bytes, stream, ctypes.byref(out))
+    return rc, out
+
+
+def vlbm_set_conserved(s, d_rho, d_mom, d_E) -> int:
+    return _lib.vlbm_set_conserved(s, d_rho, d_mom, d_E)
+
+
+def vlbm_step(s, nsteps: int) -> int:
+    return _lib.vlbm_step(s, nsteps)
+
+
+def vlbm_step_to(s, t_end: float, max_steps: int) -> int:
+    return _lib.vlbm_step_to(s, t_end, max_steps)
+
+
+def vlbm_moments(s, d_rho, d_mom, d_E) -> int:
+    return _lib.vlbm_moments(s, d_rho, d_mom, d_E)
+
+
+def vlbm_monitors(s):
+    m = vlbm_monitor_t()
+    rc = _lib.vlbm_monitors(s, ctypes.byref(m))
+    return rc, m
+
+
+def vlbm_sync(s) -> int:
+    return _lib.vlbm_sync(s)
+
+
+def vlbm_time(s):
+    t, n = _D(), _I64()
+    rc = _lib.vlbm_time(s, ctypes.byref(t), ctypes.byref(n))
+    return rc, t.value, n.value
+
+
+def vlbm_checkpoint_bytes(s) -> int:
+    return int(_lib.vlbm_checkpoint_bytes(s))
+
+
+def vlbm_save(s, d_dst) -> int:
+    return _lib.vlbm_save(s, d_dst)
+
+
+def vlbm_load(s, d_src) -> int:
+    return _lib.vlbm_load(s, d_src)
+
+
+def vlbm_profile(s, enable: bool) -> int:
+    return _lib.vlbm_profile(s, 1 if enable else 0)
+
+
+def vlbm_profile_read(s):
+    ms, n = _D(), _I64()
+    rc = _lib.vlbm_profile_read(s, ctypes.byref(ms), ctypes.byref(n))
+    return rc, ms.value, n.value
+
+
+def vlbm_destroy(s) -> None:
+    _lib.vlbm_destroy(s)
+
+
+def vlbm_strerror(code: int) -> str:
+    return _lib.vlbm_strerror(code).decode()
+
+
+def vlbm_last_error_detail(s=None) -> str:
+    buf = ctypes.create_string_buffer(256)
+    _lib.vlbm_last_error_detail(s, buf, 256)
+    return buf.value.decode()
+
+
+def _check(rc: int, s=None) -> int:
+    if rc != OK:
+        raise VLBMError(rc, vlbm_last_error_detail(s))
+    return rc
+
+
+# ------------------------------------------------------------------ torch front end
+class VLBM:
+    """One 2D grid advanced by the blended D2Q5 vectorial LBM on a CUDA device.
+
+    Device memory (the workspace, inputs, outputs) is torch-allocated; the stream
+    is torch's current stream of `device` unless one is given.
+    """
+
+    def __init__(self, nx: int, ny: int, dx: float, bc=(0, 0, 0, 0), gamma: float = 1.4,
+                 lam: float = 0.0, limiter=LIM_PP, precision=FP32, alpha: float = 0.5,
+                 eps: float = 1e-16, kernel=KERNEL_AUTO, device=None, stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        if isinstance(limiter, str):
+            limiter = LIMITERS[limiter.lower()]
+        self.nx, self.ny, self.dx = nx, ny, dx
+        self.precision = precision
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        self.grid = vlbm_grid(nx, ny, dx, (ctypes.c_int32 * 4)(*bc))
+        self.opts = vlbm_opts(alpha, eps, kernel, 0)
+        nbytes = vlbm_workspace_bytes(self.grid, precision)
+        if nbytes == 0:
+            raise VLBMError(E_INVAL, "invalid grid")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        rc, self._s = vlbm_init(self.grid, gamma, lam, limiter, precision, self.opts,
+                                self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        _check(rc)
+
+    def _ptr(self, t):
+        if t is None:
+            return None
+        if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+            raise ValueError("tensor must be contiguous, on the solver's device, in its dtype")
+        return t.data_ptr()
+
+    def set_conserved(self, rho, mom, E):
+        """rho, E: (ny, nx); mom: (2, ny, nx) -- device tensors in the solver's dtype."""
+        _check(vlbm_set_conserved(self._s, self._ptr(rho), self._ptr(mom), self._ptr(E)), self._s)
+
+    def step(self, nsteps: int = 1):
+        _check(vlbm_step(self._s, int(nsteps)), self._s)
+
+    def step_to(self, t_end: float, max_steps: int = 10 ** 9) -> int:
+        rc = vlbm_step_to(self._s, float(t_end), int(max_steps))
+        return _check(rc, self._s)
+
+    def moments(self):
+        t = self.torch
+        rho = t.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)
+        mom = t.empty((2, self.ny, self.nx), dtype=self.dtype, device=self.device)
+        E = t.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)
+        _check(vlbm_moments(self._s, rho.data_ptr(), mom.data_ptr(), E.data_ptr()), self._s)
+        return rho, mom, E
+
+    def monitors(self) -> dict:
+        rc, m = vlbm_monitors(self._s)
+        if rc == E_CUDA:
+            _check(rc, self._s)
+        return {"status": m.status, "n": m.n, "t": m.t, "a": m.a, "dt": m.dt, "lambda": m.lambda_,
+                "bad_cells": m.bad_cells, "nonfinite_cells": m.nonfinite_cells,
+                "first_bad_step": m.first_bad_step, "min_rho": m.min_rho, "sum": list(m.sum),
+                "done": m.done}
+
+    def sync(self) -> int:
+        return vlbm_sync(self._s)
+
+    def time(self):
+        rc, t, n = vlbm_time(self._s)
+        if rc == E_CUDA:
+            _check(rc, self._s)
+        return t, n
+
+    def save(self):
+        buf = self.torch.empty(vlbm_checkpoint_bytes(self._s), dtype=self.torch.uint8, device=self.device)
+        _check(vlbm_save(self._s, buf.data_ptr()), self._s)
+        return buf
+
+    def load(self, buf):
+        _check(vlbm_load(self._s, buf.data_ptr()), self._s)
+
+    def state_planes(self):
+        """(20, ny, nx) copy of the current state (u, then u_1..u_4) via a checkpoint."""
+        buf = self.save()
+        return buf[64:].view(self.dtype).view(20, self.ny, self.nx)
+
+    def profile(self, enable: bool = True):
+        """Time every step kernel with a CUDA event pair (see vlbm_profile)."""
+        _check(vlbm_profile(self._s, enable), self._s)
+
+    def profile_read(self):
+        """(summed step-kernel milliseconds, number of timed launches); waits for the stream."""
+        rc, ms, n = vlbm_profile_read(self._s)
+        _check(rc, self._s)
+        return ms, n
+
+    def close(self):
+        if getattr(self, "_s", None):
+            vlbm_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
