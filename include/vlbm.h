@@ -117,6 +117,8 @@ typedef struct {
     int64_t first_bad_step;    /* first step whose output left G (or went non-finite); -1 if none */
     double min_rho;            /* min density of the current state */
     double sum[4];             /* FP64 sums of rho, m1, m2, E over the cells of the current state */
+    int64_t theta_p_fp64_faces; /* faces of the last step whose theta_p needed the FP64 solve
+                                   (FP32 state; every face for an FP64 state) */
     int32_t done;              /* 1 once vlbm_step_to has reached its final time */
     int32_t status;            /* sticky VLBM_OK / VLBM_E_* of the device */
 } vlbm_monitor_t;

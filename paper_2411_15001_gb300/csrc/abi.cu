@@ -177,7 +177,7 @@ static bool make_tmap(vlbm_state *s) {
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     CUresult r = encode(&s->tmap, s->L.elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                         3, s->ws, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -369,6 +369,7 @@ int vlbm_monitors(vlbm_state *s, vlbm_monitor_t *out) {
     out->first_bad_step = h.first_bad_step;
     out->min_rho = h.min_rho;
     for (int c = 0; c < 4; ++c) out->sum[c] = h.sum_last[c];
+    out->theta_p_fp64_faces = h.fp64_last;
     out->done = h.done;
     out->status = h.status;
     return h.status;

@@ -39,50 +39,62 @@ struct DFloat {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Per-thread conservation sums. FP32: Kahan-compensated float accumulators
+// (the compensation keeps about twice the float precision over a column of a
+// few hundred cells); the warp and CTA reductions carry (hi, lo) pairs with
+// TwoSum, and one double per CTA goes to the FP64 atomics.
 template <typename T> struct SumAcc;
 template <> struct SumAcc<float> {
-    DFloat s[4];
-    __device__ __forceinline__ void zero() { for (int c = 0; c < 4; ++c) s[c].hi = s[c].lo = 0.f; }
-    __device__ __forceinline__ void add_cell(const float u[4]) { for (int c = 0; c < 4; ++c) s[c].add(u[c], 0.f); }
-    __device__ __forceinline__ void shfl_add(int off) {
-        for (int c = 0; c < 4; ++c) {
-            const float h = __shfl_xor_sync(0xffffffffu, s[c].hi, off);
-            const float l = __shfl_xor_sync(0xffffffffu, s[c].lo, off);
-            s[c].add(h, l);
+    float s[4], c[4];
+    __device__ __forceinline__ void zero() { for (int q = 0; q < 4; ++q) s[q] = c[q] = 0.f; }
+    __device__ __forceinline__ void add_cell(const float u[4]) {
+        for (int q = 0; q < 4; ++q) {
+            const float y = __fsub_rn(u[q], c[q]);
+            const float t = __fadd_rn(s[q], y);
+            c[q] = __fsub_rn(__fsub_rn(t, s[q]), y);
+            s[q] = t;
         }
     }
-    __device__ __forceinline__ double value(int c) const { return s[c].value(); }
+    __device__ __forceinline__ void shfl_add(int off) {
+        for (int q = 0; q < 4; ++q) {
+            DFloat a{s[q], -c[q]};
+            a.add(__shfl_xor_sync(0xffffffffu, s[q], off), -__shfl_xor_sync(0xffffffffu, c[q], off));
+            s[q] = a.hi;
+            c[q] = -a.lo;
+        }
+    }
+    __device__ __forceinline__ double value(int q) const { return (double)s[q] - (double)c[q]; }
 };
 template <> struct SumAcc<double> {
     double s[4];
-    __device__ __forceinline__ void zero() { for (int c = 0; c < 4; ++c) s[c] = 0.0; }
-    __device__ __forceinline__ void add_cell(const double u[4]) { for (int c = 0; c < 4; ++c) s[c] += u[c]; }
+    __device__ __forceinline__ void zero() { for (int q = 0; q < 4; ++q) s[q] = 0.0; }
+    __device__ __forceinline__ void add_cell(const double u[4]) { for (int q = 0; q < 4; ++q) s[q] += u[q]; }
     __device__ __forceinline__ void shfl_add(int off) {
-        for (int c = 0; c < 4; ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+        for (int q = 0; q < 4; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
     }
-    __device__ __forceinline__ double value(int c) const { return s[c]; }
+    __device__ __forceinline__ double value(int q) const { return s[q]; }
 };
 
 // Per-thread monitor of the cells a thread wrote: max lambda, min rho, sums,
-// and the counts of cells outside G / non-finite.
+// the counts of cells outside G / non-finite, and of faces whose theta_p needed
+// the FP64 solve.
 template <typename T>
 struct Monitor {
     T lam, minrho;
     SumAcc<T> sum;
-    unsigned int bad, nonfin;
+    unsigned int bad, nonfin, fp64;
     __device__ __forceinline__ void init() {
         lam = T(0);
         minrho = T(INFINITY);
         sum.zero();
-        bad = nonfin = 0u;
+        bad = nonfin = fp64 = 0u;
     }
     __device__ __forceinline__ void add_cell(const T u[4], T gamma, T gm1) {
-        const T sp = cell_speed(u, gamma, gm1);
+        const T sp = cell_speed(u, gamma, gm1);   // NaN or inf if any component is
         lam = pmax(lam, sp);
         minrho = pmin(minrho, u[0]);
         sum.add_cell(u);
-        const bool fin = isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]);
-        if (!fin) ++nonfin;
+        if (!(sp <= T(3.0e38))) ++nonfin;
         else if (!in_G(u)) ++bad;
     }
     __device__ __forceinline__ void warp_reduce() {
@@ -92,6 +104,7 @@ struct Monitor {
             sum.shfl_add(off);
             bad += __shfl_xor_sync(0xffffffffu, bad, off);
             nonfin += __shfl_xor_sync(0xffffffffu, nonfin, off);
+            fp64 += __shfl_xor_sync(0xffffffffu, fp64, off);
         }
     }
 };
@@ -117,6 +130,7 @@ __device__ void block_publish(Monitor<T> &m, DevCtl *C) {
             for (int c = 0; c < 4; ++c) atomicAdd(&C->sum[c], m.sum.value(c));
             if (m.bad) atomicAdd(&C->bad, (unsigned long long)m.bad);
             if (m.nonfin) atomicAdd(&C->nonfinite, (unsigned long long)m.nonfin);
+            if (m.fp64) atomicAdd(&C->fp64_faces, (unsigned long long)m.fp64);
         }
     }
 }
@@ -126,6 +140,7 @@ __device__ __forceinline__ void reset_slots(DevCtl *C) {
     C->minrho_key = ~0ull;
     C->bad = 0ull;
     C->nonfinite = 0ull;
+    C->fp64_faces = 0ull;
     for (int c = 0; c < 4; ++c) C->sum[c] = 0.0;
     C->blocks_done = 0u;
 }
@@ -162,6 +177,7 @@ __device__ inline void finalize_step(DevCtl *C) {
     const double lam = key_to_double(V->lam_key);
     const double minrho = key_to_double(V->minrho_key);
     const unsigned long long bad = V->bad, nonfin = V->nonfinite;
+    C->fp64_last = (long long)V->fp64_faces;
     double s[4];
     for (int c = 0; c < 4; ++c) s[c] = V->sum[c];
     const long long n1 = C->n + 1;

@@ -146,8 +146,13 @@ struct FusedCtx {
                                     S.nu[rp][br], k);
                 try_ = theta_rho_lmp(ys_us[0], ys_df[0], mu2, nu2, mu1, nu1, k);
             }
-            tx = combine_theta(trx, xs_us, xs_df, k);
-            ty = combine_theta(try_, ys_us, ys_df, k);
+            unsigned int nx64 = 0, ny64 = 0;
+            tx = combine_theta(trx, xs_us, xs_df, k, nx64);
+            ty = combine_theta(try_, ys_us, ys_df, k, ny64);
+            // faces counted once: an x-face by the cell west of it, a y-face by the one south of it
+            const bool col_own = b >= 2 && b < 2 + kFOut && c < A.nx;
+            if (col_own && R - 1 >= y0 && R - 1 < y1) mon.fp64 += nx64;
+            if (col_own && R - 2 >= y0 && R - 2 < y1) mon.fp64 += ny64;
         }
         S.thx[(R - 1) & 1][b] = tx;
         mu2 = mu1;
@@ -157,7 +162,7 @@ struct FusedCtx {
         for (int q = 0; q < 4; ++q) {
             xs_us[q] = face_star(S.X[xs][q][b], S.X[xs][4 + q][b], S.X[xs][q][br], S.X[xs][4 + q][br], k);
             xs_df[q] = face_dflux(S.X[xs][8 + q][b], S.X[xs][12 + q][br], k);
-            ys_us[q] = face_star(H1.u[q], H1.g[q], H0.u[q], H0.g[q], k);
+            ys_us[q] = q == 0 ? rsy_new : face_star(H1.u[q], H1.g[q], H0.u[q], H0.g[q], k);
             ys_df[q] = face_dflux(H1.d3[q], H0.d4[q], k);
         }
         S.rsx[R & 1][b] = xs_us[0];

@@ -25,13 +25,13 @@ struct CellLoad {
 };
 
 // theta of the four faces of cell (i, j), Sec. 3.2-3.4, given the face states.
-template <typename T, int LIM>
-__device__ __forceinline__ void cell_thetas(const CellLoad<T> &L, int i, int j, const T uC[4],
+template <typename T, int LIM, typename Loader>
+__device__ __forceinline__ void cell_thetas(const Loader &L, int i, int j, const T uC[4],
                                             const T uW[4], const T uE[4], const T uS[4],
                                             const T uN[4], const T usW[4], const T dfW[4],
                                             const T usE[4], const T dfE[4], const T usS[4],
                                             const T dfS[4], const T usN[4], const T dfN[4],
-                                            const StepConsts<T> &k, T th[4]) {
+                                            const StepConsts<T> &k, T th[4], unsigned int &n_fp64) {
     if (LIM == VLBM_LIM_FIRST_ORDER) {
         th[0] = th[1] = th[2] = th[3] = T(0);
         return;
@@ -93,10 +93,12 @@ __device__ __forceinline__ void cell_thetas(const CellLoad<T> &L, int i, int j, 
         tr[2] = theta_rho_lmp(usS[0], dfS[0], muS, nuS, muC, nuC, k);
         tr[3] = theta_rho_lmp(usN[0], dfN[0], muC, nuC, muN, nuN, k);
     }
-    th[0] = combine_theta(tr[0], usW, dfW, k);
-    th[1] = combine_theta(tr[1], usE, dfE, k);
-    th[2] = combine_theta(tr[2], usS, dfS, k);
-    th[3] = combine_theta(tr[3], usN, dfN, k);
+    unsigned int own = 0, other = 0;   // faces are owned by their west / south cell
+    th[0] = combine_theta(tr[0], usW, dfW, k, other);
+    th[1] = combine_theta(tr[1], usE, dfE, k, own);
+    th[2] = combine_theta(tr[2], usS, dfS, k, other);
+    th[3] = combine_theta(tr[3], usN, dfN, k, own);
+    n_fp64 += own;
 }
 
 // Face state u* and dF (eq. D2Q5_convexproof_3, eq. 2nd-order_flux).
@@ -108,6 +110,68 @@ __device__ __forceinline__ void face_state(const T uL[4], const T fL[4], const T
     for (int c = 0; c < 4; ++c) {
         us[c] = face_star(uL[c], fL[c], uR[c], fR[c], k);
         df[c] = face_dflux(dL[c], dR[c], k);
+    }
+}
+
+// One cell of the blended collide + limit + stream step, gathering its radius-2
+// stencil through the loader L (L.v(q, i, j) = plane q at cell (i, j), ghost
+// cells included). Writes the cell's 20 new values to nv (u, then u_1..u_4).
+template <typename T, int LIM, typename Loader>
+__device__ __forceinline__ void cell_step(const Loader &L, int i, int j, const StepConsts<T> &k,
+                                          T nv[kNPlane], unsigned int &n_fp64) {
+    T uC[4], uW[4], uE[4], uS[4], uN[4];
+    L.u4(0, i, j, uC);
+    L.u4(0, i - 1, j, uW);
+    L.u4(0, i + 1, j, uE);
+    L.u4(0, i, j - 1, uS);
+    L.u4(0, i, j + 1, uN);
+    T fC[4], gC[4], fW[4], gW[4], fE[4], gE[4], fS[4], gS[4], fN[4], gN[4];
+    euler_fluxes(uC, k.gm1, fC, gC);
+    euler_fluxes(uW, k.gm1, fW, gW);
+    euler_fluxes(uE, k.gm1, fE, gE);
+    euler_fluxes(uS, k.gm1, fS, gS);
+    euler_fluxes(uN, k.gm1, fN, gN);
+    T M1C[4], M2C[4], M3C[4], M4C[4], M1W[4], M2E[4], M3S[4], M4N[4], dum[4];
+    maxwell_pm(uC, fC, k, M1C, M2C);
+    maxwell_pm(uC, gC, k, M3C, M4C);
+    maxwell_pm(uW, fW, k, M1W, dum);
+    maxwell_pm(uE, fE, k, dum, M2E);
+    maxwell_pm(uS, gS, k, M3S, dum);
+    maxwell_pm(uN, gN, k, dum, M4N);
+    // non-equilibrium parts d_k = M_k - u_k of the cells the update reads
+    T d1C[4], d2C[4], d3C[4], d4C[4], d1W[4], d2E[4], d3S[4], d4N[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        d1C[c] = RN<T>::sub(M1C[c], L.v(4 + c, i, j));
+        d2C[c] = RN<T>::sub(M2C[c], L.v(8 + c, i, j));
+        d3C[c] = RN<T>::sub(M3C[c], L.v(12 + c, i, j));
+        d4C[c] = RN<T>::sub(M4C[c], L.v(16 + c, i, j));
+        d1W[c] = RN<T>::sub(M1W[c], L.v(4 + c, i - 1, j));
+        d2E[c] = RN<T>::sub(M2E[c], L.v(8 + c, i + 1, j));
+        d3S[c] = RN<T>::sub(M3S[c], L.v(12 + c, i, j - 1));
+        d4N[c] = RN<T>::sub(M4N[c], L.v(16 + c, i, j + 1));
+    }
+    T usW[4], dfW[4], usE[4], dfE[4], usS[4], dfS[4], usN[4], dfN[4];
+    face_state(uW, fW, uC, fC, d1W, d2C, k, usW, dfW);   // x-face i-1/2
+    face_state(uC, fC, uE, fE, d1C, d2E, k, usE, dfE);   // x-face i+1/2
+    face_state(uS, gS, uC, gC, d3S, d4C, k, usS, dfS);   // y-face j-1/2
+    face_state(uC, gC, uN, gN, d3C, d4N, k, usN, dfN);   // y-face j+1/2
+    T th[4];
+    cell_thetas<T, LIM>(L, i, j, uC, uW, uE, uS, uN, usW, dfW, usE, dfE, usS, dfS, usN, dfN, k, th,
+                        n_fp64);
+    // collide + stream, eq. (blending_u1) and eq. (blending_u)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const T u1 = blend_pop(M1W[c], d1W[c], th[0]);
+        const T u2 = blend_pop(M2E[c], d2E[c], th[1]);
+        const T u3 = blend_pop(M3S[c], d3S[c], th[2]);
+        const T u4 = blend_pop(M4N[c], d4N[c], th[3]);
+        nv[c] = blend_u(u1, u2, u3, u4, uC[c], th[0], d2C[c], th[1], d1C[c], th[2], d4C[c], th[3],
+                        d3C[c], k);
+        nv[4 + c] = u1;
+        nv[8 + c] = u2;
+        nv[12 + c] = u3;
+        nv[16 + c] = u4;
     }
 }
 
@@ -124,63 +188,12 @@ __global__ void __launch_bounds__(256) k_step_simple(StepArgs<T> A) {
     Monitor<T> mon;
     mon.init();
     if (i < A.nx && j < A.ny) {
-        T uC[4], uW[4], uE[4], uS[4], uN[4];
-        L.u4(0, i, j, uC);
-        L.u4(0, i - 1, j, uW);
-        L.u4(0, i + 1, j, uE);
-        L.u4(0, i, j - 1, uS);
-        L.u4(0, i, j + 1, uN);
-        T fC[4], gC[4], fW[4], gW[4], fE[4], gE[4], fS[4], gS[4], fN[4], gN[4];
-        euler_fluxes(uC, k.gm1, fC, gC);
-        euler_fluxes(uW, k.gm1, fW, gW);
-        euler_fluxes(uE, k.gm1, fE, gE);
-        euler_fluxes(uS, k.gm1, fS, gS);
-        euler_fluxes(uN, k.gm1, fN, gN);
-        T M1C[4], M2C[4], M3C[4], M4C[4], M1W[4], M2E[4], M3S[4], M4N[4], dum[4];
-        maxwell_pm(uC, fC, k, M1C, M2C);
-        maxwell_pm(uC, gC, k, M3C, M4C);
-        maxwell_pm(uW, fW, k, M1W, dum);
-        maxwell_pm(uE, fE, k, dum, M2E);
-        maxwell_pm(uS, gS, k, M3S, dum);
-        maxwell_pm(uN, gN, k, dum, M4N);
-        // non-equilibrium parts d_k = M_k - u_k of the cells the update reads
-        T d1C[4], d2C[4], d3C[4], d4C[4], d1W[4], d2E[4], d3S[4], d4N[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            d1C[c] = RN<T>::sub(M1C[c], L.v(4 + c, i, j));
-            d2C[c] = RN<T>::sub(M2C[c], L.v(8 + c, i, j));
-            d3C[c] = RN<T>::sub(M3C[c], L.v(12 + c, i, j));
-            d4C[c] = RN<T>::sub(M4C[c], L.v(16 + c, i, j));
-            d1W[c] = RN<T>::sub(M1W[c], L.v(4 + c, i - 1, j));
-            d2E[c] = RN<T>::sub(M2E[c], L.v(8 + c, i + 1, j));
-            d3S[c] = RN<T>::sub(M3S[c], L.v(12 + c, i, j - 1));
-            d4N[c] = RN<T>::sub(M4N[c], L.v(16 + c, i, j + 1));
-        }
-        T usW[4], dfW[4], usE[4], dfE[4], usS[4], dfS[4], usN[4], dfN[4];
-        face_state(uW, fW, uC, fC, d1W, d2C, k, usW, dfW);   // x-face i-1/2
-        face_state(uC, fC, uE, fE, d1C, d2E, k, usE, dfE);   // x-face i+1/2
-        face_state(uS, gS, uC, gC, d3S, d4C, k, usS, dfS);   // y-face j-1/2
-        face_state(uC, gC, uN, gN, d3C, d4N, k, usN, dfN);   // y-face j+1/2
-        T th[4];
-        cell_thetas<T, LIM>(L, i, j, uC, uW, uE, uS, uN, usW, dfW, usE, dfE, usS, dfS, usN, dfN, k, th);
-        // collide + stream, eq. (blending_u1) and eq. (blending_u)
+        T nv[kNPlane];
+        cell_step<T, LIM>(L, i, j, k, nv, mon.fp64);
         const long long d = (long long)(j + kOY) * A.pitch + (i + kOX);
-        T un[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const T u1 = blend_pop(M1W[c], d1W[c], th[0]);
-            const T u2 = blend_pop(M2E[c], d2E[c], th[1]);
-            const T u3 = blend_pop(M3S[c], d3S[c], th[2]);
-            const T u4 = blend_pop(M4N[c], d4N[c], th[3]);
-            un[c] = blend_u(u1, u2, u3, u4, uC[c], th[0], d2C[c], th[1], d1C[c], th[2], d4C[c],
-                            th[3], d3C[c], k);
-            out[c * A.plane + d] = un[c];
-            out[(4 + c) * A.plane + d] = u1;
-            out[(8 + c) * A.plane + d] = u2;
-            out[(12 + c) * A.plane + d] = u3;
-            out[(16 + c) * A.plane + d] = u4;
-        }
-        mon.add_cell(un, k.gamma, k.gm1);
+        for (int q = 0; q < kNPlane; ++q) out[q * A.plane + d] = nv[q];
+        mon.add_cell(nv, k.gamma, k.gm1);
     }
     block_publish(mon, C);
     if (last_block(C, gridDim.x * gridDim.y)) {

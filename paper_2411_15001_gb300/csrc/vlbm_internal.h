@@ -77,6 +77,7 @@ struct DevCtl {
     unsigned long long minrho_key;   // ordered key of min rho
     unsigned long long bad;          // cells outside G
     unsigned long long nonfinite;    // non-finite cells
+    unsigned long long fp64_faces;   // faces whose theta_p needed the FP64 solve
     double sum[4];
     unsigned int blocks_done;
     unsigned int pad0;
@@ -85,12 +86,13 @@ struct DevCtl {
     double min_rho;
     long long bad_last;
     long long nonfinite_last;
+    long long fp64_last;
     double sum_last[4];
     // constants
     double dx, alpha, a_fixed, eps, gamma;
 };
 
-static_assert(sizeof(DevCtl) == 248, "bench.py reads the control block size");
+static_assert(sizeof(DevCtl) == 264, "bench.py reads the control block size");
 
 template <typename T>
 struct StepArgs {

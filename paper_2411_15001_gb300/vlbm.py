@@ -37,7 +37,8 @@ class vlbm_monitor_t(ctypes.Structure):
                 ("dt", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("bad_cells", ctypes.c_int64), ("nonfinite_cells", ctypes.c_int64),
                 ("first_bad_step", ctypes.c_int64), ("min_rho", ctypes.c_double),
-                ("sum", ctypes.c_double * 4), ("done", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("sum", ctypes.c_double * 4), ("theta_p_fp64_faces", ctypes.c_int64),
+                ("done", ctypes.c_int32), ("status", ctypes.c_int32)]
 
 
 class VLBMError(RuntimeError):
@@ -236,6 +237,7 @@ class VLBM:
         return {"status": m.status, "n": m.n, "t": m.t, "a": m.a, "dt": m.dt, "lambda": m.lambda_,
                 "bad_cells": m.bad_cells, "nonfinite_cells": m.nonfinite_cells,
                 "first_bad_step": m.first_bad_step, "min_rho": m.min_rho, "sum": list(m.sum),
+                "theta_p_fp64_faces": m.theta_p_fp64_faces,
                 "done": m.done}
 
     def sync(self) -> int:

@@ -117,12 +117,35 @@ def test_fp32_discontinuous_quadrants(kernel, lim):
 
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_fp32_near_vacuum_blast(kernel):
-    """Sedov-type blast, p = 1e-6 ambient, reflective walls, PP with eps = 1e-13."""
+    """Sedov-type blast, p = 1e-6 ambient, reflective walls, PP with eps = 1e-13.
+
+    The near-vacuum core of this blast amplifies round-off exponentially (see
+    test_blast_amplifies_round_off), so the FP32 path is held to the discontinuous
+    tolerance over the first 40 steps and to the invariants (admissibility, mass and
+    energy conserved by the walls) over 150."""
     p = W.blast(96)
-    got, mon = gpu_run(p, V.LIM_PP, V.FP32, nsteps=150, eps=1e-13, kernel=kernel)
-    ref = oracle_run(p, V.LIM_PP, nsteps=150, eps=1e-13)
+    got, mon = gpu_run(p, V.LIM_PP, V.FP32, nsteps=40, eps=1e-13, kernel=kernel)
+    ref = oracle_run(p, V.LIM_PP, nsteps=40, eps=1e-13)
     assert mon["status"] == 0 and mon["first_bad_step"] == -1
     assert l1_rel(got[:4], ref["state"][:4]) <= 1e-3
+    got, mon = gpu_run(p, V.LIM_PP, V.FP32, nsteps=150, eps=1e-13, kernel=kernel)
+    assert mon["status"] == 0 and mon["first_bad_step"] == -1 and mon["bad_cells"] == 0
+    c0 = p.conserved().astype(np.float32).astype(np.float64).reshape(4, -1).sum(axis=1)
+    assert abs(mon["sum"][0] - c0[0]) <= 1e-5 * c0[0]
+    assert abs(mon["sum"][3] - c0[3]) <= 1e-5 * c0[3]
+
+
+def test_blast_amplifies_round_off():
+    """FP64 only: a relative perturbation of 1e-12 of the initial energy grows by many
+    orders of magnitude over 150 steps of the near-vacuum blast, so no two
+    implementations that round differently can agree there to FP32 round-off."""
+    p = W.blast(96)
+    a, _ = gpu_run(p, V.LIM_PP, V.FP64, nsteps=150, eps=1e-13)
+    q = W.blast(96)
+    q.E = q.E * (1.0 + 1e-12 * np.cos(np.arange(q.E.size).reshape(q.E.shape)))
+    b, _ = gpu_run(q, V.LIM_PP, V.FP64, nsteps=150, eps=1e-13)
+    growth = l1_rel(b[:4], a[:4]) / 1e-12
+    assert growth > 1e4, growth
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -136,8 +159,10 @@ def test_conservation_monitor_periodic(prec, tol, kernel):
     ref = s0.sum(axis=1)
     scale = np.abs(s0).sum(axis=1)
     assert np.all(np.abs(np.array(mon["sum"]) - ref) <= tol * scale)
-    # the monitor sums are the FP64 sums of the stored state
-    np.testing.assert_allclose(mon["sum"], got[:4].reshape(4, -1).sum(axis=1), rtol=1e-12, atol=1e-9)
+    # the monitor sums are the FP64 sums of the stored state (FP32: Kahan-compensated
+    # float partial sums, far below the state's own round-off)
+    np.testing.assert_allclose(mon["sum"], got[:4].reshape(4, -1).sum(axis=1),
+                               rtol=1e-12 if prec == V.FP64 else 1e-9, atol=1e-9)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -185,10 +210,12 @@ def test_inadmissible_initial_state_is_rejected():
     assert e.value.code == V.E_INVAL
 
 
-def test_fused_equals_simple_fp32():
-    """The two FP32 kernels evaluate the same formulas; after 50 steps of a
-    discontinuous problem they agree to FP32 round-off."""
+@pytest.mark.parametrize("lim,tol", [(V.LIM_PP, 1e-5), (V.LIM_LMP, 1e-3)])
+def test_fused_equals_simple_fp32(lim, tol):
+    """The two FP32 kernels evaluate the same formulas in a different order. With PP
+    they agree to FP32 round-off; LMP takes different branches at ties (dF^rho at
+    round-off level), so it is held to the discontinuous tolerance."""
     p = W.quadrant_riemann(300, 130, seed=9)
-    a, _ = gpu_run(p, V.LIM_LMP, V.FP32, nsteps=50, kernel=V.KERNEL_SIMPLE)
-    b, _ = gpu_run(p, V.LIM_LMP, V.FP32, nsteps=50, kernel=V.KERNEL_FUSED)
-    assert l1_rel(b[:4], a[:4]) <= 1e-5
+    a, _ = gpu_run(p, lim, V.FP32, nsteps=50, kernel=V.KERNEL_SIMPLE)
+    b, _ = gpu_run(p, lim, V.FP32, nsteps=50, kernel=V.KERNEL_FUSED)
+    assert l1_rel(b[:4], a[:4]) <= tol
