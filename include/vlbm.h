@@ -192,6 +192,46 @@ VLBM_API int vlbm_load(vlbm_state *s, const void *d_src);
 VLBM_API int vlbm_profile(vlbm_state *s, int32_t enable);
 VLBM_API int vlbm_profile_read(vlbm_state *s, double *kernel_ms, int64_t *launches);
 
+/* ---------------------------------------------------------- no workspace */
+
+/* Result of vlbm_step_noalloc, in host memory. */
+typedef struct {
+    double lambda;               /* max |v| + sqrt(gamma p / rho) of the new state */
+    double a_next;               /* 2 lambda / (1 - alpha): the kinetic speed for a following step */
+    double min_rho;              /* min density of the new state */
+    double sum[4];               /* FP64 sums of rho, m1, m2, E of the new state */
+    int64_t bad_cells;           /* cells of the new state outside G */
+    int64_t nonfinite_cells;
+    int64_t theta_p_fp64_faces;
+} vlbm_step_result;
+
+/* One time step that allocates nothing and needs no workspace. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device
+ * memory at all -- a plugin whose host application's memory pool already owns
+ * the device, a real-time loop that may not pay the implicit device-wide
+ * synchronisation of cudaMalloc, a sandbox without access to the allocator.
+ * Such a caller holds its state and passes it in and out.
+ *   d_in, d_out: caller-owned device buffers of 20 compact planes each (u, then
+ *     u_1..u_4, 4 planes each, plane q at q * nx * ny, cell (i, j) at j * nx + i)
+ *     in the given precision; they must not overlap. Boundaries are applied on
+ *     the fly from grid->bc.
+ *   a: the kinetic speed of this step (Delta t = dx / a); result->a_next is the
+ *     dynamic speed for the next one.
+ * The only scratch, one reduction record per CTA of 32 x 8 cells, lives in a
+ * fixed array of about 0.5 MB inside the library that every GPU loading it keeps
+ * until the process exits; grids of more than 8192 such CTAs (about two million
+ * cells, e.g. 2048 x 1024) are rejected with VLBM_E_INVAL. Every call shares that
+ * array and overwrites it, so calls whose work overlaps on the GPU (other
+ * streams, other host threads on the same device) race; serialise them. The
+ * first call on a device looks up the array's device address once, with that
+ * device current; make that first call before any stream capture. Runs on
+ * `stream` (a cudaStream_t) on the current device and synchronises it to fill
+ * *result. Returns VLBM_OK, VLBM_E_POSITIVITY / VLBM_E_NONFINITE for a new state
+ * outside G, VLBM_E_INVAL or VLBM_E_CUDA. Calls no cudaMalloc or cudaFree. */
+VLBM_API int vlbm_step_noalloc(const vlbm_grid *grid, double gamma, double a, int32_t limiter,
+                               int32_t precision, const vlbm_opts *opts, const void *d_in, void *d_out,
+                               vlbm_step_result *result, void *stream);
+
 /* Free the host object. Enqueues nothing and does not touch the workspace. */
 VLBM_API void vlbm_destroy(vlbm_state *s);
 

@@ -41,6 +41,12 @@ class vlbm_monitor_t(ctypes.Structure):
                 ("done", ctypes.c_int32), ("status", ctypes.c_int32)]
 
 
+class vlbm_step_result(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("a_next", ctypes.c_double), ("min_rho", ctypes.c_double),
+                ("sum", ctypes.c_double * 4), ("bad_cells", ctypes.c_int64),
+                ("nonfinite_cells", ctypes.c_int64), ("theta_p_fp64_faces", ctypes.c_int64)]
+
+
 class VLBMError(RuntimeError):
     def __init__(self, code: int, detail: str = ""):
         self.code = code
@@ -70,6 +76,9 @@ _SIGS = {
     "vlbm_load": (ctypes.c_int, [_P, _P]),
     "vlbm_profile": (ctypes.c_int, [_P, _I32]),
     "vlbm_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "vlbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(vlbm_grid), _D, _D, _I32, _I32,
+                                         ctypes.POINTER(vlbm_opts), _P, _P,
+                                         ctypes.POINTER(vlbm_step_result), _P]),
     "vlbm_destroy": (None, [_P]),
     "vlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vlbm_last_error_detail": (ctypes.c_int, [_P, ctypes.c_char_p, _SZ]),
@@ -149,6 +158,15 @@ def vlbm_profile_read(s):
     ms, n = _D(), _I64()
     rc = _lib.vlbm_profile_read(s, ctypes.byref(ms), ctypes.byref(n))
     return rc, ms.value, n.value
+
+
+def vlbm_step_noalloc(grid, gamma, a, limiter, precision, opts, d_in, d_out, stream):
+    """One workspace-free step (see include/vlbm.h); returns (rc, vlbm_step_result)."""
+    r = vlbm_step_result()
+    rc = _lib.vlbm_step_noalloc(ctypes.byref(grid), gamma, a, limiter, precision,
+                                ctypes.byref(opts) if opts is not None else None, d_in, d_out,
+                                ctypes.byref(r), stream)
+    return rc, r
 
 
 def vlbm_destroy(s) -> None:
