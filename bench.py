@@ -286,14 +286,131 @@ def run_ours(args):
                            "steps_total": args.warmup + args.steps,
                            "positivity_violations": mon["bad_cells"] + mon["nonfinite_cells"],
                            "first_bad_step": mon["first_bad_step"], "status": mon["status"]},
-                "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 2 * args.steps,
+                "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof}
+        if not args.no_batched:
+            line["batched"] = bench_batched(dev)
+        if not args.no_adjoint:
+            line["adjoint"] = bench_adjoint(dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.n)
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_batched(dev, steps: int = 500, count: int = 256):
+    """256 seeded quadrant problems of uneven sides (multiples of 64 up to 1024), FP32 PP:
+    one launch per step over all grids (graph-replayed, autotuned decomposition) against
+    the same problems stepped one grid at a time with one launch per grid and step."""
+    import torch
+
+    from paper_2411_15001_gb300 import vlbm as V
+    from paper_2411_15001_gb300 import workloads as W
+
+    probs = W.batch_instances(count, seed=1)
+    cells = sum(p.nx * p.ny for p in probs)
+    conss = [torch.tensor(p.conserved(), dtype=torch.float32, device=dev) for p in probs]
+
+    def load(setter):
+        for i, c in enumerate(conss):
+            setter(i, c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+
+    b = V.VLBMBatch([(p.nx, p.ny, p.dx, p.bc) for p in probs], limiter=V.LIM_PP, precision=V.FP32,
+                    eps=EPS, device=dev)
+    load(b.set_conserved)
+    tuning = b.autotune(trial_steps=3)
+    load(b.set_conserved)                    # time from n = 0 like the sequential arm
+    b.step(3)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize(dev)
+    ms_b = e0.elapsed_time(e1)
+    status = [b.monitors(i)["status"] for i in range(count)]
+    b.close()
+    del b
+    solvers = [V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, gamma=p.gamma, limiter=V.LIM_PP, precision=V.FP32,
+                      eps=EPS, device=dev) for p in probs]
+    load(lambda i, r, m, e: solvers[i].set_conserved(r, m, e))
+    for s in solvers:
+        s.step(3)
+    torch.cuda.synchronize(dev)
+    stream = solvers[0].stream
+    e0.record(stream)
+    for s in solvers:
+        s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_s = e0.elapsed_time(e1)
+    for s in solvers:
+        s.close()
+    return {"workload": f"{count} quadrant Riemann problems, sides in {{64..1024}} step 64 (seed 1), "
+                        f"FP32 PP eps=1e-13, zero-gradient walls, {steps} steps each",
+            "cells": cells, "steps": steps,
+            "batched_mlups": cells * steps / (ms_b / 1e3) / 1e6,
+            "sequential_mlups": cells * steps / (ms_s / 1e3) / 1e6,
+            "ratio": ms_s / ms_b, "batched_ms_per_step": ms_b / steps,
+            "sequential_ms_per_step": ms_s / steps, "tuning": tuning,
+            "statuses_nonzero": sum(1 for x in status if x)}
+
+
+def bench_adjoint(dev, n: int = 512, steps: int = 500, every: int = 50):
+    """Gradient of an L2 loss of u^N with respect to u_0 for the 512^2 periodic vortex with
+    8 density bumps, FP32, fixed a: forward step vs rollout (checkpoints) vs adjoint sweep
+    (recomputation + adjoint kernels), per step."""
+    import torch
+
+    from paper_2411_15001_gb300 import vlbm as V
+    from paper_2411_15001_gb300 import workloads as W
+
+    p = W.vortex_with_bumps(n)
+    u0 = torch.tensor(p.conserved(), dtype=torch.float32, device=dev)
+    probe = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, limiter=V.LIM_PP, precision=V.FP32, device=dev)
+    probe.set_conserved(u0[0].contiguous(), u0[1:3].contiguous(), u0[3].contiguous())
+    lam = 1.05 * probe.monitors()["lambda"]
+    probe.close()
+    s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, lam=lam, limiter=V.LIM_PP, precision=V.FP32, device=dev)
+    scratch = s.adjoint_scratch(steps, every)
+    t_end = steps * p.dx / (4.0 * lam)
+    target = torch.tensor(W.isentropic_vortex(n, t=t_end).conserved(), dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+
+    def fwd():
+        s.set_conserved(u0[0].contiguous(), u0[1:3].contiguous(), u0[3].contiguous())
+
+    fwd()
+    s.step(5)
+    torch.cuda.synchronize(dev)
+    fwd()
+    ev[0].record(s.stream)
+    s.step(steps)
+    ev[1].record(s.stream)
+    fwd()
+    ev[2].record(s.stream)
+    s.rollout(steps, every, scratch)
+    ev[3].record(s.stream)
+    rho, mom, E = s.moments()
+    uN = torch.cat([rho[None], mom, E[None]])
+    dL = (uN - target).contiguous()
+    ev[4].record(s.stream)
+    g = s.adjoint(dL, steps, every, scratch)
+    ev[5].record(s.stream)
+    torch.cuda.synchronize(dev)
+    t_f = ev[0].elapsed_time(ev[1]) / steps
+    t_r = ev[2].elapsed_time(ev[3]) / steps
+    t_a = ev[4].elapsed_time(ev[5]) / steps
+    finite = bool(torch.isfinite(g).all())
+    s.close()
+    return {"workload": f"{n}x{n} periodic isentropic vortex + 8 Gaussian density bumps (seed 2), FP32, "
+                        f"PP, fixed a = 4 (1.05 lambda_0), {steps} steps, checkpoints every {every}, "
+                        "L2 loss against the exact vortex at t_N",
+            "forward_ms_per_step": t_f, "rollout_ms_per_step": t_r, "adjoint_ms_per_step": t_a,
+            "adjoint_over_forward": t_a / t_f, "gradient_over_forward": (t_r + t_a) / t_f,
+            "scratch_bytes": int(scratch.numel()), "gradient_finite": finite}
 
 
 def main():
@@ -305,6 +422,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_SIDE, help="grid side (default 4096)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -192,6 +192,109 @@ VLBM_API int vlbm_load(vlbm_state *s, const void *d_src);
 VLBM_API int vlbm_profile(vlbm_state *s, int32_t enable);
 VLBM_API int vlbm_profile_read(vlbm_state *s, double *kernel_ms, int64_t *launches);
 
+/* ---------------------------------------------------------------- batches */
+
+/* Many independent grids of uneven sizes (one gamma, limiter and precision)
+ * advanced together: every time step is one launch of the row-marching kernel
+ * over the work items (grid, strip of 120 columns, chunk of rows) of all grids,
+ * persistent CTAs taking items from a shared counter; steps are replayed from
+ * a CUDA graph of 64 launches. Each grid keeps its own dynamic kinetic speed
+ * a^n = 4 lambda^n (Sec. 4 preamble), time, monitors and ghost frame. */
+typedef struct vlbm_batch vlbm_batch;
+
+#define VLBM_ORDER_LPT 0     /* work items of the grids with most cells first */
+#define VLBM_ORDER_INDEX 1   /* work items in grid index order */
+
+/* Work decomposition: rows per work item, CTAs per SM, item order; items and
+ * CTAs of the resulting launch (outputs). */
+typedef struct {
+    int32_t chunk, ctas_per_sm, order;
+    int32_t items, ctas;
+} vlbm_batch_tuning;
+
+/* Bytes of device workspace for n grids (0 if an argument is invalid). */
+VLBM_API size_t vlbm_batch_workspace_bytes(int32_t n, const vlbm_grid *grids, int32_t precision);
+
+/* Create a batch over caller-owned d_workspace (>= the size above, 256-byte
+ * aligned). Enqueues nothing. Errors as vlbm_init. */
+VLBM_API int vlbm_batch_init(int32_t n, const vlbm_grid *grids, double gamma, int32_t limiter,
+                             int32_t precision, const vlbm_opts *opts, void *d_workspace,
+                             size_t workspace_bytes, void *stream, vlbm_batch **out);
+
+/* Initial conserved planes of grid i (layout as vlbm_set_conserved), populations
+ * at equilibrium (Sec. 4 preamble). Synchronises; VLBM_E_INVAL for a state
+ * outside G. Every grid must be set before the first vlbm_batch_step. */
+VLBM_API int vlbm_batch_set_conserved(vlbm_batch *b, int32_t i, const void *d_rho, const void *d_mom,
+                                      const void *d_E);
+
+/* Advance every grid by nsteps time steps. Asynchronous. */
+VLBM_API int vlbm_batch_step(vlbm_batch *b, int64_t nsteps);
+
+/* Conserved planes of grid i into caller-owned device memory (NULL skips). */
+VLBM_API int vlbm_batch_moments(const vlbm_batch *b, int32_t i, void *d_rho, void *d_mom, void *d_E);
+
+/* Checkpoint of grid i, format of vlbm_save. Asynchronous. */
+VLBM_API int vlbm_batch_save(const vlbm_batch *b, int32_t i, void *d_dst);
+
+/* Monitors of grid i (synchronises); returns the grid's sticky status. */
+VLBM_API int vlbm_batch_monitors(vlbm_batch *b, int32_t i, vlbm_monitor_t *out);
+
+/* Current work decomposition, or set one explicitly. */
+VLBM_API int vlbm_batch_get_tuning(const vlbm_batch *b, vlbm_batch_tuning *t);
+VLBM_API int vlbm_batch_set_tuning(vlbm_batch *b, const vlbm_batch_tuning *t);
+
+/* Autotuner: times every decomposition (chunk 16/32/64 rows x 1..max CTAs per SM
+ * x both item orders) over trial_steps steps each with CUDA events, keeps the
+ * fastest and returns it with its time per step. The decomposition does not
+ * change any cell's arithmetic, so the trial steps are real steps: the grids
+ * advance by (1 + trial_steps) x candidates steps. Synchronises. */
+VLBM_API int vlbm_batch_autotune(vlbm_batch *b, int32_t trial_steps, vlbm_batch_tuning *best,
+                                 double *best_ms_per_step);
+
+VLBM_API void vlbm_batch_destroy(vlbm_batch *b);
+
+/* Last error message of a batch call: that batch's, or with b = NULL the calling
+ * thread's last failed call that had no batch object (vlbm_batch_init). */
+VLBM_API const char *vlbm_batch_last_error(const vlbm_batch *b);
+
+/* ---------------------------------------------------------------- adjoint */
+
+/* Gradient of a loss L(u^N) of the final conserved fields with respect to the
+ * initial conserved fields u_0 (rho, m1, m2, E), through N steps of the blended
+ * scheme (Sec. 3.2, eq. blending_u1 / blending_u, theta of Sec. 3.2-3.4) and the
+ * equilibrium initialisation u_k^0 = M_k(u_0) (Sec. 4 preamble). The transpose
+ * of each step is differentiated piecewise: theta on the branch the forward step
+ * took (1, the density bound, the internal-energy bound, or the clamp at 0); the
+ * kinetic speeds a^n are held as the forward run produced them (the fixed speed
+ * of a state made with lambda > 0, else the recorded dynamic a^n, whose own
+ * dependence on u through max lambda is not differentiated). Covered: the
+ * first-order, unlimited and PP schemes on fully periodic grids; other limiters
+ * or boundaries return VLBM_E_UNSUPPORTED.
+ *
+ * Memory: checkpoints of the state every ckpt_every steps, a segment buffer of
+ * ckpt_every + 1 states for the recomputation, and two cotangent buffers, all in
+ * caller-owned d_scratch of vlbm_adjoint_scratch_bytes (256-byte aligned). Cost:
+ * one forward run, one recomputation of every step but the last of each
+ * segment, and one adjoint kernel per step. */
+VLBM_API size_t vlbm_adjoint_scratch_bytes(const vlbm_state *s, int64_t nsteps, int32_t ckpt_every);
+
+/* Forward run with checkpoints: from the state vlbm_set_conserved left (n = 0),
+ * advance nsteps steps with the state's kernel, storing a checkpoint before
+ * every ckpt_every-th step into d_scratch. Afterwards the state holds u^N as
+ * after vlbm_step. Asynchronous. */
+VLBM_API int vlbm_rollout(vlbm_state *s, int64_t nsteps, int32_t ckpt_every, void *d_scratch,
+                          size_t scratch_bytes);
+
+/* Reverse sweep. d_dLduN: dL/du^N as 4 planes (rho, m1, m2, E) back to back;
+ * d_dLdu0 (output): dL/du_0 in the same layout; both in the state's precision.
+ * With d_u0 (4 planes, same layout) the call first runs vlbm_set_conserved(u_0)
+ * and vlbm_rollout itself; with d_u0 = NULL it uses the checkpoints of the
+ * preceding vlbm_rollout, which must have had the same nsteps, ckpt_every and
+ * d_scratch (VLBM_E_INVAL otherwise). The state is left at u^N. Asynchronous
+ * (the d_u0 form synchronises once, in vlbm_set_conserved). */
+VLBM_API int vlbm_adjoint(vlbm_state *s, const void *d_u0, int64_t nsteps, int32_t ckpt_every,
+                          const void *d_dLduN, void *d_dLdu0, void *d_scratch, size_t scratch_bytes);
+
 /* ---------------------------------------------------------- no workspace */
 
 /* Result of vlbm_step_noalloc, in host memory. */

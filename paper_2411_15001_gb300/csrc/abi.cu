@@ -8,35 +8,18 @@
 #include <new>
 #include <vector>
 
-#include "../../include/vlbm.h"
-#include "vlbm_internal.h"
+#include "state.h"
 
 using namespace vlbm;
+using namespace vlbm::api;
 
-struct vlbm_state {
-    vlbm_grid grid;
-    int precision, limiter, kernel;
-    double gamma, lambda, alpha, eps, a_fixed;
-    Layout L;
-    void *ws;
-    cudaStream_t stream;
-    DevCtl *ctl;
-    int device;
-    CUtensorMap tmap;   // 3D view [40 planes][rows][pitch] of both state buffers
-    bool have_tmap;
-    int strips, fused_grid;
-    bool profiling;
-    std::vector<cudaEvent_t> ev;   // event pairs of timed launches
-    size_t ev_used;
-    bool loaded;        // set_conserved or load has run
-    bool tend_active;   // a final time is armed on the device
-    char err[256];
-};
+
 
 static thread_local char g_err[256];
 
-static int fail(vlbm_state *s, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
-static int fail(vlbm_state *s, int code, const char *fmt, ...) {
+namespace vlbm {
+namespace api {
+int fail(vlbm_state *s, int code, const char *fmt, ...) {
     char *dst = s ? s->err : g_err;
     va_list ap;
     va_start(ap, fmt);
@@ -45,9 +28,11 @@ static int fail(vlbm_state *s, int code, const char *fmt, ...) {
     return code;
 }
 
-static int cuda_fail(vlbm_state *s, cudaError_t e, const char *what) {
+int cuda_fail(vlbm_state *s, cudaError_t e, const char *what) {
     return fail(s, VLBM_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+}  // namespace api
+}  // namespace vlbm
 
 namespace vlbm {
 Layout make_layout(int nx, int ny, int elem) {
@@ -55,12 +40,16 @@ Layout make_layout(int nx, int ny, int elem) {
     L.nx = nx;
     L.ny = ny;
     L.elem = elem;
-    L.pitch = ((nx + 2 * kOX + 31) / 32) * 32;
+    L.pitch = ((nx + kOX + 2 + 31) / 32) * 32;
     L.rows = ny + 2 * kOY;
     L.plane = (((long long)L.pitch * L.rows + 63) / 64) * 64;
     L.buf_bytes = (size_t)L.plane * kNPlane * elem;
     L.ctl_offset = 2 * L.buf_bytes;
-    L.total = L.ctl_offset + ((sizeof(DevCtl) + 255) / 256) * 256;
+    L.desc_offset = L.ctl_offset + ((sizeof(DevCtl) + 255) / 256) * 256;
+    // descriptor block: InstDesc (512 B), BatchCtl (256 B), item table at the smallest chunk
+    const size_t strips = (nx + kFusedOut - 1) / kFusedOut;
+    const size_t items = strips * ((ny + kFusedMinChunk - 1) / kFusedMinChunk);
+    L.total = L.desc_offset + 512 + 256 + ((items * sizeof(int) + 255) / 256) * 256;
     return L;
 }
 }  // namespace vlbm
@@ -79,45 +68,12 @@ static int elem_of(int32_t precision) {
     return precision == VLBM_FP64 ? 8 : precision == VLBM_FP32 ? 4 : 0;
 }
 
-// Keep the caller's current device; run the call on the state's device.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-template <typename T>
-static StepArgs<T> args_of(const vlbm_state *s) {
-    StepArgs<T> A;
-    A.buf0 = (T *)s->ws;
-    A.buf1 = (T *)((char *)s->ws + s->L.buf_bytes);
-    A.plane = s->L.plane;
-    A.pitch = s->L.pitch;
-    A.nx = s->grid.nx;
-    A.ny = s->grid.ny;
-    for (int k = 0; k < 4; ++k) A.bc[k] = s->grid.bc[k];
-    A.limiter = s->limiter;
-    A.gamma = s->gamma;
-    A.alpha = s->alpha;
-    A.eps = s->eps;
-    A.ctl = s->ctl;
-    return A;
-}
-
-static bool use_fused(const vlbm_state *s) {
-    return s->have_tmap && s->kernel != VLBM_KERNEL_SIMPLE;
-}
 
 static cudaError_t step_kernel_only(vlbm_state *s) {
     if (use_fused(s)) {
         if (s->precision == VLBM_FP64)
-            return launch_step_fused<double>(args_of<double>(s), s->tmap, s->strips, s->fused_grid, s->stream);
-        return launch_step_fused<float>(args_of<float>(s), s->tmap, s->strips, s->fused_grid, s->stream);
+            return launch_step_fused<double>(batch_args_of<double>(s), s->limiter, s->fused_grid, s->stream);
+        return launch_step_fused<float>(batch_args_of<float>(s), s->limiter, s->fused_grid, s->stream);
     }
     if (s->precision == VLBM_FP64) return launch_step_simple<double>(args_of<double>(s), s->stream);
     return launch_step_simple<float>(args_of<float>(s), s->stream);
@@ -128,9 +84,46 @@ static cudaError_t ghosts(vlbm_state *s) {
     return launch_ghosts<float>(args_of<float>(s), s->stream);
 }
 
+// Descriptor of this grid for the row-marching kernel, built on the host.
+template <typename T>
+static void build_desc(vlbm_state *s) {
+    InstDesc<T> d;
+    memset(&d, 0, sizeof d);
+    d.tmap = s->tmap;
+    d.buf0 = (T *)s->ws;
+    d.buf1 = (T *)((char *)s->ws + s->L.buf_bytes);
+    d.plane = s->L.plane;
+    d.pitch = s->L.pitch;
+    d.nx = s->grid.nx;
+    d.ny = s->grid.ny;
+    for (int q = 0; q < 4; ++q) d.bc[q] = s->grid.bc[q];
+    d.strips = s->strips;
+    d.chunk = s->chunk;
+    d.item0 = 0;
+    d.nitems = s->nitems;
+    d.ctl = s->ctl;
+    static_assert(sizeof(InstDesc<T>) <= 512, "descriptor block");
+    s->desc_host.assign((unsigned char *)&d, (unsigned char *)&d + sizeof d);
+    s->items_host.assign(s->nitems, 0);
+}
+
+// Upload the descriptor, the item table and a zero work counter (stream-ordered;
+// the host copies live in the state).
+static cudaError_t upload_desc(vlbm_state *s) {
+    if (!use_fused(s)) return cudaSuccess;
+    char *base = (char *)s->ws + s->L.desc_offset;
+    cudaError_t e = cudaMemcpyAsync(base, s->desc_host.data(), s->desc_host.size(), cudaMemcpyHostToDevice,
+                                    s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + 512, 0, sizeof(BatchCtl), s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + 768, s->items_host.data(), s->items_host.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, s->stream);
+    return e;
+}
+
 // One time step: the collide + limit + stream kernel, then the ghost frame of
 // the new state. With profiling on, an event pair brackets the step kernel.
-static cudaError_t step_once(vlbm_state *s) {
+cudaError_t vlbm::api::step_once(vlbm_state *s) {
     cudaError_t r;
     if (s->profiling) {
         if (s->ev_used + 2 > s->ev.size()) {
@@ -149,17 +142,18 @@ static cudaError_t step_once(vlbm_state *s) {
         r = step_kernel_only(s);
     }
     if (r != cudaSuccess) return r;
-    return ghosts(s);
+    return use_fused(s) ? cudaSuccess : ghosts(s);   // the fused kernel writes the ghost frame
 }
 
-// TMA descriptor of the two state buffers seen as one 3D tensor
+namespace vlbm {
+// TMA descriptor of the two state buffers of a grid seen as one 3D tensor
 // [40 planes][ny + 4 rows][pitch columns]; a box is 128 columns x 1 row x 20 planes.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                   CUtensorMapFloatOOBfill);
 
-static bool make_tmap(vlbm_state *s) {
+bool encode_state_tmap(CUtensorMap *out, void *base, const Layout &L) {
     static EncodeTiledFn encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -171,18 +165,21 @@ static bool make_tmap(vlbm_state *s) {
         }
         encode = (EncodeTiledFn)fn;
     }
-    const cuuint64_t dims[3] = {(cuuint64_t)s->L.pitch, (cuuint64_t)s->L.rows, (cuuint64_t)(2 * kNPlane)};
-    const cuuint64_t strides[2] = {(cuuint64_t)s->L.pitch * s->L.elem, (cuuint64_t)s->L.plane * s->L.elem};
+    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)(2 * kNPlane)};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * L.elem, (cuuint64_t)L.plane * L.elem};
     const cuuint32_t box[3] = {(cuuint32_t)kFusedBox, 1u, (cuuint32_t)kNPlane};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult r = encode(&s->tmap, s->L.elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                        3, s->ws, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    CUresult r = encode(out, L.elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                        base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
+}  // namespace vlbm
 
-static int read_ctl(vlbm_state *s, DevCtl *h) {
+static bool make_tmap(vlbm_state *s) { return encode_state_tmap(&s->tmap, s->ws, s->L); }
+
+int vlbm::api::read_ctl(vlbm_state *s, DevCtl *h) {
     cudaError_t e = cudaMemcpyAsync(h, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "reading the device control block");
@@ -258,10 +255,16 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
             const int per_sm = precision == VLBM_FP64 ? fused_occupancy<double>(limiter)
                                                       : fused_occupancy<float>(limiter);
-            long long rows = (long long)s->strips * grid->ny;
-            long long want = (long long)per_sm * (sms > 0 ? sms : 1);
-            long long cap = rows / 8 > 0 ? rows / 8 : 1;
-            s->fused_grid = (int)(want < cap ? want : cap);
+            const long long ctas = (long long)per_sm * (sms > 0 ? sms : 1);
+            const long long rows = (long long)s->strips * grid->ny;
+            long long chunk = rows / (2 * ctas);
+            if (chunk < kFusedMinChunk) chunk = kFusedMinChunk;
+            if (chunk > kFusedMaxChunk) chunk = kFusedMaxChunk;
+            s->chunk = (int)chunk;
+            s->nitems = s->strips * ((grid->ny + s->chunk - 1) / s->chunk);
+            s->fused_grid = (int)(ctas < s->nitems ? ctas : s->nitems);
+            if (precision == VLBM_FP64) build_desc<double>(s);
+            else build_desc<float>(s);
         }
         if (o.kernel == VLBM_KERNEL_FUSED && !s->have_tmap) {
             delete s;
@@ -275,8 +278,16 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
 int vlbm_set_conserved(vlbm_state *s, const void *d_rho, const void *d_mom, const void *d_E) {
     if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
     if (!d_rho || !d_mom || !d_E) return fail(s, VLBM_E_INVAL, "input plane pointer is NULL");
+    return vlbm::api::set_conserved(s, d_rho, d_mom, d_E);
+}
+
+}  // extern "C"
+
+int vlbm::api::set_conserved(vlbm_state *s, const void *d_rho, const void *d_mom, const void *d_E) {
     DeviceGuard g(s->device);
+    s->roll_scratch = nullptr;
     cudaError_t e = launch_ctl_reset(s->ctl, s->grid.dx, s->alpha, s->a_fixed, s->eps, s->gamma, s->stream);
+    if (e == cudaSuccess) e = upload_desc(s);
     if (e == cudaSuccess) {
         if (s->precision == VLBM_FP64)
             e = launch_init<double>(args_of<double>(s), (const double *)d_rho, (const double *)d_mom,
@@ -291,10 +302,13 @@ int vlbm_set_conserved(vlbm_state *s, const void *d_rho, const void *d_mom, cons
     if (rc) return rc;
     s->loaded = true;
     s->tend_active = false;
+    s->at_init = true;
     if (h.invalid_init)
         return fail(s, VLBM_E_INVAL, "initial state has cells outside G or not finite");
     return VLBM_OK;
 }
+
+extern "C" {
 
 int vlbm_step(vlbm_state *s, int64_t nsteps) {
     if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
@@ -305,6 +319,10 @@ int vlbm_step(vlbm_state *s, int64_t nsteps) {
         cudaError_t e = launch_set_tend(s->ctl, 0.0, s->stream);
         if (e != cudaSuccess) return cuda_fail(s, e, "clearing the final time");
         s->tend_active = false;
+    }
+    if (nsteps > 0) {
+        s->at_init = false;
+        s->roll_scratch = nullptr;
     }
     for (int64_t k = 0; k < nsteps; ++k) {
         cudaError_t e = step_once(s);
@@ -321,6 +339,8 @@ int vlbm_step_to(vlbm_state *s, double t_end, int64_t max_steps) {
     cudaError_t e = launch_set_tend(s->ctl, t_end, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "arming the final time");
     s->tend_active = true;
+    s->at_init = false;
+    s->roll_scratch = nullptr;
     int64_t done_steps = 0, chunk = 64;
     while (done_steps < max_steps) {
         const int64_t k = chunk < max_steps - done_steps ? chunk : max_steps - done_steps;
@@ -418,12 +438,15 @@ int vlbm_load(vlbm_state *s, const void *d_src) {
     if (!d_src || ((uintptr_t)d_src & 15)) return fail(s, VLBM_E_INVAL, "source NULL or not 16-byte aligned");
     DeviceGuard g(s->device);
     cudaError_t e = launch_ctl_reset(s->ctl, s->grid.dx, s->alpha, s->a_fixed, s->eps, s->gamma, s->stream);
+    if (e == cudaSuccess) e = upload_desc(s);
     if (e == cudaSuccess)
         e = s->precision == VLBM_FP64 ? launch_load<double>(args_of<double>(s), d_src, s->stream)
                                       : launch_load<float>(args_of<float>(s), d_src, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "load launch");
     s->loaded = true;
     s->tend_active = true;  // the restored header may carry a final time
+    s->at_init = false;
+    s->roll_scratch = nullptr;
     return VLBM_OK;
 }
 

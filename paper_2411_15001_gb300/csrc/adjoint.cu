@@ -1,0 +1,284 @@
+// adjoint.cu -- forward rollout with checkpoints and the reverse sweep that
+// gives the gradient of a loss of the final conserved fields with respect to
+// the initial ones (include/vlbm.h, "adjoint" section).
+//
+// Rollout: the state's own step kernel advances n = 0 .. N-1; the state and its
+// control block are copied to checkpoint c before step c k.
+// Reverse sweep, one segment [s, e] = [c k, min(c k + k, N) - 1] at a time, last
+// segment first: the checkpoint is restored into slot 1 of a segment buffer and
+// the same step kernel recomputes the states s+1 .. e into slots 2 .. e-s+1
+// (reading slot j, writing slot j+1, with the control block in scratch); then the
+// adjoint kernel maps the cotangent of s^{m+1} to that of s^m for m = e .. s.
+// Finally the transpose of the initialisation u_k^0 = M_k(u_0) folds the
+// population cotangents into the conserved planes.
+// a^n is held as the forward run produced it: a constant when the state was made
+// with a fixed lambda, else recorded per step during the recomputation.
+#include <stddef.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "adjoint.cuh"
+#include "state.h"
+
+using namespace vlbm;
+using namespace vlbm::api;
+
+namespace vlbm {
+
+template <typename T>
+static cudaError_t launch_adjoint_step(const AdjArgs<T> &A, int limiter, cudaStream_t s) {
+    const dim3 blk(32, 8), grd((A.nx + 31) / 32, (A.ny + 7) / 8);
+    switch (limiter) {
+        case VLBM_LIM_FIRST_ORDER: k_adjoint_step<T, VLBM_LIM_FIRST_ORDER><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_NONE: k_adjoint_step<T, VLBM_LIM_NONE><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_PP: k_adjoint_step<T, VLBM_LIM_PP><<<grd, blk, 0, s>>>(A); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_adjoint_init(const T *init_state, const Layout &L, const double *a_ptr, double alpha,
+                                       double gamma, const T *cot, T *grad, cudaStream_t s) {
+    const dim3 blk(32, 8), grd((L.nx + 31) / 32, (L.ny + 7) / 8);
+    k_adjoint_init<T><<<grd, blk, 0, s>>>(init_state, L.plane, L.pitch, L.nx, L.ny, a_ptr, alpha, gamma, cot,
+                                         grad);
+    return cudaGetLastError();
+}
+
+}  // namespace vlbm
+
+namespace {
+
+constexpr size_t kCtlBytes = ((sizeof(DevCtl) + 255) / 256) * 256;
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Carving of the caller's scratch block (all offsets 256-byte aligned).
+struct Plan {
+    int64_t nckpt;        // checkpoints at steps 0, k, 2k, ...
+    size_t ckpt_stride;   // state buffer + control block
+    size_t seg_off;       // k + 1 state slots (slot 0 is only ever a TMA window start)
+    size_t segctl_off;    // control block of the recomputation
+    size_t desc_off;      // 2 k InstDesc of the row-marching kernel (by parity of n)
+    size_t ahist_off;     // a^n of each step of a segment
+    size_t cot_off;       // two cotangent buffers of 20 compact planes
+    size_t cot_bytes;
+    size_t total;
+};
+
+Plan plan_of(const vlbm_state *s, int64_t nsteps, int32_t every) {
+    Plan p;
+    const size_t buf = s->L.buf_bytes;
+    p.nckpt = nsteps > 0 ? (nsteps + every - 1) / every : 1;
+    p.ckpt_stride = round256(buf) + kCtlBytes;
+    size_t off = (size_t)p.nckpt * p.ckpt_stride;
+    p.seg_off = off;
+    off += (size_t)(every + 1) * round256(buf);
+    p.segctl_off = off;
+    off += kCtlBytes;
+    p.desc_off = off;
+    off += (size_t)2 * every * 512;
+    p.ahist_off = off;
+    off += round256((size_t)every * sizeof(double));
+    p.cot_bytes = round256((size_t)kNPlane * s->grid.nx * s->grid.ny * s->L.elem);
+    p.cot_off = off;
+    off += 2 * p.cot_bytes;
+    p.total = off;
+    return p;
+}
+
+char *slot_ptr(char *scratch, const Plan &p, const vlbm_state *s, int64_t j) {
+    return scratch + p.seg_off + (size_t)j * round256(s->L.buf_bytes);
+}
+
+int check_scratch(vlbm_state *s, void *scratch, size_t bytes, const Plan &p) {
+    if (!scratch || ((uintptr_t)scratch & 255)) return fail(s, VLBM_E_NOMEM, "scratch NULL or not 256-byte aligned");
+    if (bytes < p.total) return fail(s, VLBM_E_NOMEM, "scratch has %zu bytes, needs %zu", bytes, p.total);
+    cudaPointerAttributes pa;
+    cudaError_t e = cudaPointerGetAttributes(&pa, scratch);
+    if (e != cudaSuccess || (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(s, VLBM_E_INVAL, "scratch is not device memory");
+    }
+    return VLBM_OK;
+}
+
+// Descriptors of the row-marching kernel for the recomputation: step j of a
+// segment reads slot j + 1 and writes slot j + 2. The kernel reads planes
+// 20 (n & 1) .. 20 (n & 1) + 19 of its TMA window, so the window starts
+// (n & 1) slots before the slot it reads.
+template <typename T>
+bool build_recompute_descs(vlbm_state *s, char *scratch, const Plan &p, int32_t every,
+                           std::vector<unsigned char> &host) {
+    host.assign((size_t)2 * every * 512, 0);
+    InstDesc<T> base;
+    memcpy(&base, s->desc_host.data(), sizeof base);
+    for (int par = 0; par < 2; ++par) {
+        for (int j = 0; j + 1 < every; ++j) {   // the last state of a segment is not stepped
+            InstDesc<T> d = base;
+            char *in = slot_ptr(scratch, p, s, j + 1);
+            if (!encode_state_tmap(&d.tmap, in - (size_t)par * round256(s->L.buf_bytes), s->L)) return false;
+            d.buf0 = d.buf1 = (T *)slot_ptr(scratch, p, s, j + 2);
+            d.ctl = (DevCtl *)(scratch + p.segctl_off);
+            memcpy(host.data() + ((size_t)par * every + j) * 512, &d, sizeof d);
+        }
+    }
+    return true;
+}
+
+// One recomputation step m = s0 + j of a segment.
+template <typename T>
+cudaError_t recompute_step(vlbm_state *s, char *scratch, const Plan &p, int32_t every, int64_t m, int64_t j) {
+    if (use_fused(s)) {
+        FusedBatchArgs<T> B = batch_args_of<T>(s);
+        B.insts = (const InstDesc<T> *)(scratch + p.desc_off + ((size_t)(m & 1) * every + j) * 512);
+        return launch_step_fused<T>(B, s->limiter, s->fused_grid, s->stream);
+    }
+    StepArgs<T> A = args_of<T>(s);
+    T *in = (T *)slot_ptr(scratch, p, s, j + 1), *out = (T *)slot_ptr(scratch, p, s, j + 2);
+    A.buf0 = (m & 1) ? out : in;
+    A.buf1 = (m & 1) ? in : out;
+    A.ctl = (DevCtl *)(scratch + p.segctl_off);
+    cudaError_t e = launch_step_simple<T>(A, s->stream);
+    if (e == cudaSuccess) e = launch_ghosts<T>(A, s->stream);   // reads the parity of n + 1
+    return e;
+}
+
+int rollout(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const Plan &p) {
+    const size_t buf = s->L.buf_bytes;
+    for (int64_t n = 0; n <= nsteps; ++n) {
+        if (n % every == 0 && (n < nsteps || nsteps == 0)) {
+            char *ck = scratch + (size_t)(n / every) * p.ckpt_stride;
+            const char *cur = (const char *)s->ws + ((n & 1) ? buf : 0);
+            cudaError_t e = cudaMemcpyAsync(ck, cur, buf, cudaMemcpyDeviceToDevice, s->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ck + round256(buf), s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "checkpoint copy");
+        }
+        if (n == nsteps) break;
+        cudaError_t e = step_once(s);
+        if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+    }
+    s->at_init = false;
+    s->roll_scratch = scratch;
+    s->roll_steps = nsteps;
+    s->roll_every = every;
+    return VLBM_OK;
+}
+
+template <typename T>
+int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const Plan &p, const void *dLduN,
+            void *dLdu0) {
+    const size_t buf = s->L.buf_bytes;
+    const long long N = (long long)s->grid.nx * s->grid.ny;
+    const bool fixed_a = s->a_fixed > 0.0;
+    T *cot[2] = {(T *)(scratch + p.cot_off), (T *)(scratch + p.cot_off + p.cot_bytes)};
+    DevCtl *segctl = (DevCtl *)(scratch + p.segctl_off);
+    double *ahist = (double *)(scratch + p.ahist_off);
+    cudaError_t e = cudaMemcpyAsync(cot[0], dLduN, (size_t)4 * N * sizeof(T), cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cot[0] + 4 * N, 0, (size_t)(kNPlane - 4) * N * sizeof(T), s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cotangent seed");
+    std::vector<unsigned char> descs;
+    if (use_fused(s)) {
+        if (!build_recompute_descs<T>(s, scratch, p, every, descs))
+            return fail(s, VLBM_E_CUDA, "TMA descriptor of a recomputation slot");
+        e = cudaMemcpyAsync(scratch + p.desc_off, descs.data(), descs.size(), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "descriptor upload");
+    }
+    int cur = 0;
+    AdjArgs<T> A;
+    A.plane = s->L.plane;
+    A.pitch = s->L.pitch;
+    A.nx = s->grid.nx;
+    A.ny = s->grid.ny;
+    A.alpha = s->alpha;
+    A.gamma = s->gamma;
+    A.eps = s->eps;
+    for (int64_t c = nsteps > 0 ? p.nckpt - 1 : -1; c >= 0; --c) {
+        const int64_t s0 = c * every;
+        const int64_t e0 = (s0 + every < nsteps ? s0 + every : nsteps) - 1;
+        const char *ck = scratch + (size_t)c * p.ckpt_stride;
+        e = cudaMemcpyAsync(slot_ptr(scratch, p, s, 1), ck, buf, cudaMemcpyDeviceToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(segctl, ck + round256(buf), sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
+        for (int64_t m = s0; e == cudaSuccess && m <= e0; ++m) {
+            if (!fixed_a)
+                e = cudaMemcpyAsync(ahist + (m - s0), &segctl->a, sizeof(double), cudaMemcpyDeviceToDevice,
+                                    s->stream);
+            if (e == cudaSuccess && m < e0) e = recompute_step<T>(s, scratch, p, every, m, m - s0);
+        }
+        if (e != cudaSuccess) return cuda_fail(s, e, "recomputation");
+        for (int64_t m = e0; m >= s0; --m) {
+            A.fwd = (const T *)slot_ptr(scratch, p, s, m - s0 + 1);
+            A.cot_in = cot[cur];
+            A.cot_out = cot[cur ^ 1];
+            A.a = fixed_a ? &segctl->a : ahist + (m - s0);
+            e = launch_adjoint_step<T>(A, s->limiter, s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "adjoint step launch");
+            cur ^= 1;
+        }
+    }
+    const char *ck0 = scratch;
+    e = launch_adjoint_init<T>((const T *)ck0, s->L, (const double *)(ck0 + round256(buf)) + 2, s->alpha, s->gamma,
+                               cot[cur], (T *)dLdu0, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "initialisation adjoint launch");
+    return VLBM_OK;
+}
+
+}  // namespace
+
+static_assert(offsetof(DevCtl, a) == 2 * sizeof(double), "a is the third field of the control block");
+
+extern "C" {
+
+size_t vlbm_adjoint_scratch_bytes(const vlbm_state *s, int64_t nsteps, int32_t ckpt_every) {
+    if (!s || nsteps < 0 || ckpt_every < 1) return 0;
+    return plan_of(s, nsteps, ckpt_every).total;
+}
+
+int vlbm_rollout(vlbm_state *s, int64_t nsteps, int32_t ckpt_every, void *d_scratch, size_t scratch_bytes) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    if (nsteps < 0 || ckpt_every < 1) return fail(s, VLBM_E_INVAL, "need nsteps >= 0 and ckpt_every >= 1");
+    if (!s->loaded || !s->at_init)
+        return fail(s, VLBM_E_INVAL, "rollout starts from the state vlbm_set_conserved leaves (n = 0)");
+    DeviceGuard g(s->device);
+    const Plan p = plan_of(s, nsteps, ckpt_every);
+    int rc = check_scratch(s, d_scratch, scratch_bytes, p);
+    if (rc) return rc;
+    return rollout(s, nsteps, ckpt_every, (char *)d_scratch, p);
+}
+
+int vlbm_adjoint(vlbm_state *s, const void *d_u0, int64_t nsteps, int32_t ckpt_every, const void *d_dLduN,
+                 void *d_dLdu0, void *d_scratch, size_t scratch_bytes) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    if (nsteps < 0 || ckpt_every < 1) return fail(s, VLBM_E_INVAL, "need nsteps >= 0 and ckpt_every >= 1");
+    if (!d_dLduN || !d_dLdu0) return fail(s, VLBM_E_INVAL, "cotangent pointer is NULL");
+    if (s->limiter != VLBM_LIM_FIRST_ORDER && s->limiter != VLBM_LIM_NONE && s->limiter != VLBM_LIM_PP)
+        return fail(s, VLBM_E_UNSUPPORTED, "the adjoint covers the first-order, unlimited and PP schemes");
+    for (int q = 0; q < 4; ++q)
+        if (s->grid.bc[q] != VLBM_BC_PERIODIC)
+            return fail(s, VLBM_E_UNSUPPORTED, "the adjoint covers periodic grids");
+    DeviceGuard g(s->device);
+    const Plan p = plan_of(s, nsteps, ckpt_every);
+    int rc = check_scratch(s, d_scratch, scratch_bytes, p);
+    if (rc) return rc;
+    char *scratch = (char *)d_scratch;
+    if (d_u0) {
+        const long long N = (long long)s->grid.nx * s->grid.ny;
+        const char *u0 = (const char *)d_u0;
+        const size_t pb = (size_t)N * s->L.elem;
+        rc = set_conserved(s, u0, u0 + pb, u0 + 3 * pb);
+        if (rc) return rc;
+        rc = rollout(s, nsteps, ckpt_every, scratch, p);
+        if (rc) return rc;
+    } else if (s->roll_scratch != d_scratch || s->roll_steps != nsteps || s->roll_every != ckpt_every) {
+        return fail(s, VLBM_E_INVAL, "no rollout with these steps, interval and scratch precedes this call");
+    }
+    return s->precision == VLBM_FP64 ? reverse<double>(s, nsteps, ckpt_every, scratch, p, d_dLduN, d_dLdu0)
+                                     : reverse<float>(s, nsteps, ckpt_every, scratch, p, d_dLduN, d_dLdu0);
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// adjoint.cuh -- transpose of one blended collide + limit + stream step.
+//
+// For cotangents (ubar', pbar_k') of the step's outputs it returns the cotangents
+// of its inputs (u, u_1..u_4), holding the kinetic speed a^n fixed and
+// differentiating the limiter piecewise on the branch the forward step took
+// (theta = 1, theta_rho, theta_p or the clamp at 0). One thread per cell
+// gathers every term in which its inputs appear:
+//  - the streamed populations u_k'(c') = M_k(c) + theta d_k(c) of the downstream
+//    neighbour c' and the local terms -theta d_k(c) of its own u'(c)
+//    (eq. blending_u1 / blending_u);
+//  - the face states u* and dF of its four faces (eq. D2Q5_convexproof_3,
+//    eq. 2nd-order_flux) through the limiter's derivative;
+//  - the Maxwellians M_k = (1-alpha)/4 u +- f/(2a) (Example D2Q5) through the
+//    Jacobians of the Euler fluxes.
+// The forward state is read from a padded buffer with its ghost frame; the
+// cotangents are compact planes and the grid is periodic.
+#pragma once
+
+#include "common.cuh"
+#include "step_simple.cuh"
+
+namespace vlbm {
+
+template <typename T>
+struct AdjArgs {
+    const T *fwd;          // forward state s^n (padded, ghost frame filled)
+    long long plane;
+    int pitch, nx, ny;
+    const T *cot_in;       // cotangent of s^{n+1}: 20 compact planes
+    T *cot_out;            // cotangent of s^n: 20 compact planes
+    const double *a;       // kinetic speed a^n of the step (device scalar)
+    double alpha, gamma, eps;
+};
+
+// w^T df/du for the Euler x-flux (dir 0) or y-flux (dir 1) at state u.
+template <typename T>
+__device__ __forceinline__ void flux_vjp(const T u[4], T gm1, int dir, const T w[4], T r[4]) {
+    const T ir = T(1) / u[0];
+    const T v1 = u[1] * ir, v2 = u[2] * ir;
+    const T q = T(0.5) * (v1 * v1 + v2 * v2);
+    const T p = gm1 * (u[3] - u[0] * q);
+    const T H = (u[3] + p) * ir;
+    if (dir == 0) {
+        r[0] = w[1] * (gm1 * q - v1 * v1) - w[2] * v1 * v2 + w[3] * v1 * (gm1 * q - H);
+        r[1] = w[0] + w[1] * (T(2) - gm1) * v1 + w[2] * v2 + w[3] * (H - gm1 * v1 * v1);
+        r[2] = -w[1] * gm1 * v2 + w[2] * v1 - w[3] * gm1 * v1 * v2;
+        r[3] = w[1] * gm1 + w[3] * (T(1) + gm1) * v1;
+    } else {
+        r[0] = -w[1] * v1 * v2 + w[2] * (gm1 * q - v2 * v2) + w[3] * v2 * (gm1 * q - H);
+        r[1] = w[1] * v2 - w[2] * gm1 * v1 - w[3] * gm1 * v1 * v2;
+        r[2] = w[0] + w[1] * v1 + w[2] * (T(2) - gm1) * v2 + w[3] * (H - gm1 * v2 * v2);
+        r[3] = w[2] * gm1 + w[3] * (T(1) + gm1) * v2;
+    }
+}
+
+// Forward theta of a face (as combine_theta computes it) and its gradient with
+// respect to (u*, dF) on the active branch. Density bounds of the PP kind only.
+template <typename T, int LIM>
+__device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const StepConsts<T> &k,
+                                            T gus[4], T gdf[4]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) gus[c] = gdf[c] = T(0);
+    if (LIM == VLBM_LIM_FIRST_ORDER) return T(0);
+    if (LIM == VLBM_LIM_NONE) return T(1);
+    const T tr = theta_rho_pp(us[0], df[0], k);
+    unsigned int dummy = 0;
+    const T th = combine_theta(tr, us, df, k, dummy);
+    if (!(th > T(0)) || !(th < T(1))) return th;    // clamped: no gradient
+    if (th == tr) {                                  // density bound active (Sec. 3.3.3)
+        const T ad = fabs(df[0]);
+        gus[0] = k.kappa / ad;
+        gdf[0] = -k.kappa * us[0] * (df[0] > T(0) ? T(1) : T(-1)) / (ad * ad);
+        return th;
+    }
+    // internal-energy bound active (Sec. 3.4): theta = kappa / varrho - eps
+    const T rs = us[0], m1 = us[1], m2 = us[2], Es = us[3];
+    const T dr = df[0], dm1 = df[1], dm2 = df[2], dE = df[3];
+    const T g0 = m1 * m1 + m2 * m2 - T(2) * rs * Es;
+    const T g1 = T(2) * (dr * Es + dE * rs - dm1 * m1 - dm2 * m2);
+    const T cq = dm1 * dm1 + dm2 * dm2 - T(2) * dr * dE;
+    T disc = g1 * g1 - T(4) * g0 * cq;
+    if (disc < T(0)) disc = T(0);
+    const T sd = sqrt(disc);
+    const T r1 = fabs(dr) / rs;
+    const T r2 = (fabs(g1) + sd) / (T(-2) * g0);
+    T gr_us[4], gr_df[4];
+    if (r1 >= r2) {
+        const T sg = dr > T(0) ? T(1) : (dr < T(0) ? T(-1) : T(0));
+        gr_us[0] = -fabs(dr) / (rs * rs);
+        gr_us[1] = gr_us[2] = gr_us[3] = T(0);
+        gr_df[0] = sg / rs;
+        gr_df[1] = gr_df[2] = gr_df[3] = T(0);
+    } else {
+        const T D = T(-2) * g0;
+        const T sg1 = g1 > T(0) ? T(1) : (g1 < T(0) ? T(-1) : T(0));
+        // dN = sg1 dg1 + ddisc / (2 sd); dD = -2 dg0; dr2 = (dN - r2 dD) / D
+        const T hs = sd > T(0) ? T(0.5) / sd : T(0);
+        // gradients of g0, g1, cq
+        const T dg0_us[4] = {T(-2) * Es, T(2) * m1, T(2) * m2, T(-2) * rs};
+        const T dg1_us[4] = {T(2) * dE, T(-2) * dm1, T(-2) * dm2, T(2) * dr};
+        const T dg1_df[4] = {T(2) * Es, T(-2) * m1, T(-2) * m2, T(2) * rs};
+        const T dcq_df[4] = {T(-2) * dE, T(2) * dm1, T(2) * dm2, T(-2) * dr};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            // ddisc = 2 g1 dg1 - 4 cq dg0 - 4 g0 dcq
+            const T ddisc_us = T(2) * g1 * dg1_us[c] - T(4) * cq * dg0_us[c];
+            const T ddisc_df = T(2) * g1 * dg1_df[c] - T(4) * g0 * dcq_df[c];
+            const T dN_us = sg1 * dg1_us[c] + hs * ddisc_us;
+            const T dN_df = sg1 * dg1_df[c] + hs * ddisc_df;
+            gr_us[c] = (dN_us - r2 * (T(-2) * dg0_us[c])) / D;
+            gr_df[c] = dN_df / D;
+        }
+    }
+    const T rr = r1 > r2 ? r1 : r2;
+    const T f = -k.kappa / (rr * rr);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        gus[c] = f * gr_us[c];
+        gdf[c] = f * gr_df[c];
+    }
+    return th;
+}
+
+template <typename T, int LIM>
+__global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= A.nx || j >= A.ny) return;
+    const StepConsts<T> k = make_consts<T>(*A.a, A.alpha, A.gamma, A.eps);
+    CellLoad<T> L{A.fwd, A.plane, A.pitch};
+    const long long N = (long long)A.nx * A.ny;
+    // ---------------------------------------------------------- forward quantities
+    T uC[4], uW[4], uE[4], uS[4], uN[4];
+    L.u4(0, i, j, uC);
+    L.u4(0, i - 1, j, uW);
+    L.u4(0, i + 1, j, uE);
+    L.u4(0, i, j - 1, uS);
+    L.u4(0, i, j + 1, uN);
+    T fC[4], gC[4], fW[4], gW[4], fE[4], gE[4], fS[4], gS[4], fN[4], gN[4];
+    euler_fluxes(uC, k.gm1, fC, gC);
+    euler_fluxes(uW, k.gm1, fW, gW);
+    euler_fluxes(uE, k.gm1, fE, gE);
+    euler_fluxes(uS, k.gm1, fS, gS);
+    euler_fluxes(uN, k.gm1, fN, gN);
+    T d1C[4], d2C[4], d3C[4], d4C[4], d1W[4], d2E[4], d3S[4], d4N[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        d1C[c] = RN<T>::sub(maxwell_plus(uC[c], fC[c], k), L.v(4 + c, i, j));
+        d2C[c] = RN<T>::sub(maxwell_minus(uC[c], fC[c], k), L.v(8 + c, i, j));
+        d3C[c] = RN<T>::sub(maxwell_plus(uC[c], gC[c], k), L.v(12 + c, i, j));
+        d4C[c] = RN<T>::sub(maxwell_minus(uC[c], gC[c], k), L.v(16 + c, i, j));
+        d1W[c] = RN<T>::sub(maxwell_plus(uW[c], fW[c], k), L.v(4 + c, i - 1, j));
+        d2E[c] = RN<T>::sub(maxwell_minus(uE[c], fE[c], k), L.v(8 + c, i + 1, j));
+        d3S[c] = RN<T>::sub(maxwell_plus(uS[c], gS[c], k), L.v(12 + c, i, j - 1));
+        d4N[c] = RN<T>::sub(maxwell_minus(uN[c], gN[c], k), L.v(16 + c, i, j + 1));
+    }
+    T us[4][4], df[4][4];   // faces W, E, S, N
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        us[0][c] = face_star(uW[c], fW[c], uC[c], fC[c], k);
+        df[0][c] = face_dflux(d1W[c], d2C[c], k);
+        us[1][c] = face_star(uC[c], fC[c], uE[c], fE[c], k);
+        df[1][c] = face_dflux(d1C[c], d2E[c], k);
+        us[2][c] = face_star(uS[c], gS[c], uC[c], gC[c], k);
+        df[2][c] = face_dflux(d3S[c], d4C[c], k);
+        us[3][c] = face_star(uC[c], gC[c], uN[c], gN[c], k);
+        df[3][c] = face_dflux(d3C[c], d4N[c], k);
+    }
+    T th[4], gus[4][4], gdf[4][4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) th[f] = theta_and_grad<T, LIM>(us[f], df[f], k, gus[f], gdf[f]);
+    // ---------------------------------------------------------- cotangents (periodic)
+    const int iw = i > 0 ? i - 1 : A.nx - 1, ie = i < A.nx - 1 ? i + 1 : 0;
+    const int js = j > 0 ? j - 1 : A.ny - 1, jn = j < A.ny - 1 ? j + 1 : 0;
+    const long long cC = (long long)j * A.nx + i, cW = (long long)j * A.nx + iw, cE = (long long)j * A.nx + ie;
+    const long long cS = (long long)js * A.nx + i, cN = (long long)jn * A.nx + i;
+    auto cot = [&](int q, long long c) { return A.cot_in[q * N + c]; };
+    T ubC[4], ubW[4], ubE[4], ubS[4], ubN[4];
+    T P1C[4], P2C[4], P3C[4], P4C[4], P1E[4], P2W[4], P3N[4], P4S[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        ubC[c] = cot(c, cC);
+        ubW[c] = cot(c, cW);
+        ubE[c] = cot(c, cE);
+        ubS[c] = cot(c, cS);
+        ubN[c] = cot(c, cN);
+        // streamed populations carry the cotangent of u' as well (u' sums them)
+        P1C[c] = cot(4 + c, cC) + ubC[c];
+        P2C[c] = cot(8 + c, cC) + ubC[c];
+        P3C[c] = cot(12 + c, cC) + ubC[c];
+        P4C[c] = cot(16 + c, cC) + ubC[c];
+        P1E[c] = cot(4 + c, cE) + ubE[c];
+        P2W[c] = cot(8 + c, cW) + ubW[c];
+        P3N[c] = cot(12 + c, cN) + ubN[c];
+        P4S[c] = cot(16 + c, cS) + ubS[c];
+    }
+    // theta cotangents of the four faces
+    T tb[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        tb[0] += d1W[c] * (P1C[c] - ubW[c]) + d2C[c] * (P2W[c] - ubC[c]);
+        tb[1] += d1C[c] * (P1E[c] - ubC[c]) + d2E[c] * (P2C[c] - ubE[c]);
+        tb[2] += d3S[c] * (P3C[c] - ubS[c]) + d4C[c] * (P4S[c] - ubC[c]);
+        tb[3] += d3C[c] * (P3N[c] - ubC[c]) + d4N[c] * (P4C[c] - ubN[c]);
+    }
+    // ---------------------------------------------------------- input cotangents
+    T wx[4], wy[4], out[kNPlane];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const T usb_W = tb[0] * gus[0][c], usb_E = tb[1] * gus[1][c];
+        const T usb_S = tb[2] * gus[2][c], usb_N = tb[3] * gus[3][c];
+        const T dfb_W = tb[0] * gdf[0][c], dfb_E = tb[1] * gdf[1][c];
+        const T dfb_S = tb[2] * gdf[2][c], dfb_N = tb[3] * gdf[3][c];
+        const T db1 = th[1] * (P1E[c] - ubC[c]) + k.a * dfb_E;
+        const T db2 = th[0] * (P2W[c] - ubC[c]) - k.a * dfb_W;
+        const T db3 = th[3] * (P3N[c] - ubC[c]) + k.a * dfb_N;
+        const T db4 = th[2] * (P4S[c] - ubC[c]) - k.a * dfb_S;
+        const T Mb1 = P1E[c] + db1, Mb2 = P2W[c] + db2, Mb3 = P3N[c] + db3, Mb4 = P4S[c] + db4;
+        out[4 + c] = -db1;
+        out[8 + c] = -db2;
+        out[12 + c] = -db3;
+        out[16 + c] = -db4;
+        out[c] = k.alpha * ubC[c] + k.w * (Mb1 + Mb2 + Mb3 + Mb4) + T(0.5) * (usb_W + usb_E + usb_S + usb_N);
+        wx[c] = (Mb1 - Mb2) * k.inv2a + (usb_E - usb_W) * k.inv2k;
+        wy[c] = (Mb3 - Mb4) * k.inv2a + (usb_N - usb_S) * k.inv2k;
+    }
+    T rx[4], ry[4];
+    flux_vjp(uC, k.gm1, 0, wx, rx);
+    flux_vjp(uC, k.gm1, 1, wy, ry);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c] += rx[c] + ry[c];
+#pragma unroll
+    for (int q = 0; q < kNPlane; ++q) A.cot_out[q * N + cC] = out[q];
+}
+
+// Cotangent of the initialisation u_k^0 = M_k(u_0) (Sec. 4 preamble) folded into
+// the conserved planes: ubar_0 = ubar^0 + sum_k (dM_k/du)^T pbar_k^0, with u_0
+// read from the padded initial state and a^0 held fixed.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adjoint_init(const T *init_state, long long plane, int pitch, int nx,
+                                                      int ny, const double *a_ptr, double alpha, double gamma,
+                                                      const T *cot, T *grad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const long long N = (long long)nx * ny, c = (long long)j * nx + i;
+    const double a = *a_ptr;
+    const T w = T((1.0 - alpha) / 4.0), inv2a = T(1.0 / (2.0 * a)), gm1 = T(gamma - 1.0);
+    const CellLoad<T> L{init_state, plane, pitch};
+    T u[4], wx[4], wy[4], rx[4], ry[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        u[q] = L.v(q, i, j);
+        const T p1 = cot[(4 + q) * N + c], p2 = cot[(8 + q) * N + c];
+        const T p3 = cot[(12 + q) * N + c], p4 = cot[(16 + q) * N + c];
+        grad[q * N + c] = cot[q * N + c] + w * (p1 + p2 + p3 + p4);
+        wx[q] = (p1 - p2) * inv2a;
+        wy[q] = (p3 - p4) * inv2a;
+    }
+    flux_vjp(u, gm1, 0, wx, rx);
+    flux_vjp(u, gm1, 1, wy, ry);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) grad[q * N + c] += rx[q] + ry[q];
+}
+
+}  // namespace vlbm

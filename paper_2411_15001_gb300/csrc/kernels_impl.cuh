@@ -46,8 +46,7 @@ cudaError_t launch_step_simple<VLBM_T>(const StepArgs<VLBM_T> &A, cudaStream_t s
 
 namespace {
 template <int LIM>
-cudaError_t fused_one(const StepArgs<VLBM_T> &A, const CUtensorMap &tm, int strips, int grid,
-                      cudaStream_t s) {
+cudaError_t fused_one(const FusedBatchArgs<VLBM_T> &B, int grid, cudaStream_t s) {
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -58,7 +57,7 @@ cudaError_t fused_one(const StepArgs<VLBM_T> &A, const CUtensorMap &tm, int stri
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    k_step_fused<VLBM_T, LIM><<<grid, kFB, smem, s>>>(tm, A, strips);
+    k_step_fused<VLBM_T, LIM><<<grid, kFB, smem, s>>>(B);
     return cudaGetLastError();
 }
 
@@ -85,18 +84,29 @@ int fused_occupancy<VLBM_T>(int limiter) {
 }
 
 template <>
-cudaError_t launch_step_fused<VLBM_T>(const StepArgs<VLBM_T> &A, const CUtensorMap &tm, int strips,
-                                      int grid, cudaStream_t s) {
-    cudaError_t e;
-    switch (A.limiter) {
-        case VLBM_LIM_FIRST_ORDER: e = fused_one<VLBM_LIM_FIRST_ORDER>(A, tm, strips, grid, s); break;
-        case VLBM_LIM_NONE: e = fused_one<VLBM_LIM_NONE>(A, tm, strips, grid, s); break;
-        case VLBM_LIM_PP: e = fused_one<VLBM_LIM_PP>(A, tm, strips, grid, s); break;
-        case VLBM_LIM_LMP: e = fused_one<VLBM_LIM_LMP>(A, tm, strips, grid, s); break;
-        case VLBM_LIM_RLMP: e = fused_one<VLBM_LIM_RLMP>(A, tm, strips, grid, s); break;
+const void *fused_kernel_fn<VLBM_T>(int limiter, size_t *smem) {
+    *smem = sizeof(FusedSmem<VLBM_T>);
+    fused_blocks_per_sm<VLBM_LIM_PP>();   // sets the dynamic shared memory attributes
+    switch (limiter) {
+        case VLBM_LIM_FIRST_ORDER: fused_blocks_per_sm<VLBM_LIM_FIRST_ORDER>(); return (const void *)k_step_fused<VLBM_T, VLBM_LIM_FIRST_ORDER>;
+        case VLBM_LIM_NONE: fused_blocks_per_sm<VLBM_LIM_NONE>(); return (const void *)k_step_fused<VLBM_T, VLBM_LIM_NONE>;
+        case VLBM_LIM_PP: return (const void *)k_step_fused<VLBM_T, VLBM_LIM_PP>;
+        case VLBM_LIM_LMP: fused_blocks_per_sm<VLBM_LIM_LMP>(); return (const void *)k_step_fused<VLBM_T, VLBM_LIM_LMP>;
+        default: fused_blocks_per_sm<VLBM_LIM_RLMP>(); return (const void *)k_step_fused<VLBM_T, VLBM_LIM_RLMP>;
+    }
+}
+
+template <>
+cudaError_t launch_step_fused<VLBM_T>(const FusedBatchArgs<VLBM_T> &B, int limiter, int grid,
+                                      cudaStream_t s) {
+    switch (limiter) {
+        case VLBM_LIM_FIRST_ORDER: return fused_one<VLBM_LIM_FIRST_ORDER>(B, grid, s);
+        case VLBM_LIM_NONE: return fused_one<VLBM_LIM_NONE>(B, grid, s);
+        case VLBM_LIM_PP: return fused_one<VLBM_LIM_PP>(B, grid, s);
+        case VLBM_LIM_LMP: return fused_one<VLBM_LIM_LMP>(B, grid, s);
+        case VLBM_LIM_RLMP: return fused_one<VLBM_LIM_RLMP>(B, grid, s);
         default: return cudaErrorInvalidValue;
     }
-    return e;
 }
 
 template <>

@@ -1,0 +1,99 @@
+// state.h -- the host object behind vlbm_state* and the helpers that the entry
+// points of abi.cu (single grid) and adjoint.cu (rollout and adjoint) share.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/vlbm.h"
+#include "vlbm_internal.h"
+
+struct vlbm_state {
+    vlbm_grid grid;
+    int precision, limiter, kernel;
+    double gamma, lambda, alpha, eps, a_fixed;
+    vlbm::Layout L;
+    void *ws;
+    cudaStream_t stream;
+    vlbm::DevCtl *ctl;
+    int device;
+    CUtensorMap tmap;   // 3D view [40 planes][rows][pitch] of both state buffers
+    bool have_tmap;
+    int strips, chunk, nitems, fused_grid;
+    std::vector<unsigned char> desc_host;   // InstDesc<T> of this grid
+    std::vector<int> items_host;            // item -> grid (all 0)
+    bool profiling;
+    std::vector<cudaEvent_t> ev;   // event pairs of timed launches
+    size_t ev_used;
+    bool loaded;        // set_conserved or load has run
+    bool tend_active;   // a final time is armed on the device
+    bool at_init;       // the state is u_k = M_k(u_0) at n = 0, as set_conserved leaves it
+    // checkpoints written by the last vlbm_rollout (consumed by vlbm_adjoint)
+    const void *roll_scratch;
+    int64_t roll_steps;
+    int32_t roll_every;
+    char err[256];
+};
+
+namespace vlbm {
+namespace api {
+
+// Record a message for vlbm_last_error_detail (per state, or per thread when
+// s is NULL) and return code.
+int fail(vlbm_state *s, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int cuda_fail(vlbm_state *s, cudaError_t e, const char *what);
+
+// Keep the caller's current device; run the call on the state's device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+inline StepArgs<T> args_of(const vlbm_state *s) {
+    StepArgs<T> A;
+    A.buf0 = (T *)s->ws;
+    A.buf1 = (T *)((char *)s->ws + s->L.buf_bytes);
+    A.plane = s->L.plane;
+    A.pitch = s->L.pitch;
+    A.nx = s->grid.nx;
+    A.ny = s->grid.ny;
+    for (int k = 0; k < 4; ++k) A.bc[k] = s->grid.bc[k];
+    A.limiter = s->limiter;
+    A.gamma = s->gamma;
+    A.alpha = s->alpha;
+    A.eps = s->eps;
+    A.ctl = s->ctl;
+    return A;
+}
+
+inline bool use_fused(const vlbm_state *s) { return s->have_tmap && s->kernel != VLBM_KERNEL_SIMPLE; }
+
+// Arguments of the row-marching kernel for this grid (descriptor block of the workspace).
+template <typename T>
+inline FusedBatchArgs<T> batch_args_of(const vlbm_state *s) {
+    FusedBatchArgs<T> B;
+    char *base = (char *)s->ws + s->L.desc_offset;
+    B.insts = (const InstDesc<T> *)base;
+    B.bctl = (BatchCtl *)(base + 512);
+    B.item_inst = (const int *)(base + 768);
+    B.nitems = s->nitems;
+    B.gamma = s->gamma;
+    B.alpha = s->alpha;
+    B.eps = s->eps;
+    return B;
+}
+
+cudaError_t step_once(vlbm_state *s);           // one step of the state's configured kernel
+int read_ctl(vlbm_state *s, DevCtl *h);         // synchronous copy of the control block
+int set_conserved(vlbm_state *s, const void *rho, const void *mom, const void *E);
+
+}  // namespace api
+}  // namespace vlbm

@@ -1,24 +1,29 @@
 // step_fused.cuh -- one blended collide + limit + stream step as a single
 // row-marching pass: every cell's 20 values are read from HBM once and written
-// once.
+// once, together with the ghost images of the boundary cells.
 //
-// Decomposition. The grid is cut into strips of kFOut = 124 output columns.
-// A CTA of kFB = 128 threads (one padded column each, two halo columns on
-// either side) marches up a strip; persistent CTAs split the strips' rows
-// evenly. Rows arrive by TMA (one 3D box of 128 columns x 20 planes per row)
-// into a 3-slot ring completed on mbarriers, so up to three rows are in flight
-// per CTA while earlier rows are computed.
+// Work. A grid is cut into strips of kFOut = 120 output columns and chunks of
+// `chunk` rows; a work item is one (instance, strip, chunk). Persistent CTAs of
+// kFB = 128 threads (one column each: four halo columns on either side of the
+// strip) take items from a global counter, so items that cost more (faces whose
+// theta_p needs the FP64 solve cluster on shocks) do not hold up the step. One
+// launch can advance many independent grids (a batch); each grid has its own
+// kinetic speed, control block and completion count, and the CTA that finishes a
+// grid's last item runs that grid's end-of-step reduction.
 //
-// Per row R (output row O = R - 2, the radius-2 LMP stencil of eq. LMP_minmax):
-//  P1  fluxes, Maxwellians and non-equilibrium parts d_k of row R; the values
-//      x-neighbours need (u, f, d_1, d_2) go to a 4-row shared ring, the ones
-//      only the own column needs (u, g, d_3, d_4) stay in a 4-row register
-//      history; rho* of the y-face R - 1/2.
-//  P2  density bounds mu, nu of row R - 1 (LMP/RLMP).
-//  P3  theta of the x-faces of row R - 1 and of the y-face R - 3/2 (Sec.
-//      3.3-3.4); then u*, dF of the x-faces of row R and the y-face R - 1/2.
-//  P4  collide + stream of row O (eq. blending_u1 / blending_u), stores, monitors.
-// Three __syncthreads per row; every quantity is computed once.
+// Rows arrive by TMA (one 3D box of 128 columns x 20 planes per row) into a
+// 3-slot ring completed on mbarriers. Per row R (output row O = R - 2, the
+// radius-2 stencil of the LMP bounds, eq. LMP_minmax):
+//  P1  fluxes, Maxwellians, non-equilibrium parts d_k of row R; what x-neighbours
+//      need (u, f, d_1, d_2) goes to a 4-row shared ring, what only the own column
+//      needs (u, g, d_3, d_4) to a 4-row register history; rho* of y-face R - 1/2.
+//  P2  density bounds of row R - 1 (LMP/RLMP).
+//  P3  theta of the x-faces of row R - 1 and of y-face R - 3/2 (Sec. 3.3-3.4);
+//      then u*, dF of the x-faces of row R and of y-face R - 1/2.
+//  P4  collide + stream of row O (eq. blending_u1 / blending_u), stores, ghost
+//      images, monitors.
+// Output rows start on 32-byte sector boundaries (kOX = 8, strips of 120 floats),
+// so no sector is written partially by two CTAs.
 #pragma once
 
 #include "common.cuh"
@@ -27,7 +32,8 @@
 namespace vlbm {
 
 constexpr int kFB = 128;       // threads per CTA = TMA box width (columns)
-constexpr int kFOut = 124;     // output columns per strip
+constexpr int kFOut = 120;     // output columns per strip
+constexpr int kFHalo = 4;      // box columns left of the strip
 constexpr int kRawSlots = 3;   // TMA row ring
 constexpr int kXSlots = 4;     // shared ring of per-row neighbour data
 
@@ -39,6 +45,7 @@ struct FusedSmem {
     T mu[2][kFB], nu[2][kFB];  // density bounds
     T thx[2][kFB];             // theta of x-face (b, b+1)
     unsigned long long bar[kRawSlots];
+    int item;
     int abort;
 };
 
@@ -47,17 +54,84 @@ struct Hist {
     T u[4], g[4], d3[4], d4[4];
 };
 
+// The fields of a grid's descriptor that the row loop uses, held in registers
+// (the descriptor itself lives in global memory).
+struct Geo {
+    long long plane;
+    int pitch, nx, ny;
+    int bc[4];
+};
+
+// Write the ghost images of interior cell (c, O) into `out`: its periodic
+// copies, zero-gradient copies or mirror images on the other side of every
+// boundary it sits next to (the inverse of the ghost_source map).
+template <typename T>
+__device__ __forceinline__ void write_ghost_images(const Geo &D, T *out, int c, int O,
+                                                   const T nv[kNPlane]) {
+    int gx[3], gy[3];
+    bool mxs[3], mys[3];
+    int ngx = 1, ngy = 1;
+    gx[0] = c;
+    mxs[0] = false;
+    gy[0] = O;
+    mys[0] = false;
+    const int nx = D.nx, ny = D.ny;
+    if (D.bc[0] == VLBM_BC_PERIODIC) {
+        if (c >= nx - 2) { gx[ngx] = c - nx; mxs[ngx++] = false; }
+        if (c <= 1) { gx[ngx] = c + nx; mxs[ngx++] = false; }
+    } else {
+        if (c == 0 && D.bc[0] == VLBM_BC_TRANSMISSIVE) {
+            gx[ngx] = -1; mxs[ngx++] = false;
+            gx[ngx] = -2; mxs[ngx++] = false;
+        }
+        if (c <= 1 && D.bc[0] == VLBM_BC_REFLECTIVE) { gx[ngx] = -1 - c; mxs[ngx++] = true; }
+        if (c == nx - 1 && D.bc[1] == VLBM_BC_TRANSMISSIVE) {
+            gx[ngx] = nx; mxs[ngx++] = false;
+            gx[ngx] = nx + 1; mxs[ngx++] = false;
+        }
+        if (c >= nx - 2 && D.bc[1] == VLBM_BC_REFLECTIVE) { gx[ngx] = 2 * nx - 1 - c; mxs[ngx++] = true; }
+    }
+    if (D.bc[2] == VLBM_BC_PERIODIC) {
+        if (O >= ny - 2) { gy[ngy] = O - ny; mys[ngy++] = false; }
+        if (O <= 1) { gy[ngy] = O + ny; mys[ngy++] = false; }
+    } else {
+        if (O == 0 && D.bc[2] == VLBM_BC_TRANSMISSIVE) {
+            gy[ngy] = -1; mys[ngy++] = false;
+            gy[ngy] = -2; mys[ngy++] = false;
+        }
+        if (O <= 1 && D.bc[2] == VLBM_BC_REFLECTIVE) { gy[ngy] = -1 - O; mys[ngy++] = true; }
+        if (O == ny - 1 && D.bc[3] == VLBM_BC_TRANSMISSIVE) {
+            gy[ngy] = ny; mys[ngy++] = false;
+            gy[ngy] = ny + 1; mys[ngy++] = false;
+        }
+        if (O >= ny - 2 && D.bc[3] == VLBM_BC_REFLECTIVE) { gy[ngy] = 2 * ny - 1 - O; mys[ngy++] = true; }
+    }
+    for (int a = 0; a < ngx; ++a)
+        for (int e = 0; e < ngy; ++e) {
+            if (a == 0 && e == 0) continue;
+            const long long d = (long long)(gy[e] + kOY) * D.pitch + (gx[a] + kOX);
+#pragma unroll
+            for (int q = 0; q < kNPlane; ++q) {
+                int src = q;
+                if (mxs[a] && q >= 4 && q < 12) src = q < 8 ? q + 4 : q - 4;   // u_1 <-> u_2
+                if (mys[e] && q >= 12) src = q < 16 ? q + 4 : q - 4;           // u_3 <-> u_4
+                T v = nv[src];
+                if ((mxs[a] && (q & 3) == 1) || (mys[e] && (q & 3) == 2)) v = -v;  // normal momentum
+                out[q * D.plane + d] = v;
+            }
+        }
+}
+
 template <typename T, int LIM>
 struct FusedCtx {
     FusedSmem<T> &S;
     const CUtensorMap *tmap;
-    const StepArgs<T> &A;
+    const Geo &D;
     const StepConsts<T> &k;
     T *__restrict__ out;
     Monitor<T> &mon;
     int b, zin;
-    uint32_t nissued, nconsumed;
-    // current item
+    uint32_t &nissued, &nconsumed;
     int xb, xpad, c, y0, y1, R1;
     // carried face state
     T xs_us[4], xs_df[4];   // x-face (c+1/2) of row R-1
@@ -65,6 +139,8 @@ struct FusedCtx {
     T rsy_prev;             // rho* of that y-face
     T mu2, nu2;             // bounds of row R-2 (own column)
     T thy_prev;             // theta of the y-face between rows R-3 and R-2
+    Hist<T> h1, h2;         // rows R-1, R-2 of the own column
+    T p3n[4];               // u_3 of row R-2 after the step (pulled from row R-3)
 
     __device__ __forceinline__ void issue(int row) {
         const int slot = nissued % kRawSlots;
@@ -75,14 +151,20 @@ struct FusedCtx {
 
     __device__ __forceinline__ void reset_state() {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) xs_us[q] = xs_df[q] = ys_us[q] = ys_df[q] = T(0);
+        for (int q = 0; q < 4; ++q) {
+            xs_us[q] = xs_df[q] = ys_us[q] = ys_df[q] = T(0);
+            h1.u[q] = h2.u[q] = T(1);
+            h1.g[q] = h2.g[q] = T(0);
+            h1.d3[q] = h2.d3[q] = T(0);
+            h1.d4[q] = h2.d4[q] = T(0);
+            p3n[q] = T(0);
+        }
         rsy_prev = mu2 = nu2 = thy_prev = T(0);
     }
 
-    // One row iteration; H0 receives row R, H1..H3 hold rows R-1..R-3.
-    // Returns false if a wait timed out (the CTA then stops).
-    __device__ __forceinline__ bool row(int R, Hist<T> &H0, const Hist<T> &H1, const Hist<T> &H2,
-                                        const Hist<T> &H3) {
+    // One row iteration; returns false if a wait timed out (the CTA then stops).
+    __device__ __forceinline__ bool row(int R) {
+        Hist<T> h0;
         // ---------------------------------------------------------------- P1
         const int slot = nconsumed % kRawSlots;
         const uint32_t par = (nconsumed / kRawSlots) & 1u;
@@ -99,16 +181,16 @@ struct FusedCtx {
         for (int q = 0; q < 4; ++q) {
             const T d1 = RN<T>::sub(M1[q], S.raw[slot][4 + q][b]);
             const T d2 = RN<T>::sub(M2[q], S.raw[slot][8 + q][b]);
-            H0.d3[q] = RN<T>::sub(M3[q], S.raw[slot][12 + q][b]);
-            H0.d4[q] = RN<T>::sub(M4[q], S.raw[slot][16 + q][b]);
-            H0.u[q] = u[q];
-            H0.g[q] = g[q];
+            h0.d3[q] = RN<T>::sub(M3[q], S.raw[slot][12 + q][b]);
+            h0.d4[q] = RN<T>::sub(M4[q], S.raw[slot][16 + q][b]);
+            h0.u[q] = u[q];
+            h0.g[q] = g[q];
             S.X[xs][q][b] = u[q];
             S.X[xs][4 + q][b] = f[q];
             S.X[xs][8 + q][b] = d1;
             S.X[xs][12 + q][b] = d2;
         }
-        const T rsy_new = face_star(H1.u[0], H1.g[0], u[0], g[0], k);  // y-face R - 1/2
+        const T rsy_new = face_star(h1.u[0], h1.g[0], u[0], g[0], k);  // y-face R - 1/2
         __syncthreads();                                                  // S1
         if (S.abort) return false;
         if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
@@ -118,7 +200,7 @@ struct FusedCtx {
         T mu1 = T(0), nu1 = T(0);
         if (LIM == VLBM_LIM_LMP || LIM == VLBM_LIM_RLMP) {
             const int rp = (R - 1) & 1;
-            const T v0 = H1.u[0], v1 = S.rsx[rp][bl], v2 = S.rsx[rp][b];
+            const T v0 = h1.u[0], v1 = S.rsx[rp][bl], v2 = S.rsx[rp][b];
             mu1 = fmin(fmin(fmin(v0, v1), fmin(v2, rsy_prev)), rsy_new);
             nu1 = fmax(fmax(fmax(v0, v1), fmax(v2, rsy_prev)), rsy_new);
             if (LIM == VLBM_LIM_RLMP) {  // Sec. 3.3.2
@@ -150,7 +232,7 @@ struct FusedCtx {
             tx = combine_theta(trx, xs_us, xs_df, k, nx64);
             ty = combine_theta(try_, ys_us, ys_df, k, ny64);
             // faces counted once: an x-face by the cell west of it, a y-face by the one south of it
-            const bool col_own = b >= 2 && b < 2 + kFOut && c < A.nx;
+            const bool col_own = b >= kFHalo && b < kFHalo + kFOut && c < D.nx;
             if (col_own && R - 1 >= y0 && R - 1 < y1) mon.fp64 += nx64;
             if (col_own && R - 2 >= y0 && R - 2 < y1) mon.fp64 += ny64;
         }
@@ -162,8 +244,8 @@ struct FusedCtx {
         for (int q = 0; q < 4; ++q) {
             xs_us[q] = face_star(S.X[xs][q][b], S.X[xs][4 + q][b], S.X[xs][q][br], S.X[xs][4 + q][br], k);
             xs_df[q] = face_dflux(S.X[xs][8 + q][b], S.X[xs][12 + q][br], k);
-            ys_us[q] = q == 0 ? rsy_new : face_star(H1.u[q], H1.g[q], H0.u[q], H0.g[q], k);
-            ys_df[q] = face_dflux(H1.d3[q], H0.d4[q], k);
+            ys_us[q] = q == 0 ? rsy_new : face_star(h1.u[q], h1.g[q], h0.u[q], h0.g[q], k);
+            ys_df[q] = face_dflux(h1.d3[q], h0.d4[q], k);
         }
         S.rsx[R & 1][b] = xs_us[0];
         rsy_prev = rsy_new;
@@ -173,114 +255,130 @@ struct FusedCtx {
         const int xo = O & 3, tp = O & 1;
         const T tw = S.thx[tp][bl], te = S.thx[tp][b];
         const T ts = thy_prev, tn = ty;
-        T un[4], p1[4], p2[4], p3[4], p4[4];
+        T nv[kNPlane];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const T M1W = maxwell_plus(S.X[xo][q][bl], S.X[xo][4 + q][bl], k);
             const T M2E = maxwell_minus(S.X[xo][q][br], S.X[xo][4 + q][br], k);
-            const T M3S = maxwell_plus(H3.u[q], H3.g[q], k);
-            const T M4N = maxwell_minus(H1.u[q], H1.g[q], k);
-            p1[q] = blend_pop(M1W, S.X[xo][8 + q][bl], tw);
-            p2[q] = blend_pop(M2E, S.X[xo][12 + q][br], te);
-            p3[q] = blend_pop(M3S, H3.d3[q], ts);
-            p4[q] = blend_pop(M4N, H1.d4[q], tn);
-            un[q] = blend_u(p1[q], p2[q], p3[q], p4[q], H2.u[q], tw, S.X[xo][12 + q][b], te,
-                            S.X[xo][8 + q][b], ts, H2.d4[q], tn, H2.d3[q], k);
+            const T M4N = maxwell_minus(h1.u[q], h1.g[q], k);
+            nv[4 + q] = blend_pop(M1W, S.X[xo][8 + q][bl], tw);
+            nv[8 + q] = blend_pop(M2E, S.X[xo][12 + q][br], te);
+            nv[12 + q] = p3n[q];
+            nv[16 + q] = blend_pop(M4N, h1.d4[q], tn);
+            nv[q] = blend_u(nv[4 + q], nv[8 + q], nv[12 + q], nv[16 + q], h2.u[q], tw, S.X[xo][12 + q][b],
+                            te, S.X[xo][8 + q][b], ts, h2.d4[q], tn, h2.d3[q], k);
+            // u_3 of row O + 1 after the step, pulled from row O with theta of y-face O + 1/2
+            p3n[q] = blend_pop(maxwell_plus(h2.u[q], h2.g[q], k), h2.d3[q], tn);
         }
         thy_prev = ty;
-        if (O >= y0 && O < y1 && b >= 2 && b < 2 + kFOut && c < A.nx) {
-            const long long d = (long long)(O + kOY) * A.pitch + (c + kOX);
+        if (O >= y0 && O < y1 && b >= kFHalo && b < kFHalo + kFOut && c < D.nx) {
+            const long long d = (long long)(O + kOY) * D.pitch + (c + kOX);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                out[q * A.plane + d] = un[q];
-                out[(4 + q) * A.plane + d] = p1[q];
-                out[(8 + q) * A.plane + d] = p2[q];
-                out[(12 + q) * A.plane + d] = p3[q];
-                out[(16 + q) * A.plane + d] = p4[q];
-            }
-            mon.add_cell(un, k.gamma, k.gm1);
+            for (int q = 0; q < kNPlane; ++q) out[q * D.plane + d] = nv[q];
+            if (c < 2 || c >= D.nx - 2 || O < 2 || O >= D.ny - 2) write_ghost_images(D, out, c, O, nv);
+            mon.add_cell(nv, k.gamma, k.gm1);
         }
+        // shift the register history
+        h2 = h1;
+        h1 = h0;
         return true;
-    }
-
-    // Wait (bounded) for this CTA's loads still in flight before it exits.
-    __device__ void drain() {
-        if (b == 0) {
-            while (nconsumed < nissued) {
-                const int slot = nconsumed % kRawSlots;
-                mbar_wait_bounded(&S.bar[slot], (nconsumed / kRawSlots) & 1u, 500000000ull);
-                ++nconsumed;
-            }
-        }
     }
 };
 
+// Wait (bounded) for this CTA's loads still in flight before it exits.
+template <typename T>
+__device__ void drain_loads(FusedSmem<T> &S, uint32_t nissued, uint32_t nconsumed) {
+    if (threadIdx.x == 0) {
+        while (nconsumed < nissued) {
+            const int slot = nconsumed % kRawSlots;
+            mbar_wait_bounded(&S.bar[slot], (nconsumed / kRawSlots) & 1u, 500000000ull);
+            ++nconsumed;
+        }
+    }
+}
+
 template <typename T, int LIM>
 __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
-    k_step_fused(const __grid_constant__ CUtensorMap tmap, StepArgs<T> A, int strips) {
-    DevCtl *C = A.ctl;
-    if (C->done) return;
+    k_step_fused(FusedBatchArgs<T> B) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     FusedSmem<T> &S = *reinterpret_cast<FusedSmem<T> *>(smem_raw);
-    const long long n = C->n;
-    const StepConsts<T> k = make_consts<T>(C->a, A.alpha, A.gamma, A.eps);
-    Monitor<T> mon;
-    mon.init();
-    FusedCtx<T, LIM> X{S, &tmap, A, k, (n & 1) ? A.buf0 : A.buf1, mon};
-    X.b = threadIdx.x;
-    X.zin = (n & 1) ? kNPlane : 0;
-    X.nissued = X.nconsumed = 0;
+    const int b = threadIdx.x;
     // TMA destinations must be 128-byte aligned; dynamic shared memory follows
     // the static block of the reductions, so check rather than assume.
     if (smem_addr(&S.raw[0][0][0]) & 127u) {
-        if (X.b == 0) atomicCAS(&C->status, 0, VLBM_E_UNSUPPORTED);
+        if (b == 0) atomicCAS(&B.insts[0].ctl->status, 0, VLBM_E_UNSUPPORTED);
         return;
     }
-    if (X.b == 0) {
+    if (b == 0) {
         for (int s = 0; s < kRawSlots; ++s) mbar_init(&S.bar[s], 1);
         S.abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
-    const int ny = A.ny;
-    const long long total = (long long)strips * ny;
-    const long long L0 = total * blockIdx.x / gridDim.x, L1 = total * (blockIdx.x + 1) / gridDim.x;
+    uint32_t nissued = 0, nconsumed = 0;
     bool ok = true;
-    for (long long Lc = L0; Lc < L1 && ok;) {
-        const int s = (int)(Lc / ny);
-        X.y0 = (int)(Lc % ny);
-        X.y1 = (int)(X.y0 + (L1 - Lc) < (long long)ny ? X.y0 + (L1 - Lc) : ny);
-        Lc += X.y1 - X.y0;
-        X.xb = kFOut * s - 2;
+    for (;;) {
+        if (b == 0) S.item = (int)atomicAdd(&B.bctl->work, 1u);
+        __syncthreads();
+        const int item = S.item;
+        __syncthreads();
+        if (item >= B.nitems) break;
+        const InstDesc<T> &D = B.insts[B.item_inst[item]];
+        DevCtl *C = D.ctl;
+        if (C->done) continue;
+        Geo geo;
+        geo.plane = D.plane;
+        geo.pitch = D.pitch;
+        geo.nx = D.nx;
+        geo.ny = D.ny;
+        for (int q = 0; q < 4; ++q) geo.bc[q] = D.bc[q];
+        const long long n = C->n;
+        const StepConsts<T> k = make_consts<T>(C->a, B.alpha, B.gamma, B.eps);
+        const int local = item - D.item0;
+        const int s = local % D.strips, ch = local / D.strips;
+        Monitor<T> mon;
+        mon.init();
+        FusedCtx<T, LIM> X{S, &D.tmap, geo, k, (n & 1) ? D.buf0 : D.buf1, mon, b, (n & 1) ? kNPlane : 0,
+                           nissued, nconsumed};
+        X.y0 = ch * D.chunk;
+        X.y1 = X.y0 + D.chunk < D.ny ? X.y0 + D.chunk : D.ny;
+        X.xb = kFOut * s - kFHalo;
         X.xpad = X.xb + kOX;
-        X.c = X.xb + X.b;
+        X.c = X.xb + b;
         const int R0 = X.y0 - 2;
         X.R1 = X.y1 + 1;
-        if (X.b == 0)
+        if (b == 0)
             for (int r = R0; r < R0 + kRawSlots && r <= X.R1; ++r) X.issue(r);
         X.reset_state();
-        Hist<T> h0, h1, h2, h3;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            h0.u[q] = h1.u[q] = h2.u[q] = h3.u[q] = T(1);
-            h0.g[q] = h1.g[q] = h2.g[q] = h3.g[q] = T(0);
-            h0.d3[q] = h1.d3[q] = h2.d3[q] = h3.d3[q] = T(0);
-            h0.d4[q] = h1.d4[q] = h2.d4[q] = h3.d4[q] = T(0);
-        }
-        for (int R = R0; R <= X.R1 && ok; R += 4) {
-            ok = X.row(R, h0, h1, h2, h3);
-            if (ok && R + 1 <= X.R1) ok = X.row(R + 1, h3, h0, h1, h2);
-            if (ok && R + 2 <= X.R1) ok = X.row(R + 2, h2, h3, h0, h1);
-            if (ok && R + 3 <= X.R1) ok = X.row(R + 3, h1, h2, h3, h0);
+        for (int R = R0; R <= X.R1 && ok; ++R) ok = X.row(R);
+        if (!ok) break;
+        // the item's monitors go to its grid; the CTA finishing the grid's last item
+        // ends that grid's step
+        block_publish(mon, C);
+        if (last_block(C, (unsigned)D.nitems)) {
+            if (b == 0) finalize_step(C);
         }
     }
     if (!ok) {
-        X.drain();
-        if (X.b == 0) atomicCAS(&C->status, 0, VLBM_E_TIMEOUT);
+        drain_loads(S, nissued, nconsumed);
+        if (b == 0) atomicCAS(&B.insts[0].ctl->status, 0, VLBM_E_TIMEOUT);
+        // keep fetching so that the counter reaches the end before the reset below
+        for (;;) {
+            if (b == 0) S.item = (int)atomicAdd(&B.bctl->work, 1u);
+            __syncthreads();
+            const int item = S.item;
+            __syncthreads();
+            if (item >= B.nitems) break;
+        }
     }
-    block_publish(mon, C);
-    if (last_block(C, gridDim.x)) {
-        if (X.b == 0) finalize_step(C);
+    // the last CTA to leave resets the work counter for the next launch
+    if (b == 0) {
+        __threadfence();
+        if (atomicAdd(&B.bctl->ctas_done, 1u) == gridDim.x - 1) {
+            B.bctl->work = 0u;
+            B.bctl->ctas_done = 0u;
+            __threadfence();
+        }
     }
 }
 

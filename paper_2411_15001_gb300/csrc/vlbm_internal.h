@@ -11,12 +11,13 @@ namespace vlbm {
 
 // Padded plane layout. Cell (i, j), -2 <= i < nx+2, -2 <= j < ny+2, of plane q
 // in a state buffer lives at q * plane + (j + kOY) * pitch + (i + kOX).
-// Columns 0, 1 and nx+2, nx+3 of a padded row hold the two ghost layers of the
-// x sides, rows 0, 1 and ny+2, ny+3 those of the y sides. With kOX = 2 the
-// row-marching kernel's TMA boxes, which start two cells left of a strip of
-// 124 output columns (interior column 124 s - 2, padded column 124 s), begin on
-// a 16-byte boundary; pitch is a multiple of 32 elements.
-constexpr int kOX = 2;
+// Padded columns 6, 7 and nx+8, nx+9 hold the two ghost layers of the x sides,
+// rows 0, 1 and ny+2, ny+3 those of the y sides. kOX = 8 and a pitch that is a
+// multiple of 32 elements put interior column 0 of every row on a 32-byte
+// sector boundary: the row-marching kernel writes strips of 120 columns that
+// start on sector boundaries, and its TMA boxes (four columns left of a strip)
+// start on 16-byte boundaries.
+constexpr int kOX = 8;
 constexpr int kOY = 2;
 constexpr int kNPlane = 20;   // u (4) and u_1..u_4 (4 each); u_5 is never stored
 
@@ -28,6 +29,7 @@ struct Layout {
     int elem;           // bytes per element (4 or 8)
     size_t buf_bytes;   // bytes of one 20-plane buffer
     size_t ctl_offset;  // byte offset of the control block in the workspace
+    size_t desc_offset; // byte offset of the row-marching kernel's descriptor block
     size_t total;       // workspace bytes
 };
 
@@ -94,6 +96,33 @@ struct DevCtl {
 
 static_assert(sizeof(DevCtl) == 264, "bench.py reads the control block size");
 
+// One grid as the row-marching kernel sees it (device memory, 64-byte aligned).
+template <typename T>
+struct InstDesc {
+    CUtensorMap tmap;     // 3D view [40 planes][ny + 4 rows][pitch] of both state buffers
+    T *buf0, *buf1;
+    long long plane;
+    int pitch, nx, ny;
+    int bc[4];
+    int strips, chunk;    // strips of 120 columns, chunks of `chunk` rows
+    int item0, nitems;    // this grid's work items in the launch
+    DevCtl *ctl;
+};
+
+// Work counter of one row-marching launch; reset by the last CTA to leave.
+struct BatchCtl {
+    unsigned int work, ctas_done;
+};
+
+template <typename T>
+struct FusedBatchArgs {
+    const InstDesc<T> *insts;
+    const int *item_inst;  // grid of every work item
+    int nitems;
+    BatchCtl *bctl;
+    double gamma, alpha, eps;
+};
+
 template <typename T>
 struct StepArgs {
     T *buf0, *buf1;     // the two 20-plane state buffers
@@ -115,12 +144,17 @@ template <typename T> cudaError_t launch_init(const StepArgs<T> &a, const T *rho
                                               const T *E, cudaStream_t s);
 template <typename T> cudaError_t launch_ghosts(const StepArgs<T> &a, cudaStream_t s);
 template <typename T> cudaError_t launch_step_simple(const StepArgs<T> &a, cudaStream_t s);
-// Row-marching kernel: strips of 124 columns, `grid` persistent CTAs.
-template <typename T> cudaError_t launch_step_fused(const StepArgs<T> &a, const CUtensorMap &tm, int strips,
-                                                   int grid, cudaStream_t s);
+// Row-marching kernel over the work items of one or more grids, `grid` persistent CTAs.
+template <typename T> cudaError_t launch_step_fused(const FusedBatchArgs<T> &a, int limiter, int grid,
+                                                   cudaStream_t s);
 template <typename T> int fused_occupancy(int limiter);   // CTAs per SM of the fused kernel
-constexpr int kFusedOut = 124;                             // output columns per strip
+// Kernel function and dynamic shared memory of the fused kernel, for graph nodes.
+template <typename T> const void *fused_kernel_fn(int limiter, size_t *smem);
+bool encode_state_tmap(CUtensorMap *out, void *base, const Layout &L);
+constexpr int kFusedOut = 120;                             // output columns per strip
 constexpr int kFusedBox = 128;                             // TMA box width (columns)
+constexpr int kFusedMinChunk = 16;                         // rows per work item, bounds
+constexpr int kFusedMaxChunk = 64;
 template <typename T> cudaError_t launch_moments(const StepArgs<T> &a, T *rho, T *mom, T *E,
                                                  cudaStream_t s);
 template <typename T> cudaError_t launch_save(const StepArgs<T> &a, void *dst, cudaStream_t s);

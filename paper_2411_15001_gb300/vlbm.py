@@ -47,6 +47,14 @@ class vlbm_step_result(ctypes.Structure):
                 ("nonfinite_cells", ctypes.c_int64), ("theta_p_fp64_faces", ctypes.c_int64)]
 
 
+class vlbm_batch_tuning(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("items", ctypes.c_int32), ("ctas", ctypes.c_int32)]
+
+
+ORDER_LPT, ORDER_INDEX = 0, 1
+
+
 class VLBMError(RuntimeError):
     def __init__(self, code: int, detail: str = ""):
         self.code = code
@@ -79,6 +87,22 @@ _SIGS = {
     "vlbm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(vlbm_grid), _D, _D, _I32, _I32,
                                          ctypes.POINTER(vlbm_opts), _P, _P,
                                          ctypes.POINTER(vlbm_step_result), _P]),
+    "vlbm_adjoint_scratch_bytes": (_SZ, [_P, _I64, _I32]),
+    "vlbm_rollout": (ctypes.c_int, [_P, _I64, _I32, _P, _SZ]),
+    "vlbm_adjoint": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P, _SZ]),
+    "vlbm_batch_workspace_bytes": (_SZ, [_I32, ctypes.POINTER(vlbm_grid), _I32]),
+    "vlbm_batch_init": (ctypes.c_int, [_I32, ctypes.POINTER(vlbm_grid), _D, _I32, _I32,
+                                       ctypes.POINTER(vlbm_opts), _P, _SZ, _P, ctypes.POINTER(_P)]),
+    "vlbm_batch_set_conserved": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "vlbm_batch_step": (ctypes.c_int, [_P, _I64]),
+    "vlbm_batch_moments": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "vlbm_batch_save": (ctypes.c_int, [_P, _I32, _P]),
+    "vlbm_batch_monitors": (ctypes.c_int, [_P, _I32, ctypes.POINTER(vlbm_monitor_t)]),
+    "vlbm_batch_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(vlbm_batch_tuning)]),
+    "vlbm_batch_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(vlbm_batch_tuning)]),
+    "vlbm_batch_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(vlbm_batch_tuning), ctypes.POINTER(_D)]),
+    "vlbm_batch_destroy": (None, [_P]),
+    "vlbm_batch_last_error": (ctypes.c_char_p, [_P]),
     "vlbm_destroy": (None, [_P]),
     "vlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vlbm_last_error_detail": (ctypes.c_int, [_P, ctypes.c_char_p, _SZ]),
@@ -167,6 +191,80 @@ def vlbm_step_noalloc(grid, gamma, a, limiter, precision, opts, d_in, d_out, str
                                 ctypes.byref(opts) if opts is not None else None, d_in, d_out,
                                 ctypes.byref(r), stream)
     return rc, r
+
+
+def vlbm_adjoint_scratch_bytes(s, nsteps: int, ckpt_every: int) -> int:
+    return int(_lib.vlbm_adjoint_scratch_bytes(s, nsteps, ckpt_every))
+
+
+def vlbm_rollout(s, nsteps: int, ckpt_every: int, d_scratch, scratch_bytes: int) -> int:
+    return _lib.vlbm_rollout(s, nsteps, ckpt_every, d_scratch, scratch_bytes)
+
+
+def vlbm_adjoint(s, d_u0, nsteps: int, ckpt_every: int, d_dLduN, d_dLdu0, d_scratch, scratch_bytes: int) -> int:
+    return _lib.vlbm_adjoint(s, d_u0, nsteps, ckpt_every, d_dLduN, d_dLdu0, d_scratch, scratch_bytes)
+
+
+def vlbm_batch_workspace_bytes(grids, precision) -> int:
+    arr = (vlbm_grid * len(grids))(*grids)
+    return int(_lib.vlbm_batch_workspace_bytes(len(grids), arr, precision))
+
+
+def vlbm_batch_init(grids, gamma, limiter, precision, opts, d_workspace, workspace_bytes, stream):
+    arr = (vlbm_grid * len(grids))(*grids)
+    out = _P()
+    rc = _lib.vlbm_batch_init(len(grids), arr, gamma, limiter, precision,
+                              ctypes.byref(opts) if opts is not None else None, d_workspace,
+                              workspace_bytes, stream, ctypes.byref(out))
+    return rc, out
+
+
+def vlbm_batch_set_conserved(b, i, d_rho, d_mom, d_E) -> int:
+    return _lib.vlbm_batch_set_conserved(b, i, d_rho, d_mom, d_E)
+
+
+def vlbm_batch_step(b, nsteps: int) -> int:
+    return _lib.vlbm_batch_step(b, nsteps)
+
+
+def vlbm_batch_moments(b, i, d_rho, d_mom, d_E) -> int:
+    return _lib.vlbm_batch_moments(b, i, d_rho, d_mom, d_E)
+
+
+def vlbm_batch_save(b, i, d_dst) -> int:
+    return _lib.vlbm_batch_save(b, i, d_dst)
+
+
+def vlbm_batch_monitors(b, i):
+    m = vlbm_monitor_t()
+    rc = _lib.vlbm_batch_monitors(b, i, ctypes.byref(m))
+    return rc, m
+
+
+def vlbm_batch_get_tuning(b):
+    t = vlbm_batch_tuning()
+    rc = _lib.vlbm_batch_get_tuning(b, ctypes.byref(t))
+    return rc, t
+
+
+def vlbm_batch_set_tuning(b, t) -> int:
+    return _lib.vlbm_batch_set_tuning(b, ctypes.byref(t))
+
+
+def vlbm_batch_autotune(b, trial_steps: int):
+    t = vlbm_batch_tuning()
+    ms = _D()
+    rc = _lib.vlbm_batch_autotune(b, trial_steps, ctypes.byref(t), ctypes.byref(ms))
+    return rc, t, ms.value
+
+
+def vlbm_batch_destroy(b) -> None:
+    _lib.vlbm_batch_destroy(b)
+
+
+def vlbm_batch_last_error(b) -> str:
+    r = _lib.vlbm_batch_last_error(b)
+    return r.decode() if r else ""
 
 
 def vlbm_destroy(s) -> None:
@@ -290,6 +388,28 @@ class VLBM:
         _check(rc, self._s)
         return ms, n
 
+    def adjoint_scratch(self, nsteps: int, ckpt_every: int):
+        """Device scratch for vlbm_rollout / vlbm_adjoint with these arguments."""
+        n = vlbm_adjoint_scratch_bytes(self._s, int(nsteps), int(ckpt_every))
+        if n == 0:
+            raise VLBMError(E_INVAL, "invalid rollout arguments")
+        return self.torch.empty(n, dtype=self.torch.uint8, device=self.device)
+
+    def rollout(self, nsteps: int, ckpt_every: int, scratch):
+        """Advance nsteps from the state set_conserved left, checkpointing into scratch."""
+        _check(vlbm_rollout(self._s, int(nsteps), int(ckpt_every), scratch.data_ptr(), scratch.numel()),
+               self._s)
+
+    def adjoint(self, dLduN, nsteps: int, ckpt_every: int, scratch, u0=None):
+        """dL/du_0 (4, ny, nx) from dL/du^N (4, ny, nx): planes rho, m1, m2, E.
+
+        With u0 the call sets the state from it and runs the rollout itself; without
+        it, the checkpoints of the preceding rollout (same arguments) are used."""
+        g = self.torch.empty((4, self.ny, self.nx), dtype=self.dtype, device=self.device)
+        _check(vlbm_adjoint(self._s, self._ptr(u0), int(nsteps), int(ckpt_every), self._ptr(dLduN),
+                            g.data_ptr(), scratch.data_ptr(), scratch.numel()), self._s)
+        return g
+
     def close(self):
         if getattr(self, "_s", None):
             vlbm_destroy(self._s)
@@ -300,3 +420,137 @@ class VLBM:
             self.close()
         except Exception:
             pass
+
+
+class VLBMBatch:
+    """Independent grids of uneven sizes advanced together (vlbm_batch_*)."""
+
+    def __init__(self, grids, gamma: float = 1.4, limiter=LIM_PP, precision=FP32,
+                 alpha: float = 0.5, eps: float = 1e-16, device=None, stream=None):
+        """grids: sequence of (nx, ny, dx, bc) tuples."""
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        if isinstance(limiter, str):
+            limiter = LIMITERS[limiter.lower()]
+        self.shapes = [(int(g[0]), int(g[1])) for g in grids]
+        self.precision = precision
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        self._grids = [vlbm_grid(int(g[0]), int(g[1]), float(g[2]), (ctypes.c_int32 * 4)(*g[3]))
+                       for g in grids]
+        self.opts = vlbm_opts(alpha, eps, 0, 0)
+        nbytes = vlbm_batch_workspace_bytes(self._grids, precision)
+        if nbytes == 0:
+            raise VLBMError(E_INVAL, "invalid grids")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        rc, self._b = vlbm_batch_init(self._grids, gamma, limiter, precision, self.opts,
+                                      self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+        if rc != OK:
+            raise VLBMError(rc, vlbm_batch_last_error(None))
+
+    def _chk(self, rc):
+        if rc != OK:
+            raise VLBMError(rc, vlbm_batch_last_error(self._b))
+
+    def set_conserved(self, i, rho, mom, E):
+        for t in (rho, mom, E):
+            if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+                raise ValueError("tensor must be contiguous, on the batch's device, in its dtype")
+        self._chk(vlbm_batch_set_conserved(self._b, i, rho.data_ptr(), mom.data_ptr(), E.data_ptr()))
+
+    def step(self, nsteps: int = 1):
+        self._chk(vlbm_batch_step(self._b, int(nsteps)))
+
+    def moments(self, i):
+        nx, ny = self.shapes[i]
+        t = self.torch
+        rho = t.empty((ny, nx), dtype=self.dtype, device=self.device)
+        mom = t.empty((2, ny, nx), dtype=self.dtype, device=self.device)
+        E = t.empty((ny, nx), dtype=self.dtype, device=self.device)
+        self._chk(vlbm_batch_moments(self._b, i, rho.data_ptr(), mom.data_ptr(), E.data_ptr()))
+        return rho, mom, E
+
+    def state_planes(self, i):
+        nx, ny = self.shapes[i]
+        el = 8 if self.precision == FP64 else 4
+        buf = self.torch.empty(64 + 20 * nx * ny * el, dtype=self.torch.uint8, device=self.device)
+        self._chk(vlbm_batch_save(self._b, i, buf.data_ptr()))
+        return buf[64:].view(self.dtype).view(20, ny, nx)
+
+    def monitors(self, i) -> dict:
+        rc, m = vlbm_batch_monitors(self._b, i)
+        return {"status": m.status, "n": m.n, "t": m.t, "a": m.a, "lambda": m.lambda_,
+                "bad_cells": m.bad_cells, "nonfinite_cells": m.nonfinite_cells,
+                "first_bad_step": m.first_bad_step, "min_rho": m.min_rho, "sum": list(m.sum),
+                "theta_p_fp64_faces": m.theta_p_fp64_faces, "done": m.done}
+
+    def tuning(self) -> dict:
+        rc, t = vlbm_batch_get_tuning(self._b)
+        self._chk(rc)
+        return {"chunk": t.chunk, "ctas_per_sm": t.ctas_per_sm, "order": t.order, "items": t.items,
+                "ctas": t.ctas}
+
+    def set_tuning(self, chunk, ctas_per_sm, order=ORDER_LPT):
+        self._chk(vlbm_batch_set_tuning(self._b, vlbm_batch_tuning(chunk, ctas_per_sm, order, 0, 0)))
+
+    def autotune(self, trial_steps: int = 3):
+        rc, t, ms = vlbm_batch_autotune(self._b, int(trial_steps))
+        self._chk(rc)
+        return {"chunk": t.chunk, "ctas_per_sm": t.ctas_per_sm, "order": t.order, "items": t.items,
+                "ctas": t.ctas, "ms_per_step": ms}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            vlbm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _rollout_function():
+    import torch
+
+    class VLBMRollout(torch.autograd.Function):
+        """u^N = rollout(u_0) through `nsteps` steps of a VLBM solver, differentiable in u_0.
+
+        forward(rho, mom, E, solver, nsteps, ckpt_every) -> (rho^N, mom^N, E^N); the
+        backward pass is the library's adjoint (vlbm_adjoint) over the checkpoints
+        the forward pass stored. a^n is held as the forward run produced it."""
+
+        @staticmethod
+        def forward(ctx, rho, mom, E, solver, nsteps, ckpt_every):
+            scratch = solver.adjoint_scratch(nsteps, ckpt_every)
+            solver.set_conserved(rho.contiguous(), mom.contiguous(), E.contiguous())
+            solver.rollout(nsteps, ckpt_every, scratch)
+            ctx.solver, ctx.nsteps, ctx.every, ctx.scratch = solver, nsteps, ckpt_every, scratch
+            return solver.moments()
+
+        @staticmethod
+        def backward(ctx, g_rho, g_mom, g_E):
+            s = ctx.solver
+            t = torch
+            z = lambda g, shape: g if g is not None else t.zeros(shape, dtype=s.dtype, device=s.device)
+            dLduN = t.cat([z(g_rho, (s.ny, s.nx)).reshape(1, s.ny, s.nx),
+                           z(g_mom, (2, s.ny, s.nx)).reshape(2, s.ny, s.nx),
+                           z(g_E, (s.ny, s.nx)).reshape(1, s.ny, s.nx)]).to(s.dtype).contiguous()
+            g = s.adjoint(dLduN, ctx.nsteps, ctx.every, ctx.scratch)
+            ctx.scratch = None
+            return g[0], g[1:3], g[3], None, None, None
+
+    return VLBMRollout
+
+
+def __getattr__(name):
+    if name == "VLBMRollout":
+        cls = _rollout_function()
+        globals()["VLBMRollout"] = cls
+        return cls
+    raise AttributeError(name)

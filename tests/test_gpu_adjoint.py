@@ -1,0 +1,267 @@
+"""Adjoint of the rollout (vlbm_rollout / vlbm_adjoint) against central finite
+differences of the forward map (needs a GB300).
+
+The loss is L = 1/2 sum w (u^N - u_target)^2 over the conserved planes, so
+dL/du^N = w (u^N - u_target). The kinetic speed is fixed (a state made with
+lambda > 0, a = 4 lambda), so the forward map is the one the adjoint transposes.
+Finite differences: central, h = 1e-6 max(1, |u|) on smooth data, the loss
+difference formed cell by cell; a difference is compared with the adjoint at a
+relative tolerance taken against max(|g_i|, 1e-2 rms(g)) so that near-zero
+entries are judged on the gradient's scale.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_15001_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_15001_gb300 import vlbm as V  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _lam0(p):
+    cfg = O.Config(p.nx, p.ny, p.bc, 0, p.gamma, 0.5, 1e-16)
+    return O.max_speed(cfg, O.new_state(p.conserved()))
+
+
+def _solver(p, limiter, prec, lam, kernel=V.KERNEL_AUTO, eps=1e-16):
+    return V.VLBM(p.nx, p.ny, p.dx, bc=(0, 0, 0, 0), gamma=p.gamma, lam=lam, limiter=limiter,
+                  precision=prec, eps=eps, kernel=kernel, device=DEV)
+
+
+def _final(s, u0, nsteps):
+    s.set_conserved(u0[0].contiguous(), u0[1:3].contiguous(), u0[3].contiguous())
+    s.step(nsteps)
+    rho, mom, E = s.moments()
+    return torch.cat([rho[None], mom, E[None]])
+
+
+def _setup(p, t_final, seed=5):
+    rng = np.random.default_rng(seed)
+    w = torch.tensor(rng.uniform(0.5, 1.5, size=(4, p.ny, p.nx)), dtype=torch.float64, device=DEV)
+    tgt = W.isentropic_vortex(p.nx, t=t_final).conserved() if p.name.startswith("vortex") else \
+        p.conserved() * 0.97
+    return w, torch.tensor(tgt, dtype=torch.float64, device=DEV)
+
+
+def _loss_diff(up, dn, w, tgt):
+    """L(up) - L(dn) as 1/2 sum w (up - dn)(up + dn - 2 tgt): the difference is formed
+    cell by cell before the sum, so the sum's round-off is relative to the difference
+    (summing the two losses first loses ~1e-13 L to cancellation, which / 2h is the
+    size of a small gradient entry)."""
+    up, dn = up.double(), dn.double()
+    return 0.5 * float((w * (up - dn) * (up + dn - 2.0 * tgt)).sum())
+
+
+def _adjoint(s, u0, nsteps, every, w, tgt):
+    """(u^N, dL/du_0) through VLBMRollout."""
+    rho = u0[0].clone().requires_grad_(True)
+    mom = u0[1:3].clone().requires_grad_(True)
+    E = u0[3].clone().requires_grad_(True)
+    rN, mN, EN = V.VLBMRollout.apply(rho, mom, E, s, nsteps, every)
+    uN = torch.cat([rN[None], mN, EN[None]])
+    L = 0.5 * (w.to(uN.dtype) * (uN - tgt.to(uN.dtype)) ** 2).sum()
+    L.backward()
+    g = torch.cat([rho.grad[None], mom.grad, E.grad[None]]).double()
+    return uN.detach(), g
+
+
+def _fd_check(s, u0, nsteps, w, tgt, g, cells, h_rel=1e-6, tol=1e-5):
+    scale = 1e-2 * float(torch.sqrt((g * g).mean()))
+    worst = 0.0
+    for (j, i) in cells:
+        for c in range(4):
+            h = h_rel * max(1.0, abs(float(u0[c, j, i])))
+            up = u0.clone()
+            up[c, j, i] += h
+            dn = u0.clone()
+            dn[c, j, i] -= h
+            fd = _loss_diff(_final(s, up, nsteps), _final(s, dn, nsteps), w, tgt) / (2 * h)
+            ad = float(g[c, j, i])
+            err = abs(fd - ad) / max(abs(ad), scale)
+            worst = max(worst, err)
+            assert err <= tol, (j, i, c, fd, ad, err)
+    return worst
+
+
+def _cells(p, n, seed):
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(p.ny)), int(rng.integers(p.nx))) for _ in range(n)]
+
+
+@pytest.mark.parametrize("kernel", [V.KERNEL_SIMPLE, V.KERNEL_FUSED])
+@pytest.mark.parametrize("limiter", [V.LIM_FIRST_ORDER, V.LIM_NONE, V.LIM_PP])
+def test_adjoint_fd_fp64_vortex(limiter, kernel):
+    p = W.vortex_with_bumps(48)
+    lam = 1.05 * _lam0(p)
+    nsteps, every = 60, 16            # a ragged last segment of 12 steps
+    tN = nsteps * p.dx / (4.0 * lam)
+    w, tgt = _setup(p, tN)
+    s = _solver(p, limiter, V.FP64, lam, kernel)
+    u0 = torch.tensor(p.conserved(), dtype=torch.float64, device=DEV)
+    uN, g = _adjoint(s, u0, nsteps, every, w, tgt)
+    assert torch.equal(uN, _final(s, u0, nsteps))       # rollout = plain stepping, bit for bit
+    _fd_check(s, u0, nsteps, w, tgt, g, _cells(p, 12, 7))
+    s.close()
+
+
+def _expansion(nx=40, ny=36, p0=1e-2):
+    """Periodic strong expansion: v1 = +-2 tanh profiles pulling the gas apart around
+    x = 1/2 (and colliding at x = 0), rho modulated in x and y, p = 1e-2. The PP
+    limiter's internal-energy bound is active on hundreds of faces from the first
+    step (theta down to ~0.003 by step 15)."""
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) / nx, (np.arange(ny) + 0.5) / ny)   # unit periods
+    rho = 1.0 + 0.5 * np.sin(2 * np.pi * Y) * np.cos(2 * np.pi * X)
+    v1 = 2.0 * np.tanh((X - 0.5) / 0.05) * np.where(np.abs(X - 0.5) < 0.25, 1.0, -1.0)
+    v2 = 0.3 * np.sin(2 * np.pi * Y)
+    cons = np.stack(W.primitive_to_conserved(rho, v1, v2, np.full((ny, nx), p0)))
+    return cons, 1.0 / nx
+
+
+def test_adjoint_fd_fp64_limiter_active():
+    """PP limiter active (theta < 1 on many faces, the internal-energy bound): the
+    adjoint follows theta's active branch through 20 steps."""
+    cons, dx = _expansion()
+    ny, nx = cons.shape[1:]
+    cfg = O.Config(nx, ny, (0, 0, 0, 0), O.LIM_PP, 1.4, 0.5, 1e-13)
+    lam = 1.05 * O.max_speed(cfg, O.new_state(cons))
+    a = O.kinetic_speed(lam, 0.5)
+    for k in (1, 10):
+        st = O.run(cfg, cons, dx, nsteps=k, lam_fixed=lam)["state"]
+        _, dbg = O.step(cfg, st, a, debug=True)
+        th = np.concatenate([dbg["theta_x"].ravel(), dbg["theta_y"].ravel()])
+        assert (th < 1.0).sum() > 100
+    nsteps, every = 20, 8
+    p = W.Problem("expansion", nx, ny, dx, 0.0, 0.0, cons[0], cons[1], cons[2], cons[3])
+    w, tgt = _setup(p, 0.0)
+    s = _solver(p, V.LIM_PP, V.FP64, lam, eps=1e-13)
+    u0 = torch.tensor(cons, dtype=torch.float64, device=DEV)
+    _, g = _adjoint(s, u0, nsteps, every, w, tgt)
+    # cells in the expansion fan and at the collision, where the limiter acts
+    cells = [(ny // 2, nx // 2), (ny // 2 - 1, nx // 2 + 1), (3, nx // 2 - 2), (ny // 2, nx - 1),
+             (ny - 2, 0), (10, nx // 4), (20, 3 * nx // 4)]
+    _fd_check(s, u0, nsteps, w, tgt, g, cells, h_rel=1e-7, tol=1e-4)
+    s.close()
+
+
+def test_adjoint_zero_steps_and_linearity():
+    p = W.vortex_with_bumps(32)
+    lam = 1.05 * _lam0(p)
+    s = _solver(p, V.LIM_PP, V.FP64, lam)
+    u0 = torch.tensor(p.conserved(), dtype=torch.float64, device=DEV)
+    scratch = s.adjoint_scratch(0, 4)
+    gN = torch.randn((4, p.ny, p.nx), dtype=torch.float64, device=DEV, generator=torch.Generator(DEV).manual_seed(1))
+    g0 = s.adjoint(gN, 0, 4, scratch, u0=u0)
+    assert torch.equal(g0, gN)            # N = 0: u^0 = u_0, the identity
+    nsteps, every = 9, 4
+    scratch = s.adjoint_scratch(nsteps, every)
+    g1 = s.adjoint(gN, nsteps, every, scratch, u0=u0)
+    g2 = s.adjoint(2.0 * gN, nsteps, every, scratch)        # reuses the checkpoints
+    g3 = s.adjoint(gN, nsteps, 1, s.adjoint_scratch(nsteps, 1), u0=u0)
+    assert torch.equal(g2, 2.0 * g1)      # the transpose is linear in the cotangent
+    assert torch.equal(g3, g1)            # independent of the checkpoint interval
+    s.close()
+
+
+def test_adjoint_dynamic_a_matches_fixed_on_uniform_flow():
+    """A uniform state keeps lambda constant, so the recorded dynamic a^n equals the
+    fixed speed 4 lambda(u_0) and both adjoints must agree (to round-off)."""
+    nx, ny = 40, 24
+    rho = np.full((ny, nx), 0.8)
+    v1, v2, pr = np.full((ny, nx), 0.3), np.full((ny, nx), -0.2), np.full((ny, nx), 0.9)
+    cons = W.primitive_to_conserved(rho, v1, v2, pr)
+    u0 = torch.tensor(np.stack(cons), dtype=torch.float64, device=DEV)
+    gN = torch.randn((4, ny, nx), dtype=torch.float64, device=DEV, generator=torch.Generator(DEV).manual_seed(3))
+    dyn = V.VLBM(nx, ny, 0.1, limiter=V.LIM_PP, precision=V.FP64, device=DEV)
+    dyn.set_conserved(u0[0].contiguous(), u0[1:3].contiguous(), u0[3].contiguous())
+    lam = dyn.monitors()["lambda"]
+    fix = V.VLBM(nx, ny, 0.1, lam=lam, limiter=V.LIM_PP, precision=V.FP64, device=DEV)
+    ga = dyn.adjoint(gN, 12, 5, dyn.adjoint_scratch(12, 5), u0=u0)
+    gb = fix.adjoint(gN, 12, 5, fix.adjoint_scratch(12, 5), u0=u0)
+    # the uniform state may drift by an ulp per step, and a^n with it
+    assert abs(dyn.monitors()["a"] / fix.monitors()["a"] - 1.0) < 1e-13
+    assert torch.allclose(ga, gb, rtol=1e-12, atol=1e-12 * float(gb.abs().max()))
+    dyn.close()
+    fix.close()
+
+
+def test_adjoint_against_oracle_fd():
+    """GPU FP64 adjoint against central differences of the oracle (64^2, 100 steps)."""
+    p = W.vortex_with_bumps(64)
+    lam = 1.05 * _lam0(p)
+    nsteps, every = 100, 25
+    a = O.kinetic_speed(lam, 0.5)
+    w, tgt = _setup(p, nsteps * p.dx / a)
+    s = _solver(p, V.LIM_PP, V.FP64, lam)
+    u0 = torch.tensor(p.conserved(), dtype=torch.float64, device=DEV)
+    _, g = _adjoint(s, u0, nsteps, every, w, tgt)
+    s.close()
+    cfg = O.Config(p.nx, p.ny, (0, 0, 0, 0), O.LIM_PP, p.gamma, 0.5, 1e-16)
+    wn, tn, c0 = w.cpu().numpy(), tgt.cpu().numpy(), p.conserved()
+
+    def uN(c):
+        return O.run(cfg, c, p.dx, nsteps=nsteps, lam_fixed=lam)["state"][:4]
+
+    gn = g.cpu().numpy()
+    scale = 1e-2 * float(np.sqrt((gn * gn).mean()))
+    for (j, i) in _cells(p, 20, 2):
+        for c in range(4):
+            h = 1e-6 * max(1.0, abs(c0[c, j, i]))
+            up, dn = c0.copy(), c0.copy()
+            up[c, j, i] += h
+            dn[c, j, i] -= h
+            a_, b_ = uN(up), uN(dn)
+            fd = 0.5 * float((wn * (a_ - b_) * (a_ + b_ - 2.0 * tn)).sum()) / (2 * h)
+            err = abs(fd - gn[c, j, i]) / max(abs(gn[c, j, i]), scale)
+            assert err <= 1e-5, (j, i, c, fd, gn[c, j, i])
+
+
+def test_adjoint_full_size_vortex_with_bumps():
+    """512^2 vortex with 8 bumps, 500 steps, checkpoints every 50: the FP32 adjoint
+    against the FP64 adjoint (<= 1e-3 of max |g|), and the FP64 adjoint against
+    central differences of the FP64 GPU forward map on 20 cells (seed 2) x 4."""
+    p = W.vortex_with_bumps(512)
+    lam = 1.05 * _lam0(p)
+    nsteps, every = 500, 50
+    w, tgt = _setup(p, nsteps * p.dx / (4.0 * lam))
+    s64 = _solver(p, V.LIM_PP, V.FP64, lam)
+    u64 = torch.tensor(p.conserved(), dtype=torch.float64, device=DEV)
+    _, g64 = _adjoint(s64, u64, nsteps, every, w, tgt)
+    s32 = _solver(p, V.LIM_PP, V.FP32, lam)
+    _, g32 = _adjoint(s32, u64.float(), nsteps, every, w, tgt)
+    s32.close()
+    rel = float((g32 - g64).abs().max() / g64.abs().max())
+    assert rel <= 1e-3, rel
+    _fd_check(s64, u64, nsteps, w, tgt, g64, _cells(p, 20, 2))
+    s64.close()
+
+
+def test_adjoint_rejects_unsupported():
+    p = W.vortex_with_bumps(32)
+    s = V.VLBM(p.nx, p.ny, p.dx, bc=(1, 1, 0, 0), lam=1.0, limiter=V.LIM_PP, precision=V.FP64, device=DEV)
+    u0 = torch.tensor(p.conserved(), dtype=torch.float64, device=DEV)
+    with pytest.raises(V.VLBMError) as e:
+        s.adjoint(u0, 4, 2, s.adjoint_scratch(4, 2), u0=u0)
+    assert e.value.code == V.E_UNSUPPORTED
+    s.close()
+    s = V.VLBM(p.nx, p.ny, p.dx, lam=1.0, limiter=V.LIM_LMP, precision=V.FP64, device=DEV)
+    with pytest.raises(V.VLBMError) as e:
+        s.adjoint(u0, 4, 2, s.adjoint_scratch(4, 2), u0=u0)
+    assert e.value.code == V.E_UNSUPPORTED
+    s.close()
+    s = V.VLBM(p.nx, p.ny, p.dx, lam=1.0, limiter=V.LIM_PP, precision=V.FP64, device=DEV)
+    s.set_conserved(u0[0].contiguous(), u0[1:3].contiguous(), u0[3].contiguous())
+    with pytest.raises(V.VLBMError) as e:        # no rollout precedes it
+        s.adjoint(u0, 4, 2, s.adjoint_scratch(4, 2))
+    assert e.value.code == V.E_INVAL
+    s.step(1)
+    with pytest.raises(V.VLBMError):             # rollout must start at n = 0
+        s.rollout(4, 2, s.adjoint_scratch(4, 2))
+    s.close()
