@@ -102,7 +102,9 @@ typedef struct {
                          preservation); default 0.5 as in Sec. 4 */
     double eps;       /* epsilon subtracted in the PP and pressure bounds; default 1e-16 */
     int32_t kernel;   /* VLBM_KERNEL_*; default AUTO */
-    int32_t reserved;
+    int32_t sponge;   /* sponge layer of Sec. 4.2: theta = 0 on every face of the cells within
+                         `sponge` cells of a zero-gradient side (the paper uses 5 with its
+                         zero-gradient boundaries); 0 = none, at most min(nx, ny) / 2 */
 } vlbm_opts;
 
 /* Host copy of the device-side step state and monitors. */

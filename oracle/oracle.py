@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
 class _Cfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("bc", ctypes.c_int * 4),
                 ("limiter", ctypes.c_int), ("gamma", ctypes.c_double),
-                ("alpha", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("eps", ctypes.c_double), ("sponge", ctypes.c_int)]
 
 
 _DBG_FIELDS = ["theta_x", "theta_y", "theta_rho_x", "theta_rho_y", "theta_p_x", "theta_p_y",
@@ -102,10 +102,11 @@ class Config:
     gamma: float = 1.4
     alpha: float = 0.5
     eps: float = 1e-16
+    sponge: int = 0       # Sec. 4.2: theta = 0 within `sponge` cells of a zero-gradient side
 
     def c(self) -> _Cfg:
         return _Cfg(self.nx, self.ny, (ctypes.c_int * 4)(*self.bc), self.limiter,
-                    self.gamma, self.alpha, self.eps)
+                    self.gamma, self.alpha, self.eps, self.sponge)
 
 
 def kinetic_speed(lam: float, alpha: float) -> float:

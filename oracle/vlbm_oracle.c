@@ -48,7 +48,7 @@ int orc_check_cfg(const orc_cfg *c) {
         if (c->bc[s] < 0 || c->bc[s] > 2) return -1;
     if ((c->bc[0] == ORC_BC_PERIODIC) != (c->bc[1] == ORC_BC_PERIODIC)) return -1;
     if ((c->bc[2] == ORC_BC_PERIODIC) != (c->bc[3] == ORC_BC_PERIODIC)) return -1;
-    if (c->limiter < 0 || c->limiter > 4) return -1;
+    if (c->limiter < 0 || c->limiter > 4 || c->sponge < 0) return -1;
     if (!(c->alpha >= 0.0 && c->alpha < 1.0) || !(c->gamma > 1.0)) return -1;
     return 0;
 }
@@ -265,6 +265,15 @@ static int work_alloc(work_t *w, size_t n) {
     return 0;
 }
 
+/* Cell (i, j) (ghost cells included) lies in the sponge layer of Sec. 4.2: within
+ * c->sponge cells of a zero-gradient side. */
+static int in_sponge(const orc_cfg *c, int i, int j) {
+    const int s = c->sponge;
+    if (s <= 0) return 0;
+    return (c->bc[0] == ORC_BC_ZEROGRAD && i < s) || (c->bc[1] == ORC_BC_ZEROGRAD && i >= c->nx - s) ||
+           (c->bc[2] == ORC_BC_ZEROGRAD && j < s) || (c->bc[3] == ORC_BC_ZEROGRAD && j >= c->ny - s);
+}
+
 /* Steps a3-a8 of the scheme on the extended grid: equilibria, face states u* and
  * dF, density bounds, theta. Shared by the kinetic and the flux-form updates. */
 static void compute_theta(const orc_cfg *c, double a, const ext_t *e, work_t *w) {
@@ -333,7 +342,7 @@ static void compute_theta(const orc_cfg *c, double a, const ext_t *e, work_t *w)
     }
 
     /* a6-a8: theta_rho, theta_p and theta = min(1, theta_rho, theta_p) on the faces
-     * that touch an interior cell */
+     * that touch an interior cell; theta = 0 on the faces of sponge-layer cells */
 #pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int J = G - 1; J < ey - G + 1; ++J)
         for (int I = G - 1; I < ex - G + 1; ++I) {
@@ -361,6 +370,9 @@ static void compute_theta(const orc_cfg *c, double a, const ext_t *e, work_t *w)
                     if (thp < th) th = thp;
                     if (th < 0.0) th = 0.0;
                 }
+                const int iL = I - G, jL = J - G;
+                if (in_sponge(c, iL, jL) || in_sponge(c, dir == 0 ? iL + 1 : iL, dir == 0 ? jL : jL + 1))
+                    th = 0.0;
                 if (dir == 0) { w->thr_x[L] = thr; w->thp_x[L] = thp; w->th_x[L] = th; }
                 else          { w->thr_y[L] = thr; w->thp_y[L] = thp; w->th_y[L] = th; }
             }

@@ -37,6 +37,8 @@ typedef struct {
     double gamma;     /* ideal-gas heat capacity ratio */
     double alpha;     /* D2Q5 rest weight, 1/2 <= alpha < 1 (Prop. convex preservation) */
     double eps;       /* epsilon subtracted in the PP and pressure bounds (1e-16 in Sec. 3.3.3) */
+    int sponge;       /* Sec. 4.2: theta = 0 on every face of the cells within `sponge` cells
+                         of a zero-gradient side (0 = none) */
 } orc_cfg;
 
 /* Optional per-face / per-cell outputs of one step. Any pointer may be NULL.

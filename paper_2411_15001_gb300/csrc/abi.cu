@@ -102,6 +102,7 @@ static void build_desc(vlbm_state *s) {
     d.item0 = 0;
     d.nitems = s->nitems;
     d.ctl = s->ctl;
+    d.sponge = s->sponge;
     static_assert(sizeof(InstDesc<T>) <= 512, "descriptor block");
     s->desc_host.assign((unsigned char *)&d, (unsigned char *)&d + sizeof d);
     s->items_host.assign(s->nitems, 0);
@@ -212,6 +213,8 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
     if (!(o.eps >= 0.0 && o.eps < 1e-3)) return fail(nullptr, VLBM_E_INVAL, "eps must be in [0, 1e-3)");
     if (o.kernel < VLBM_KERNEL_AUTO || o.kernel > VLBM_KERNEL_FUSED)
         return fail(nullptr, VLBM_E_INVAL, "kernel out of range");
+    if (o.sponge < 0 || 2 * o.sponge > grid->nx || 2 * o.sponge > grid->ny)
+        return fail(nullptr, VLBM_E_INVAL, "sponge must be in [0, min(nx, ny) / 2]");
     if (!(lambda == lambda)) return fail(nullptr, VLBM_E_INVAL, "lambda is NaN");
     const Layout L = make_layout(grid->nx, grid->ny, elem);
     if (!d_workspace || ((uintptr_t)d_workspace & 255))
@@ -240,6 +243,7 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
     s->lambda = lambda;
     s->alpha = o.alpha;
     s->eps = o.eps;
+    s->sponge = o.sponge;
     s->a_fixed = lambda > 0.0 ? 2.0 * lambda / (1.0 - o.alpha) : 0.0;
     s->L = L;
     s->ws = d_workspace;

@@ -84,7 +84,7 @@ __device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const 
     const T r1 = fabs(dr) / rs;
     const T r2 = (fabs(g1) + sd) / (T(-2) * g0);
     T gr_us[4], gr_df[4];
-    if (r1 >= r2) {
+    if (r1 > r2) {   // the step takes r = r1 > r2 ? r1 : r2
         const T sg = dr > T(0) ? T(1) : (dr < T(0) ? T(-1) : T(0));
         gr_us[0] = -fabs(dr) / (rs * rs);
         gr_us[1] = gr_us[2] = gr_us[3] = T(0);

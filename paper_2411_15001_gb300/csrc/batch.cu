@@ -32,6 +32,7 @@ static_assert(kDescStride % 256 == 0, "descriptor stride");
 struct vlbm_batch {
     int n = 0, precision = 0, limiter = 0, device = 0;
     double gamma = 1.4, alpha = 0.5, eps = 1e-16;
+    int sponge = 0;
     std::vector<vlbm_grid> grids;
     std::vector<Layout> L;
     std::vector<size_t> buf_off;       // per grid: offset of its two state buffers
@@ -115,6 +116,7 @@ static StepArgs<T> inst_args(const vlbm_batch *b, int i) {
     A.alpha = b->alpha;
     A.eps = b->eps;
     A.ctl = (DevCtl *)((char *)b->ws + b->ctl_off + (size_t)i * kCtlStride);
+    A.sponge = b->sponge;
     return A;
 }
 
@@ -147,6 +149,7 @@ static void build_items(vlbm_batch *b) {
         d.item0 = (int)b->items_host.size();
         d.nitems = d.strips * ((A.ny + b->chunk - 1) / b->chunk);
         d.ctl = A.ctl;
+        d.sponge = A.sponge;
         for (int q = 0; q < d.nitems; ++q) b->items_host.push_back(i);
         memcpy(&b->desc_host[(size_t)i * kDescStride], &d, sizeof d);
     }
@@ -285,6 +288,9 @@ int vlbm_batch_init(int32_t n, const vlbm_grid *grids, double gamma, int32_t lim
     if (opts) o = *opts;
     if (!(o.alpha >= 0.5 && o.alpha < 1.0) || !(o.eps >= 0.0 && o.eps < 1e-3))
         return bfail(nullptr, VLBM_E_INVAL, "alpha or eps out of range");
+    for (int i = 0; i < n; ++i)
+        if (o.sponge < 0 || 2 * o.sponge > grids[i].nx || 2 * o.sponge > grids[i].ny)
+            return bfail(nullptr, VLBM_E_INVAL, "sponge must be in [0, min(nx, ny) / 2] for grid %d", i);
     if (!d_workspace || ((uintptr_t)d_workspace & 255))
         return bfail(nullptr, VLBM_E_NOMEM, "workspace NULL or not 256-byte aligned");
     vlbm_batch *b = new (std::nothrow) vlbm_batch();
@@ -308,6 +314,7 @@ int vlbm_batch_init(int32_t n, const vlbm_grid *grids, double gamma, int32_t lim
     b->gamma = gamma;
     b->alpha = o.alpha;
     b->eps = o.eps;
+    b->sponge = o.sponge;
     b->grids.assign(grids, grids + n);
     b->ws = d_workspace;
     b->stream = (cudaStream_t)stream;

@@ -74,7 +74,7 @@ struct CompactLoad {
 template <typename T, int LIM>
 __global__ void __launch_bounds__(kNaBX *kNaBY)
     k_step_noalloc(CompactLoad<T> L, T *__restrict__ out, double a, double alpha, double gamma,
-                   double eps, NoAllocPartial *part) {
+                   double eps, int sponge, NoAllocPartial *part) {
     const StepConsts<T> k = make_consts<T>(a, alpha, gamma, eps);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kNaBX *kNaBY)
     mon.init();
     if (i < L.nx && j < L.ny) {
         T nv[kNPlane];
-        cell_step<T, LIM>(L, i, j, k, nv, mon.fp64);
+        cell_step<T, LIM>(L, i, j, k, Sponge(sponge, L.nx, L.ny, L.bc), nv, mon.fp64);
         const long long d = (long long)j * L.nx + i;
 #pragma unroll
         for (int q = 0; q < kNPlane; ++q) out[q * L.N + d] = nv[q];
@@ -145,7 +145,7 @@ __global__ void k_noalloc_reduce(const NoAllocPartial *part, int n, NoAllocResul
 
 template <typename T>
 cudaError_t launch_noalloc(const vlbm_grid *g, int limiter, const void *in, void *out, double a,
-                           double alpha, double gamma, double eps, unsigned char *scratch,
+                           double alpha, double gamma, double eps, int sponge, unsigned char *scratch,
                            cudaStream_t s) {
     CompactLoad<T> L;
     L.in = (const T *)in;
@@ -158,11 +158,11 @@ cudaError_t launch_noalloc(const vlbm_grid *g, int limiter, const void *in, void
     NoAllocResult *res = (NoAllocResult *)(scratch + kNoAllocMaxBlocks * sizeof(NoAllocPartial));
     T *o = (T *)out;
     switch (limiter) {
-        case VLBM_LIM_FIRST_ORDER: k_step_noalloc<T, VLBM_LIM_FIRST_ORDER><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, part); break;
-        case VLBM_LIM_NONE: k_step_noalloc<T, VLBM_LIM_NONE><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, part); break;
-        case VLBM_LIM_PP: k_step_noalloc<T, VLBM_LIM_PP><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, part); break;
-        case VLBM_LIM_LMP: k_step_noalloc<T, VLBM_LIM_LMP><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, part); break;
-        default: k_step_noalloc<T, VLBM_LIM_RLMP><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, part); break;
+        case VLBM_LIM_FIRST_ORDER: k_step_noalloc<T, VLBM_LIM_FIRST_ORDER><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
+        case VLBM_LIM_NONE: k_step_noalloc<T, VLBM_LIM_NONE><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
+        case VLBM_LIM_PP: k_step_noalloc<T, VLBM_LIM_PP><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
+        case VLBM_LIM_LMP: k_step_noalloc<T, VLBM_LIM_LMP><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
+        default: k_step_noalloc<T, VLBM_LIM_RLMP><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -207,11 +207,14 @@ extern "C" int vlbm_step_noalloc(const vlbm_grid *grid, double gamma, double a, 
     if (limiter < VLBM_LIM_FIRST_ORDER || limiter > VLBM_LIM_RLMP) return VLBM_E_INVAL;
     if (precision != VLBM_FP32 && precision != VLBM_FP64) return VLBM_E_INVAL;
     double alpha = 0.5, eps = 1e-16;
+    int sponge = 0;
     if (opts) {
         alpha = opts->alpha;
         eps = opts->eps;
+        sponge = opts->sponge;
     }
     if (!(alpha >= 0.5 && alpha < 1.0) || !(eps >= 0.0 && eps < 1e-3)) return VLBM_E_INVAL;
+    if (sponge < 0 || 2 * sponge > grid->nx || 2 * sponge > grid->ny) return VLBM_E_INVAL;
     if (!d_in || !d_out || d_in == d_out || !result) return VLBM_E_INVAL;
     const long long blocks =
         (long long)((grid->nx + kNaBX - 1) / kNaBX) * ((grid->ny + kNaBY - 1) / kNaBY);
@@ -229,8 +232,8 @@ extern "C" int vlbm_step_noalloc(const vlbm_grid *grid, double gamma, double a, 
     }
     cudaStream_t s = (cudaStream_t)stream;
     e = precision == VLBM_FP64
-            ? launch_noalloc<double>(grid, limiter, d_in, d_out, a, alpha, gamma, eps, scratch, s)
-            : launch_noalloc<float>(grid, limiter, d_in, d_out, a, alpha, gamma, eps, scratch, s);
+            ? launch_noalloc<double>(grid, limiter, d_in, d_out, a, alpha, gamma, eps, sponge, scratch, s)
+            : launch_noalloc<float>(grid, limiter, d_in, d_out, a, alpha, gamma, eps, sponge, scratch, s);
     if (e != cudaSuccess) return VLBM_E_CUDA;
     NoAllocResult r;
     e = cudaMemcpyAsync(&r, scratch + kNoAllocMaxBlocks * sizeof(NoAllocPartial), sizeof r,

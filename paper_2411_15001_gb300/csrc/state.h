@@ -13,6 +13,7 @@ struct vlbm_state {
     vlbm_grid grid;
     int precision, limiter, kernel;
     double gamma, lambda, alpha, eps, a_fixed;
+    int sponge;
     vlbm::Layout L;
     void *ws;
     cudaStream_t stream;
@@ -71,6 +72,7 @@ inline StepArgs<T> args_of(const vlbm_state *s) {
     A.alpha = s->alpha;
     A.eps = s->eps;
     A.ctl = s->ctl;
+    A.sponge = s->sponge;
     return A;
 }
 

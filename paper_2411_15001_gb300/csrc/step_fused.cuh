@@ -60,6 +60,7 @@ struct Geo {
     long long plane;
     int pitch, nx, ny;
     int bc[4];
+    int sponge;
 };
 
 // Write the ghost images of interior cell (c, O) into `out`: its periodic
@@ -220,8 +221,8 @@ struct FusedCtx {
         } else {
             T trx, try_;
             if (LIM == VLBM_LIM_PP) {
-                trx = theta_rho_pp(xs_us[0], xs_df[0], k);
-                try_ = theta_rho_pp(ys_us[0], ys_df[0], k);
+                trx = pp_density_target(xs_us[0], xs_df[0], k);
+                try_ = pp_density_target(ys_us[0], ys_df[0], k);
             } else {
                 const int rp = (R - 1) & 1;
                 trx = theta_rho_lmp(xs_us[0], xs_df[0], S.mu[rp][b], S.nu[rp][b], S.mu[rp][br],
@@ -235,6 +236,12 @@ struct FusedCtx {
             const bool col_own = b >= kFHalo && b < kFHalo + kFOut && c < D.nx;
             if (col_own && R - 1 >= y0 && R - 1 < y1) mon.fp64 += nx64;
             if (col_own && R - 2 >= y0 && R - 2 < y1) mon.fp64 += ny64;
+        }
+        if (D.sponge > 0) {   // sponge layer (Sec. 4.2): theta = 0 on the faces of layer cells
+            const Sponge sp(D.sponge, D.nx, D.ny, D.bc);
+            const bool c1 = sp.cell(c, R - 1);
+            if (c1 || sp.cell(c + 1, R - 1)) tx = T(0);        // x-face (c, c+1) of row R-1
+            if (c1 || sp.cell(c, R - 2)) ty = T(0);            // y-face (R-2, R-1) of column c
         }
         S.thx[(R - 1) & 1][b] = tx;
         mu2 = mu1;
@@ -332,6 +339,7 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         geo.nx = D.nx;
         geo.ny = D.ny;
         for (int q = 0; q < 4; ++q) geo.bc[q] = D.bc[q];
+        geo.sponge = D.sponge;
         const long long n = C->n;
         const StepConsts<T> k = make_consts<T>(C->a, B.alpha, B.gamma, B.eps);
         const int local = item - D.item0;

@@ -42,10 +42,10 @@ __device__ __forceinline__ void cell_thetas(const Loader &L, int i, int j, const
     }
     T tr[4];
     if (LIM == VLBM_LIM_PP) {
-        tr[0] = theta_rho_pp(usW[0], dfW[0], k);
-        tr[1] = theta_rho_pp(usE[0], dfE[0], k);
-        tr[2] = theta_rho_pp(usS[0], dfS[0], k);
-        tr[3] = theta_rho_pp(usN[0], dfN[0], k);
+        tr[0] = pp_density_target(usW[0], dfW[0], k);
+        tr[1] = pp_density_target(usE[0], dfE[0], k);
+        tr[2] = pp_density_target(usS[0], dfS[0], k);
+        tr[3] = pp_density_target(usN[0], dfN[0], k);
     } else {
         // density bounds (eq. LMP_minmax) of C and its four neighbours; the extra
         // face densities come from the radius-2 and diagonal cells
@@ -118,7 +118,7 @@ __device__ __forceinline__ void face_state(const T uL[4], const T fL[4], const T
 // cells included). Writes the cell's 20 new values to nv (u, then u_1..u_4).
 template <typename T, int LIM, typename Loader>
 __device__ __forceinline__ void cell_step(const Loader &L, int i, int j, const StepConsts<T> &k,
-                                          T nv[kNPlane], unsigned int &n_fp64) {
+                                          const Sponge &sp, T nv[kNPlane], unsigned int &n_fp64) {
     T uC[4], uW[4], uE[4], uS[4], uN[4];
     L.u4(0, i, j, uC);
     L.u4(0, i - 1, j, uW);
@@ -159,6 +159,13 @@ __device__ __forceinline__ void cell_step(const Loader &L, int i, int j, const S
     T th[4];
     cell_thetas<T, LIM>(L, i, j, uC, uW, uE, uS, uN, usW, dfW, usE, dfE, usS, dfS, usN, dfN, k, th,
                         n_fp64);
+    if (sp.w > 0) {   // sponge layer (Sec. 4.2): theta = 0 on the faces of layer cells
+        const bool cC = sp.cell(i, j);
+        if (cC || sp.cell(i - 1, j)) th[0] = T(0);
+        if (cC || sp.cell(i + 1, j)) th[1] = T(0);
+        if (cC || sp.cell(i, j - 1)) th[2] = T(0);
+        if (cC || sp.cell(i, j + 1)) th[3] = T(0);
+    }
     // collide + stream, eq. (blending_u1) and eq. (blending_u)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -189,7 +196,7 @@ __global__ void __launch_bounds__(256) k_step_simple(StepArgs<T> A) {
     mon.init();
     if (i < A.nx && j < A.ny) {
         T nv[kNPlane];
-        cell_step<T, LIM>(L, i, j, k, nv, mon.fp64);
+        cell_step<T, LIM>(L, i, j, k, Sponge(A.sponge, A.nx, A.ny, A.bc), nv, mon.fp64);
         const long long d = (long long)(j + kOY) * A.pitch + (i + kOX);
 #pragma unroll
         for (int q = 0; q < kNPlane; ++q) out[q * A.plane + d] = nv[q];

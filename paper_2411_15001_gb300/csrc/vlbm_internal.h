@@ -7,6 +7,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "../../include/vlbm.h"
+
 namespace vlbm {
 
 // Padded plane layout. Cell (i, j), -2 <= i < nx+2, -2 <= j < ny+2, of plane q
@@ -107,6 +109,20 @@ struct InstDesc {
     int strips, chunk;    // strips of 120 columns, chunks of `chunk` rows
     int item0, nitems;    // this grid's work items in the launch
     DevCtl *ctl;
+    int sponge;           // width of the theta = 0 layer at zero-gradient sides (Sec. 4.2)
+};
+
+// Sponge layer of Sec. 4.2: theta = 0 on every face of a cell that lies within
+// `w` cells of a zero-gradient side (ghost cells included); w = 0 disables it.
+struct Sponge {
+    int w, nx, ny;
+    bool tw, te, ts, tn;   // west, east, south, north side is zero-gradient
+    __host__ __device__ Sponge(int w_, int nx_, int ny_, const int bc[4])
+        : w(w_), nx(nx_), ny(ny_), tw(bc[0] == VLBM_BC_TRANSMISSIVE), te(bc[1] == VLBM_BC_TRANSMISSIVE),
+          ts(bc[2] == VLBM_BC_TRANSMISSIVE), tn(bc[3] == VLBM_BC_TRANSMISSIVE) {}
+    __host__ __device__ bool cell(int i, int j) const {
+        return (tw && i < w) || (te && i >= nx - w) || (ts && j < w) || (tn && j >= ny - w);
+    }
 };
 
 // Work counter of one row-marching launch; reset by the last CTA to leave.
@@ -135,6 +151,7 @@ struct StepArgs {
     double alpha;
     double eps;
     DevCtl *ctl;
+    int sponge;         // width of the theta = 0 layer at zero-gradient sides (Sec. 4.2)
 };
 
 // Host launchers (stream-ordered; return cudaError_t of the launch).

@@ -29,7 +29,7 @@ class vlbm_grid(ctypes.Structure):
 
 class vlbm_opts(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("eps", ctypes.c_double), ("kernel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("sponge", ctypes.c_int32)]
 
 
 class vlbm_monitor_t(ctypes.Structure):
@@ -297,7 +297,7 @@ class VLBM:
 
     def __init__(self, nx: int, ny: int, dx: float, bc=(0, 0, 0, 0), gamma: float = 1.4,
                  lam: float = 0.0, limiter=LIM_PP, precision=FP32, alpha: float = 0.5,
-                 eps: float = 1e-16, kernel=KERNEL_AUTO, device=None, stream=None):
+                 eps: float = 1e-16, kernel=KERNEL_AUTO, device=None, stream=None, sponge: int = 0):
         import torch
 
         self.torch = torch
@@ -310,7 +310,7 @@ class VLBM:
         self.precision = precision
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self.grid = vlbm_grid(nx, ny, dx, (ctypes.c_int32 * 4)(*bc))
-        self.opts = vlbm_opts(alpha, eps, kernel, 0)
+        self.opts = vlbm_opts(alpha, eps, kernel, sponge)
         nbytes = vlbm_workspace_bytes(self.grid, precision)
         if nbytes == 0:
             raise VLBMError(E_INVAL, "invalid grid")
@@ -426,7 +426,7 @@ class VLBMBatch:
     """Independent grids of uneven sizes advanced together (vlbm_batch_*)."""
 
     def __init__(self, grids, gamma: float = 1.4, limiter=LIM_PP, precision=FP32,
-                 alpha: float = 0.5, eps: float = 1e-16, device=None, stream=None):
+                 alpha: float = 0.5, eps: float = 1e-16, device=None, stream=None, sponge: int = 0):
         """grids: sequence of (nx, ny, dx, bc) tuples."""
         import torch
 
@@ -441,7 +441,7 @@ class VLBMBatch:
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self._grids = [vlbm_grid(int(g[0]), int(g[1]), float(g[2]), (ctypes.c_int32 * 4)(*g[3]))
                        for g in grids]
-        self.opts = vlbm_opts(alpha, eps, 0, 0)
+        self.opts = vlbm_opts(alpha, eps, 0, sponge)
         nbytes = vlbm_batch_workspace_bytes(self._grids, precision)
         if nbytes == 0:
             raise VLBMError(E_INVAL, "invalid grids")

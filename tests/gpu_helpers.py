@@ -7,14 +7,14 @@ LIM_NAMES = {0: "first", 1: "none", 2: "PP", 3: "LMP", 4: "RLMP"}
 
 
 def gpu_run(p, limiter, precision, nsteps=None, t_end=None, lam=0.0, eps=1e-16, kernel=0,
-            return_solver=False):
+            return_solver=False, sponge=0):
     import torch
 
     from paper_2411_15001_gb300 import vlbm as V
 
     dt = torch.float64 if precision == V.FP64 else torch.float32
     s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, gamma=p.gamma, lam=lam, limiter=limiter,
-               precision=precision, eps=eps, kernel=kernel, device="cuda:0")
+               precision=precision, eps=eps, kernel=kernel, device="cuda:0", sponge=sponge)
     c = torch.tensor(p.conserved(), dtype=dt, device="cuda:0")
     s.set_conserved(c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
     if nsteps is not None:
@@ -29,8 +29,8 @@ def gpu_run(p, limiter, precision, nsteps=None, t_end=None, lam=0.0, eps=1e-16, 
     return planes, mon
 
 
-def oracle_run(p, limiter, nsteps=None, t_end=None, lam=0.0, eps=1e-16):
-    cfg = O.Config(p.nx, p.ny, p.bc, limiter, p.gamma, 0.5, eps)
+def oracle_run(p, limiter, nsteps=None, t_end=None, lam=0.0, eps=1e-16, sponge=0):
+    cfg = O.Config(p.nx, p.ny, p.bc, limiter, p.gamma, 0.5, eps, sponge)
     return O.run(cfg, p.conserved(), p.dx, nsteps=nsteps, t_end=t_end,
                  lam_fixed=lam if lam > 0 else None)
 

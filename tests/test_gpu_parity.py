@@ -45,6 +45,19 @@ def test_fp64_parity_random_quadrants(kernel, lim, bc, shape):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("lim", [V.LIM_PP, V.LIM_LMP])
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (0, 0, 1, 1), (1, 2, 2, 1)])
+def test_fp64_parity_sponge(kernel, lim, bc):
+    """Sponge layer of Sec. 4.2 (theta = 0 within 5 cells of a zero-gradient side),
+    on a grid of two strips with a ragged tail."""
+    p = W.quadrant_riemann(130, 37, seed=8, bc=bc)
+    got, mon = gpu_run(p, lim, V.FP64, nsteps=15, kernel=kernel, sponge=5)
+    ref = oracle_run(p, lim, nsteps=15, sponge=5)
+    assert mon["status"] == 0
+    assert np.array_equal(got, ref["state"])
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_fp64_parity_unlimited_smooth(kernel):
     p = W.isentropic_vortex(40)
     got, mon = gpu_run(p, V.LIM_NONE, V.FP64, nsteps=30, kernel=kernel)

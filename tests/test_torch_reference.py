@@ -1,0 +1,59 @@
+"""The PyTorch restatement used to check the adjoint against autograd, pinned to
+the oracle: same forward map to round-off, and autograd equal to central
+differences of the oracle on smooth data."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_15001_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+
+from tests import torch_reference as TR  # noqa: E402
+
+
+@pytest.mark.parametrize("lim", [O.LIM_FIRST, O.LIM_SECOND, O.LIM_PP])
+def test_forward_matches_oracle(lim):
+    p = W.vortex_with_bumps(24)
+    cfg = O.Config(24, 24, (0, 0, 0, 0), lim, 1.4, 0.5, 1e-16)
+    lam = 1.05 * O.max_speed(cfg, O.new_state(p.conserved()))
+    ref = O.run(cfg, p.conserved(), p.dx, nsteps=25, lam_fixed=lam)["state"]
+    got = TR.rollout(torch.tensor(p.conserved()), 25, O.kinetic_speed(lam, 0.5), lim).numpy()
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_forward_matches_oracle_with_active_limiter():
+    """Random admissible cells (periodic): theta < 1 and theta = 0 occur."""
+    p = W.random_cells(16, 12, seed=3)
+    cfg = O.Config(16, 12, (0, 0, 0, 0), O.LIM_PP, 1.4, 0.5, 1e-13)
+    lam = 1.05 * O.max_speed(cfg, O.new_state(p.conserved()))
+    a = O.kinetic_speed(lam, 0.5)
+    st = O.run(cfg, p.conserved(), p.dx, nsteps=2, lam_fixed=lam)["state"]
+    _, dbg = O.step(cfg, st, a, debug=True)
+    assert (dbg["theta_x"] < 1).sum() + (dbg["theta_y"] < 1).sum() > 10
+    ref = O.run(cfg, p.conserved(), p.dx, nsteps=6, lam_fixed=lam)["state"]
+    got = TR.rollout(torch.tensor(p.conserved()), 6, a, O.LIM_PP, eps=1e-13).numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_autograd_matches_oracle_differences():
+    p = W.vortex_with_bumps(20)
+    cfg = O.Config(20, 20, (0, 0, 0, 0), O.LIM_PP, 1.4, 0.5, 1e-16)
+    lam = 1.05 * O.max_speed(cfg, O.new_state(p.conserved()))
+    a = O.kinetic_speed(lam, 0.5)
+    rng = np.random.default_rng(1)
+    w = rng.uniform(0.5, 1.5, size=(4, 20, 20))
+    c0 = p.conserved()
+    u0 = torch.tensor(c0, requires_grad=True)
+    sN = TR.rollout(u0, 15, a, O.LIM_PP)
+    (0.5 * (torch.tensor(w) * sN[:4] ** 2).sum()).backward()
+    g = u0.grad.numpy()
+    for (j, i, c) in [(3, 4, 0), (10, 17, 1), (15, 2, 2), (8, 8, 3)]:
+        h = 1e-5 * max(1.0, abs(c0[c, j, i]))
+        up, dn = c0.copy(), c0.copy()
+        up[c, j, i] += h
+        dn[c, j, i] -= h
+        A = O.run(cfg, up, p.dx, nsteps=15, lam_fixed=lam)["state"][:4]
+        B = O.run(cfg, dn, p.dx, nsteps=15, lam_fixed=lam)["state"][:4]
+        fd = 0.5 * float((w * (A - B) * (A + B)).sum()) / (2 * h)
+        assert abs(fd - g[c, j, i]) <= 1e-6 * abs(g[c, j, i]), (j, i, c, fd, g[c, j, i])
