@@ -82,7 +82,8 @@ extern "C" {
 #define VLBM_FP64 0
 #define VLBM_FP32 1
 
-/* Kernel choice (VLBM_KERNEL_AUTO picks the fastest available). */
+/* Kernel choice. VLBM_KERNEL_AUTO takes the row-marching kernel for FP32 grids of at
+ * least 2^19 cells and the one-thread-per-cell kernel otherwise (where it is faster). */
 #define VLBM_KERNEL_AUTO 0
 #define VLBM_KERNEL_SIMPLE 1    /* one thread per cell, radius-2 gather from L2 */
 #define VLBM_KERNEL_FUSED 2     /* row-marching TMA kernel, one pass per step */
@@ -123,6 +124,9 @@ typedef struct {
                                    (FP32 state; every face for an FP64 state) */
     int32_t done;              /* 1 once vlbm_step_to has reached its final time */
     int32_t status;            /* sticky VLBM_OK / VLBM_E_* of the device */
+    double min_internal_energy; /* min of E - |m|^2 / (2 rho) over the cells of the current state,
+                                   evaluated in the state's precision (membership of G is decided
+                                   by an exact test: bad_cells) */
 } vlbm_monitor_t;
 
 /* Bytes of device workspace for a grid and precision (two padded 20-plane

@@ -178,6 +178,77 @@ bool encode_state_tmap(CUtensorMap *out, void *base, const Layout &L) {
 }
 }  // namespace vlbm
 
+// A graph of kGraphSteps steps: kernel nodes with the same arguments as the
+// stream launches (the step kernel reads its buffers' parity from the control
+// block, so every step's node is identical).
+template <typename T>
+static cudaError_t build_graph(vlbm_state *s) {
+    cudaError_t e = cudaGraphCreate(&s->graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    const bool fused = use_fused(s);
+    FusedBatchArgs<T> B = batch_args_of<T>(s);
+    StepArgs<T> A = args_of<T>(s);
+    void *pf[] = {&B};
+    void *pa[] = {&A};
+    cudaKernelNodeParams kg;
+    memset(&kg, 0, sizeof kg);
+    if (fused) {
+        size_t smem = 0;
+        kp.func = const_cast<void *>(fused_kernel_fn<T>(s->limiter, &smem));
+        kp.gridDim = dim3(s->fused_grid);
+        kp.blockDim = dim3(kFusedBox);
+        kp.sharedMemBytes = (unsigned)smem;
+        kp.kernelParams = pf;
+    } else {
+        kp.func = const_cast<void *>(simple_kernel_fn<T>(s->limiter));
+        simple_launch_shape(s->grid.nx, s->grid.ny, &kp.gridDim, &kp.blockDim);
+        kp.kernelParams = pa;
+        kg.func = const_cast<void *>(ghosts_kernel_fn<T>());
+        ghosts_launch_shape(s->grid.nx, s->grid.ny, &kg.gridDim, &kg.blockDim);
+        kg.kernelParams = pa;
+    }
+    cudaGraphNode_t prev = nullptr;
+    for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, s->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        prev = node;
+        if (e == cudaSuccess && !fused) {
+            e = cudaGraphAddKernelNode(&node, s->graph, &prev, 1, &kg);
+            prev = node;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, s->graph, 0);
+    if (e != cudaSuccess) {
+        if (s->gexec) cudaGraphExecDestroy(s->gexec);
+        cudaGraphDestroy(s->graph);
+        s->gexec = nullptr;
+        s->graph = nullptr;
+    }
+    return e;
+}
+
+// n steps: whole groups of kGraphSteps replayed from the graph (not while the
+// per-launch kernel timing is on), the rest as single launches.
+cudaError_t vlbm::api::step_many(vlbm_state *s, int64_t n) {
+    if (!s->profiling && n >= kGraphSteps) {
+        cudaError_t e = cudaSuccess;
+        if (!s->gexec)
+            e = s->precision == VLBM_FP64 ? build_graph<double>(s) : build_graph<float>(s);
+        if (e != cudaSuccess) return e;
+        for (; n >= kGraphSteps; n -= kGraphSteps) {
+            e = cudaGraphLaunch(s->gexec, s->stream);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    for (; n > 0; --n) {
+        cudaError_t e = step_once(s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 static bool make_tmap(vlbm_state *s) { return encode_state_tmap(&s->tmap, s->ws, s->L); }
 
 int vlbm::api::read_ctl(vlbm_state *s, DevCtl *h) {
@@ -328,10 +399,8 @@ int vlbm_step(vlbm_state *s, int64_t nsteps) {
         s->at_init = false;
         s->roll_scratch = nullptr;
     }
-    for (int64_t k = 0; k < nsteps; ++k) {
-        cudaError_t e = step_once(s);
-        if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
-    }
+    cudaError_t e = step_many(s, nsteps);
+    if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     return VLBM_OK;
 }
 
@@ -348,10 +417,8 @@ int vlbm_step_to(vlbm_state *s, double t_end, int64_t max_steps) {
     int64_t done_steps = 0, chunk = 64;
     while (done_steps < max_steps) {
         const int64_t k = chunk < max_steps - done_steps ? chunk : max_steps - done_steps;
-        for (int64_t q = 0; q < k; ++q) {
-            e = step_once(s);
-            if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
-        }
+        e = step_many(s, k);
+        if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
         done_steps += k;
         DevCtl h;
         int rc = read_ctl(s, &h);
@@ -392,6 +459,7 @@ int vlbm_monitors(vlbm_state *s, vlbm_monitor_t *out) {
     out->nonfinite_cells = h.nonfinite_last;
     out->first_bad_step = h.first_bad_step;
     out->min_rho = h.min_rho;
+    out->min_internal_energy = h.min_rhoe;
     for (int c = 0; c < 4; ++c) out->sum[c] = h.sum_last[c];
     out->theta_p_fp64_faces = h.fp64_last;
     out->done = h.done;
@@ -480,6 +548,8 @@ int vlbm_profile_read(vlbm_state *s, double *kernel_ms, int64_t *launches) {
 
 void vlbm_destroy(vlbm_state *s) {
     if (!s) return;
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->graph) cudaGraphDestroy(s->graph);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     delete s;
 }

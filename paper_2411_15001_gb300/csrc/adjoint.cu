@@ -12,7 +12,8 @@
 // Finally the transpose of the initialisation u_k^0 = M_k(u_0) folds the
 // population cotangents into the conserved planes.
 // a^n is held as the forward run produced it: a constant when the state was made
-// with a fixed lambda, else recorded per step during the recomputation.
+// with a fixed lambda, else the step constants are recorded per step during the
+// recomputation.
 #include <stddef.h>
 #include <stdio.h>
 #include <string.h>
@@ -40,19 +41,25 @@ static cudaError_t launch_adjoint_step(const AdjArgs<T> &A, int limiter, cudaStr
 }
 
 template <typename T>
-static cudaError_t launch_adjoint_init(const T *init_state, const Layout &L, const double *a_ptr, double alpha,
-                                       double gamma, const T *cot, T *grad, cudaStream_t s) {
+static cudaError_t launch_adjoint_init(const T *init_state, const Layout &L, const StepConsts<T> *kc, const T *cot,
+                                       T *grad, cudaStream_t s) {
     const dim3 blk(32, 8), grd((L.nx + 31) / 32, (L.ny + 7) / 8);
-    k_adjoint_init<T><<<grd, blk, 0, s>>>(init_state, L.plane, L.pitch, L.nx, L.ny, a_ptr, alpha, gamma, cot,
-                                         grad);
+    k_adjoint_init<T><<<grd, blk, 0, s>>>(init_state, L.plane, L.pitch, L.nx, L.ny, kc, cot, grad);
     return cudaGetLastError();
 }
+
+// The constants of the precision T inside a control block.
+template <typename T> const StepConsts<T> *ctl_consts(const DevCtl *C);
+template <> const StepConsts<float> *ctl_consts<float>(const DevCtl *C) { return &C->kf; }
+template <> const StepConsts<double> *ctl_consts<double>(const DevCtl *C) { return &C->kd; }
 
 }  // namespace vlbm
 
 namespace {
 
 constexpr size_t kCtlBytes = ((sizeof(DevCtl) + 255) / 256) * 256;
+constexpr size_t kConstSlot = 128;   // one StepConsts<T> of the constants history
+static_assert(sizeof(StepConsts<double>) <= kConstSlot && sizeof(StepConsts<float>) <= kConstSlot, "slot");
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -63,7 +70,7 @@ struct Plan {
     size_t seg_off;       // k + 1 state slots (slot 0 is only ever a TMA window start)
     size_t segctl_off;    // control block of the recomputation
     size_t desc_off;      // 2 k InstDesc of the row-marching kernel (by parity of n)
-    size_t ahist_off;     // a^n of each step of a segment
+    size_t khist_off;     // the step constants (a^n) of each step of a segment
     size_t cot_off;       // two cotangent buffers of 20 compact planes
     size_t cot_bytes;
     size_t total;
@@ -81,8 +88,8 @@ Plan plan_of(const vlbm_state *s, int64_t nsteps, int32_t every) {
     off += kCtlBytes;
     p.desc_off = off;
     off += (size_t)2 * every * 512;
-    p.ahist_off = off;
-    off += round256((size_t)every * sizeof(double));
+    p.khist_off = off;
+    off += round256((size_t)every * kConstSlot);
     p.cot_bytes = round256((size_t)kNPlane * s->grid.nx * s->grid.ny * s->L.elem);
     p.cot_off = off;
     off += 2 * p.cot_bytes;
@@ -177,7 +184,7 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     const bool fixed_a = s->a_fixed > 0.0;
     T *cot[2] = {(T *)(scratch + p.cot_off), (T *)(scratch + p.cot_off + p.cot_bytes)};
     DevCtl *segctl = (DevCtl *)(scratch + p.segctl_off);
-    double *ahist = (double *)(scratch + p.ahist_off);
+    char *khist = scratch + p.khist_off;
     cudaError_t e = cudaMemcpyAsync(cot[0], dLduN, (size_t)4 * N * sizeof(T), cudaMemcpyDeviceToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(cot[0] + 4 * N, 0, (size_t)(kNPlane - 4) * N * sizeof(T), s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "cotangent seed");
@@ -194,9 +201,6 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     A.pitch = s->L.pitch;
     A.nx = s->grid.nx;
     A.ny = s->grid.ny;
-    A.alpha = s->alpha;
-    A.gamma = s->gamma;
-    A.eps = s->eps;
     for (int64_t c = nsteps > 0 ? p.nckpt - 1 : -1; c >= 0; --c) {
         const int64_t s0 = c * every;
         const int64_t e0 = (s0 + every < nsteps ? s0 + every : nsteps) - 1;
@@ -206,8 +210,8 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
             e = cudaMemcpyAsync(segctl, ck + round256(buf), sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
         for (int64_t m = s0; e == cudaSuccess && m <= e0; ++m) {
             if (!fixed_a)
-                e = cudaMemcpyAsync(ahist + (m - s0), &segctl->a, sizeof(double), cudaMemcpyDeviceToDevice,
-                                    s->stream);
+                e = cudaMemcpyAsync(khist + (m - s0) * kConstSlot, ctl_consts<T>(segctl), sizeof(StepConsts<T>),
+                                    cudaMemcpyDeviceToDevice, s->stream);
             if (e == cudaSuccess && m < e0) e = recompute_step<T>(s, scratch, p, every, m, m - s0);
         }
         if (e != cudaSuccess) return cuda_fail(s, e, "recomputation");
@@ -215,22 +219,21 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
             A.fwd = (const T *)slot_ptr(scratch, p, s, m - s0 + 1);
             A.cot_in = cot[cur];
             A.cot_out = cot[cur ^ 1];
-            A.a = fixed_a ? &segctl->a : ahist + (m - s0);
+            A.k = fixed_a ? ctl_consts<T>(segctl) : (const StepConsts<T> *)(khist + (m - s0) * kConstSlot);
             e = launch_adjoint_step<T>(A, s->limiter, s->stream);
             if (e != cudaSuccess) return cuda_fail(s, e, "adjoint step launch");
             cur ^= 1;
         }
     }
     const char *ck0 = scratch;
-    e = launch_adjoint_init<T>((const T *)ck0, s->L, (const double *)(ck0 + round256(buf)) + 2, s->alpha, s->gamma,
-                               cot[cur], (T *)dLdu0, s->stream);
+    e = launch_adjoint_init<T>((const T *)ck0, s->L, ctl_consts<T>((const DevCtl *)(ck0 + round256(buf))), cot[cur],
+                               (T *)dLdu0, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "initialisation adjoint launch");
     return VLBM_OK;
 }
 
 }  // namespace
 
-static_assert(offsetof(DevCtl, a) == 2 * sizeof(double), "a is the third field of the control block");
 
 extern "C" {
 

@@ -28,8 +28,7 @@ struct AdjArgs {
     int pitch, nx, ny;
     const T *cot_in;       // cotangent of s^{n+1}: 20 compact planes
     T *cot_out;            // cotangent of s^n: 20 compact planes
-    const double *a;       // kinetic speed a^n of the step (device scalar)
-    double alpha, gamma, eps;
+    const StepConsts<T> *k;  // constants of the step (kinetic speed a^n as the forward run used it)
 };
 
 // w^T df/du for the Euler x-flux (dir 0) or y-flux (dir 1) at state u.
@@ -126,7 +125,7 @@ __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= A.nx || j >= A.ny) return;
-    const StepConsts<T> k = make_consts<T>(*A.a, A.alpha, A.gamma, A.eps);
+    const StepConsts<T> k = *A.k;
     CellLoad<T> L{A.fwd, A.plane, A.pitch};
     const long long N = (long long)A.nx * A.ny;
     // ---------------------------------------------------------- forward quantities
@@ -238,14 +237,12 @@ __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
 // read from the padded initial state and a^0 held fixed.
 template <typename T>
 __global__ void __launch_bounds__(256) k_adjoint_init(const T *init_state, long long plane, int pitch, int nx,
-                                                      int ny, const double *a_ptr, double alpha, double gamma,
-                                                      const T *cot, T *grad) {
+                                                      int ny, const StepConsts<T> *kc, const T *cot, T *grad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= nx || j >= ny) return;
     const long long N = (long long)nx * ny, c = (long long)j * nx + i;
-    const double a = *a_ptr;
-    const T w = T((1.0 - alpha) / 4.0), inv2a = T(1.0 / (2.0 * a)), gm1 = T(gamma - 1.0);
+    const T w = kc->w, inv2a = kc->inv2a, gm1 = kc->gm1;
     const CellLoad<T> L{init_state, plane, pitch};
     T u[4], wx[4], wy[4], rx[4], ry[4];
 #pragma unroll

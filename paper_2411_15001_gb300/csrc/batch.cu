@@ -408,6 +408,7 @@ int vlbm_batch_monitors(vlbm_batch *b, int32_t i, vlbm_monitor_t *out) {
     out->nonfinite_cells = h.nonfinite_last;
     out->first_bad_step = h.first_bad_step;
     out->min_rho = h.min_rho;
+    out->min_internal_energy = h.min_rhoe;
     for (int c = 0; c < 4; ++c) out->sum[c] = h.sum_last[c];
     out->theta_p_fp64_faces = h.fp64_last;
     out->done = h.done;

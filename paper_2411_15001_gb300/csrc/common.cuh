@@ -80,12 +80,13 @@ template <> struct SumAcc<double> {
 // the FP64 solve.
 template <typename T>
 struct Monitor {
-    T lam, minrho;
+    T lam, minrho, minrhoe;
     SumAcc<T> sum;
     unsigned int bad, nonfin, fp64;
     __device__ __forceinline__ void init() {
         lam = T(0);
         minrho = T(INFINITY);
+        minrhoe = T(INFINITY);
         sum.zero();
         bad = nonfin = fp64 = 0u;
     }
@@ -93,6 +94,12 @@ struct Monitor {
         const T sp = cell_speed(u, gamma, gm1);   // NaN or inf if any component is
         lam = pmax(lam, sp);
         minrho = pmin(minrho, u[0]);
+        // internal energy in the state's precision (reported; admissibility below
+        // is decided by the exact test)
+        T ir;
+        if constexpr (is_f64<T>::value) ir = 1.0 / u[0];
+        else ir = fast_rcp(u[0]);
+        minrhoe = pmin(minrhoe, u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ir);
         sum.add_cell(u);
         if (!(sp <= T(3.0e38))) ++nonfin;
         else if (!in_G(u)) ++bad;
@@ -101,6 +108,7 @@ struct Monitor {
         for (int off = 16; off > 0; off >>= 1) {
             lam = pmax(lam, __shfl_xor_sync(0xffffffffu, lam, off));
             minrho = pmin(minrho, __shfl_xor_sync(0xffffffffu, minrho, off));
+            minrhoe = pmin(minrhoe, __shfl_xor_sync(0xffffffffu, minrhoe, off));
             sum.shfl_add(off);
             bad += __shfl_xor_sync(0xffffffffu, bad, off);
             nonfin += __shfl_xor_sync(0xffffffffu, nonfin, off);
@@ -127,6 +135,7 @@ __device__ void block_publish(Monitor<T> &m, DevCtl *C) {
         if (lane == 0) {
             atomicMax(&C->lam_key, ordered_key((double)m.lam));
             atomicMin(&C->minrho_key, ordered_key((double)m.minrho));
+            atomicMin(&C->minrhoe_key, ordered_key((double)m.minrhoe));
             for (int c = 0; c < 4; ++c) atomicAdd(&C->sum[c], m.sum.value(c));
             if (m.bad) atomicAdd(&C->bad, (unsigned long long)m.bad);
             if (m.nonfin) atomicAdd(&C->nonfinite, (unsigned long long)m.nonfin);
@@ -138,6 +147,7 @@ __device__ void block_publish(Monitor<T> &m, DevCtl *C) {
 __device__ __forceinline__ void reset_slots(DevCtl *C) {
     C->lam_key = 0ull;
     C->minrho_key = ~0ull;
+    C->minrhoe_key = ~0ull;
     C->bad = 0ull;
     C->nonfinite = 0ull;
     C->fp64_faces = 0ull;
@@ -150,6 +160,17 @@ __device__ __forceinline__ void reset_slots(DevCtl *C) {
 __device__ __forceinline__ double next_speed(const DevCtl *C, double lam) {
     return C->a_fixed > 0.0 ? C->a_fixed : 2.0 * lam / (1.0 - C->alpha);
 }
+
+// The constants of the step about to run with kinetic speed C->a, in both
+// precisions (FP64 divisions once per step instead of once per CTA or cell).
+__device__ __forceinline__ void set_consts(DevCtl *C) {
+    C->kf = make_consts<float>(C->a, C->alpha, C->gamma, C->eps);
+    C->kd = make_consts<double>(C->a, C->alpha, C->gamma, C->eps);
+}
+
+template <typename T> __device__ __forceinline__ StepConsts<T> consts_of(const DevCtl *C);
+template <> __device__ __forceinline__ StepConsts<float> consts_of<float>(const DevCtl *C) { return C->kf; }
+template <> __device__ __forceinline__ StepConsts<double> consts_of<double>(const DevCtl *C) { return C->kd; }
 
 // Step control for the next step: Delta t = dx / a, shortened to land on t_end.
 __device__ __forceinline__ void plan_next(DevCtl *C, double t, double a_free) {
@@ -167,6 +188,7 @@ __device__ __forceinline__ void plan_next(DevCtl *C, double t, double a_free) {
     C->a = a;
     C->dt = dt;
     C->last = last;
+    set_consts(C);
 }
 
 // Called by one thread of the last CTA to finish a step: the grid-wide max of
@@ -176,6 +198,7 @@ __device__ inline void finalize_step(DevCtl *C) {
     volatile DevCtl *V = C;
     const double lam = key_to_double(V->lam_key);
     const double minrho = key_to_double(V->minrho_key);
+    const double minrhoe = key_to_double(V->minrhoe_key);
     const unsigned long long bad = V->bad, nonfin = V->nonfinite;
     C->fp64_last = (long long)V->fp64_faces;
     double s[4];
@@ -184,6 +207,7 @@ __device__ inline void finalize_step(DevCtl *C) {
     const double t1 = C->t + C->dt;
     C->lambda = lam;
     C->min_rho = minrho;
+    C->min_rhoe = minrhoe;
     C->bad_last = (long long)bad;
     C->nonfinite_last = (long long)nonfin;
     for (int c = 0; c < 4; ++c) C->sum_last[c] = s[c];
@@ -309,6 +333,7 @@ __global__ void k_init_load(StepArgs<T> A, const T *__restrict__ rho, const T *_
             C->invalid_init = bad ? 1 : 0;
             C->lambda = lam;
             C->min_rho = key_to_double(V->minrho_key);
+            C->min_rhoe = key_to_double(V->minrhoe_key);
             for (int c = 0; c < 4; ++c) C->sum_last[c] = V->sum[c];
             double a_free = next_speed(C, lam);
             if (!(a_free > 0.0) || !isfinite(a_free)) {
@@ -333,7 +358,7 @@ __global__ void k_init_pops(StepArgs<T> A) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= A.nx || j >= A.ny) return;
-    const StepConsts<T> k = make_consts<T>(A.ctl->a, A.alpha, A.gamma, A.eps);
+    const StepConsts<T> k = consts_of<T>(A.ctl);
     const long long d = cidx(A, i, j);
     T u[4], f[4], g[4], M1[4], M2[4], M3[4], M4[4];
 #pragma unroll

@@ -49,6 +49,7 @@ __global__ void k_load_header(DevCtl *C, const unsigned char *src) {
     C->invalid_init = 0;
     C->first_bad_step = -1;
     reset_slots(C);
+    set_consts(C);
 }
 
 cudaError_t launch_ctl_reset(DevCtl *ctl, double dx, double alpha, double a_fixed, double eps,
@@ -65,6 +66,18 @@ cudaError_t launch_set_tend(DevCtl *ctl, double t_end, cudaStream_t s) {
 cudaError_t launch_load_header(DevCtl *ctl, const void *src, cudaStream_t s) {
     k_load_header<<<1, 1, 0, s>>>(ctl, (const unsigned char *)src);
     return cudaGetLastError();
+}
+
+// Launch shapes shared by the stream launchers and the graph builder.
+void simple_launch_shape(int nx, int ny, dim3 *grid, dim3 *block) {
+    *block = dim3(32, 8);
+    *grid = dim3((nx + 31) / 32, (ny + 7) / 8);
+}
+
+void ghosts_launch_shape(int nx, int ny, dim3 *grid, dim3 *block) {
+    const long long total = 4ll * (nx + 4) + 4ll * ny;
+    *block = dim3(128);
+    *grid = dim3((unsigned)((total + 127) / 128));
 }
 
 }  // namespace vlbm

@@ -13,9 +13,9 @@ inline dim3 cell_grid(int nx, int ny) { return dim3((nx + kBX - 1) / kBX, (ny + 
 
 template <>
 cudaError_t launch_ghosts<VLBM_T>(const StepArgs<VLBM_T> &A, cudaStream_t s) {
-    const long long total = 4ll * (A.nx + 4) + 4ll * A.ny;
-    const int thr = 128;
-    k_ghosts<VLBM_T><<<(unsigned)((total + thr - 1) / thr), thr, 0, s>>>(A);
+    dim3 grd, blk;
+    ghosts_launch_shape(A.nx, A.ny, &grd, &blk);
+    k_ghosts<VLBM_T><<<grd, blk, 0, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -32,7 +32,8 @@ cudaError_t launch_init<VLBM_T>(const StepArgs<VLBM_T> &A, const VLBM_T *rho, co
 
 template <>
 cudaError_t launch_step_simple<VLBM_T>(const StepArgs<VLBM_T> &A, cudaStream_t s) {
-    const dim3 blk(kBX, kBY), grd = cell_grid(A.nx, A.ny);
+    dim3 grd, blk;
+    simple_launch_shape(A.nx, A.ny, &grd, &blk);
     switch (A.limiter) {
         case VLBM_LIM_FIRST_ORDER: k_step_simple<VLBM_T, VLBM_LIM_FIRST_ORDER><<<grd, blk, 0, s>>>(A); break;
         case VLBM_LIM_NONE: k_step_simple<VLBM_T, VLBM_LIM_NONE><<<grd, blk, 0, s>>>(A); break;
@@ -42,6 +43,22 @@ cudaError_t launch_step_simple<VLBM_T>(const StepArgs<VLBM_T> &A, cudaStream_t s
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <>
+const void *simple_kernel_fn<VLBM_T>(int limiter) {
+    switch (limiter) {
+        case VLBM_LIM_FIRST_ORDER: return (const void *)k_step_simple<VLBM_T, VLBM_LIM_FIRST_ORDER>;
+        case VLBM_LIM_NONE: return (const void *)k_step_simple<VLBM_T, VLBM_LIM_NONE>;
+        case VLBM_LIM_PP: return (const void *)k_step_simple<VLBM_T, VLBM_LIM_PP>;
+        case VLBM_LIM_LMP: return (const void *)k_step_simple<VLBM_T, VLBM_LIM_LMP>;
+        default: return (const void *)k_step_simple<VLBM_T, VLBM_LIM_RLMP>;
+    }
+}
+
+template <>
+const void *ghosts_kernel_fn<VLBM_T>() {
+    return (const void *)k_ghosts<VLBM_T>;
 }
 
 namespace {

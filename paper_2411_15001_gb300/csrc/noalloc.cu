@@ -73,9 +73,8 @@ struct CompactLoad {
 
 template <typename T, int LIM>
 __global__ void __launch_bounds__(kNaBX *kNaBY)
-    k_step_noalloc(CompactLoad<T> L, T *__restrict__ out, double a, double alpha, double gamma,
-                   double eps, int sponge, NoAllocPartial *part) {
-    const StepConsts<T> k = make_consts<T>(a, alpha, gamma, eps);
+    k_step_noalloc(CompactLoad<T> L, T *__restrict__ out, const StepConsts<T> k, int sponge,
+                   NoAllocPartial *part) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     Monitor<T> mon;
@@ -157,12 +156,13 @@ cudaError_t launch_noalloc(const vlbm_grid *g, int limiter, const void *in, void
     NoAllocPartial *part = (NoAllocPartial *)scratch;
     NoAllocResult *res = (NoAllocResult *)(scratch + kNoAllocMaxBlocks * sizeof(NoAllocPartial));
     T *o = (T *)out;
+    const StepConsts<T> k = make_consts<T>(a, alpha, gamma, eps);
     switch (limiter) {
-        case VLBM_LIM_FIRST_ORDER: k_step_noalloc<T, VLBM_LIM_FIRST_ORDER><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
-        case VLBM_LIM_NONE: k_step_noalloc<T, VLBM_LIM_NONE><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
-        case VLBM_LIM_PP: k_step_noalloc<T, VLBM_LIM_PP><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
-        case VLBM_LIM_LMP: k_step_noalloc<T, VLBM_LIM_LMP><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
-        default: k_step_noalloc<T, VLBM_LIM_RLMP><<<grd, blk, 0, s>>>(L, o, a, alpha, gamma, eps, sponge, part); break;
+        case VLBM_LIM_FIRST_ORDER: k_step_noalloc<T, VLBM_LIM_FIRST_ORDER><<<grd, blk, 0, s>>>(L, o, k, sponge, part); break;
+        case VLBM_LIM_NONE: k_step_noalloc<T, VLBM_LIM_NONE><<<grd, blk, 0, s>>>(L, o, k, sponge, part); break;
+        case VLBM_LIM_PP: k_step_noalloc<T, VLBM_LIM_PP><<<grd, blk, 0, s>>>(L, o, k, sponge, part); break;
+        case VLBM_LIM_LMP: k_step_noalloc<T, VLBM_LIM_LMP><<<grd, blk, 0, s>>>(L, o, k, sponge, part); break;
+        default: k_step_noalloc<T, VLBM_LIM_RLMP><<<grd, blk, 0, s>>>(L, o, k, sponge, part); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -30,6 +30,9 @@ struct vlbm_state {
     bool loaded;        // set_conserved or load has run
     bool tend_active;   // a final time is armed on the device
     bool at_init;       // the state is u_k = M_k(u_0) at n = 0, as set_conserved leaves it
+    // CUDA graph of kGraphSteps consecutive steps (built on first use)
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
     // checkpoints written by the last vlbm_rollout (consumed by vlbm_adjoint)
     const void *roll_scratch;
     int64_t roll_steps;
@@ -76,7 +79,18 @@ inline StepArgs<T> args_of(const vlbm_state *s) {
     return A;
 }
 
-inline bool use_fused(const vlbm_state *s) { return s->have_tmap && s->kernel != VLBM_KERNEL_SIMPLE; }
+// VLBM_KERNEL_AUTO. FP32: below this many cells a grid has too few row-marching
+// work items to fill the GPU and the one-thread-per-cell kernel is faster (PP on a
+// GB300: 45 vs 56 us at 512^2, 141 vs 101 us at 1024^2). FP64: every face's theta_p
+// solve makes the step FP64-bound, where the one-thread-per-cell kernel's many warps
+// per SM win at every size measured (0.62 vs 1.50 ms at 512^2, 9.4 vs 10.3 ms at 2048^2).
+constexpr long long kAutoFusedMinCells = 1ll << 19;
+
+inline bool use_fused(const vlbm_state *s) {
+    if (!s->have_tmap || s->kernel == VLBM_KERNEL_SIMPLE) return false;
+    if (s->kernel == VLBM_KERNEL_FUSED) return true;
+    return s->precision == VLBM_FP32 && (long long)s->grid.nx * s->grid.ny >= kAutoFusedMinCells;
+}
 
 // Arguments of the row-marching kernel for this grid (descriptor block of the workspace).
 template <typename T>
@@ -94,6 +108,8 @@ inline FusedBatchArgs<T> batch_args_of(const vlbm_state *s) {
 }
 
 cudaError_t step_once(vlbm_state *s);           // one step of the state's configured kernel
+cudaError_t step_many(vlbm_state *s, int64_t n); // n steps, whole groups of kGraphSteps from a graph
+constexpr int kGraphSteps = 64;
 int read_ctl(vlbm_state *s, DevCtl *h);         // synchronous copy of the control block
 int set_conserved(vlbm_state *s, const void *rho, const void *mom, const void *E);
 

@@ -214,10 +214,17 @@ struct FusedCtx {
         }
         // ---------------------------------------------------------------- P3
         T tx, ty;
+        // theta is needed for the x-faces of columns kFHalo-1 .. kFHalo+kFOut-1 and the
+        // y-faces of the strip's own columns, inside the grid. The other threads hold
+        // halo padding or (past the last column) TMA fill, on which the FP32 screen
+        // would fail and send the face to the FP64 solve: they skip theta.
+        const bool live = b >= kFHalo - 1 && b < kFHalo + kFOut && c < D.nx;
         if (LIM == VLBM_LIM_FIRST_ORDER) {
             tx = ty = T(0);
         } else if (LIM == VLBM_LIM_NONE) {
             tx = ty = T(1);
+        } else if (!live) {
+            tx = ty = T(0);
         } else {
             T trx, try_;
             if (LIM == VLBM_LIM_PP) {
@@ -341,7 +348,7 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         for (int q = 0; q < 4; ++q) geo.bc[q] = D.bc[q];
         geo.sponge = D.sponge;
         const long long n = C->n;
-        const StepConsts<T> k = make_consts<T>(C->a, B.alpha, B.gamma, B.eps);
+        const StepConsts<T> k = consts_of<T>(C);
         const int local = item - D.item0;
         const int s = local % D.strips, ch = local / D.strips;
         Monitor<T> mon;

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_step_simple(StepArgs<T> A) {
     const long long n = C->n;
     CellLoad<T> L{(n & 1) ? A.buf1 : A.buf0, A.plane, A.pitch};
     T *__restrict__ out = (n & 1) ? A.buf0 : A.buf1;
-    const StepConsts<T> k = make_consts<T>(C->a, A.alpha, A.gamma, A.eps);
+    const StepConsts<T> k = consts_of<T>(C);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     Monitor<T> mon;

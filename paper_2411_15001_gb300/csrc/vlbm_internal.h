@@ -60,6 +60,19 @@ __host__ __device__ inline double key_to_double(unsigned long long k) {
 #endif
 }
 
+// Constants of one step, derived from the kinetic speed a^n (Sec. 2 and Sec. 3.2).
+template <typename T>
+struct StepConsts {
+    T a, two_a, inv2a;        // a, 2a, 1/(2a)
+    T kappa, two_kappa, inv2k;  // kappa = a (1 - alpha) / 2, 2 kappa, 1/(2 kappa)
+    T w, alpha;               // (1 - alpha)/4 and alpha
+    T gamma, gm1;             // gamma, gamma - 1
+    T eps;                    // epsilon of the PP and pressure bounds
+    float eps_margin;         // 2 eps as float, the FP32 screen's allowance for epsilon
+    float rmax1;              // FP32 screen: a lower bound of kappa / (1 + eps) (see below)
+    double kappa64, eps64;    // FP64 copies for the internal-energy solve
+};
+
 // Device control block: time-step state written by the last CTA of each step
 // (the grid-wide lambda^n dependency of Sec. 4 is resolved at the kernel
 // boundary), the per-step reduction slots, and the published monitors.
@@ -79,6 +92,7 @@ struct DevCtl {
     // reduction slots of the step in flight (reset by the finaliser)
     unsigned long long lam_key;      // ordered key of max lambda
     unsigned long long minrho_key;   // ordered key of min rho
+    unsigned long long minrhoe_key;  // ordered key of min internal energy E - |m|^2 / (2 rho)
     unsigned long long bad;          // cells outside G
     unsigned long long nonfinite;    // non-finite cells
     unsigned long long fp64_faces;   // faces whose theta_p needed the FP64 solve
@@ -88,15 +102,19 @@ struct DevCtl {
     // published monitors of the current state
     double lambda;
     double min_rho;
+    double min_rhoe;       // min internal energy per volume of the current state
     long long bad_last;
     long long nonfinite_last;
     long long fp64_last;
     double sum_last[4];
     // constants
     double dx, alpha, a_fixed, eps, gamma;
+    // the next step's constants (derived from a), set whenever a is
+    StepConsts<float> kf;
+    StepConsts<double> kd;
 };
 
-static_assert(sizeof(DevCtl) == 264, "bench.py reads the control block size");
+static_assert(sizeof(DevCtl) == 464, "bench.py reads the control block size");
 
 // One grid as the row-marching kernel sees it (device memory, 64-byte aligned).
 template <typename T>
@@ -167,6 +185,12 @@ template <typename T> cudaError_t launch_step_fused(const FusedBatchArgs<T> &a, 
 template <typename T> int fused_occupancy(int limiter);   // CTAs per SM of the fused kernel
 // Kernel function and dynamic shared memory of the fused kernel, for graph nodes.
 template <typename T> const void *fused_kernel_fn(int limiter, size_t *smem);
+// Kernel functions and launch shapes of the one-thread-per-cell step and of the
+// ghost-frame pass (for CUDA graph kernel nodes).
+template <typename T> const void *simple_kernel_fn(int limiter);
+template <typename T> const void *ghosts_kernel_fn();
+void simple_launch_shape(int nx, int ny, dim3 *grid, dim3 *block);
+void ghosts_launch_shape(int nx, int ny, dim3 *grid, dim3 *block);
 bool encode_state_tmap(CUtensorMap *out, void *base, const Layout &L);
 constexpr int kFusedOut = 120;                             // output columns per strip
 constexpr int kFusedBox = 128;                             // TMA box width (columns)

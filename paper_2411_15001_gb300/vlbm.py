@@ -38,7 +38,8 @@ class vlbm_monitor_t(ctypes.Structure):
                 ("bad_cells", ctypes.c_int64), ("nonfinite_cells", ctypes.c_int64),
                 ("first_bad_step", ctypes.c_int64), ("min_rho", ctypes.c_double),
                 ("sum", ctypes.c_double * 4), ("theta_p_fp64_faces", ctypes.c_int64),
-                ("done", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("done", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("min_internal_energy", ctypes.c_double)]
 
 
 class vlbm_step_result(ctypes.Structure):
@@ -354,7 +355,7 @@ class VLBM:
                 "bad_cells": m.bad_cells, "nonfinite_cells": m.nonfinite_cells,
                 "first_bad_step": m.first_bad_step, "min_rho": m.min_rho, "sum": list(m.sum),
                 "theta_p_fp64_faces": m.theta_p_fp64_faces,
-                "done": m.done}
+                "min_internal_energy": m.min_internal_energy, "done": m.done}
 
     def sync(self) -> int:
         return vlbm_sync(self._s)
@@ -486,7 +487,8 @@ class VLBMBatch:
         return {"status": m.status, "n": m.n, "t": m.t, "a": m.a, "lambda": m.lambda_,
                 "bad_cells": m.bad_cells, "nonfinite_cells": m.nonfinite_cells,
                 "first_bad_step": m.first_bad_step, "min_rho": m.min_rho, "sum": list(m.sum),
-                "theta_p_fp64_faces": m.theta_p_fp64_faces, "done": m.done}
+                "theta_p_fp64_faces": m.theta_p_fp64_faces,
+                "min_internal_energy": m.min_internal_energy, "done": m.done}
 
     def tuning(self) -> dict:
         rc, t = vlbm_batch_get_tuning(self._b)

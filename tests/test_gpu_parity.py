@@ -232,3 +232,39 @@ def test_fused_equals_simple_fp32(lim, tol):
     a, _ = gpu_run(p, lim, V.FP32, nsteps=50, kernel=V.KERNEL_SIMPLE)
     b, _ = gpu_run(p, lim, V.FP32, nsteps=50, kernel=V.KERNEL_FUSED)
     assert l1_rel(b[:4], a[:4]) <= tol
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec", [V.FP64, V.FP32])
+def test_graph_replay_equals_single_launches(kernel, prec):
+    """vlbm_step replays whole groups of 64 steps from a CUDA graph; with kernel
+    timing on it launches every step alone. Both give the same state bit for bit."""
+    import torch
+
+    p = W.quadrant_riemann(70, 45, seed=3, bc=(2, 1, 0, 0))
+    out = []
+    for timed in (False, True):
+        s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, limiter=V.LIM_LMP, precision=prec, kernel=kernel,
+                   device="cuda:0")
+        dt = torch.float64 if prec == V.FP64 else torch.float32
+        c = torch.tensor(p.conserved(), dtype=dt, device="cuda:0")
+        s.set_conserved(c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+        s.profile(timed)
+        s.step(200)          # 3 graph replays + 8 single launches when not timed
+        s.step(64)
+        out.append((s.state_planes().cpu().numpy(), s.monitors()))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1]["n"] == out[1][1]["n"] == 264 and out[0][1]["t"] == out[1][1]["t"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("prec,rtol", [(V.FP64, 1e-13), (V.FP32, 1e-5)])
+def test_monitor_min_density_and_internal_energy(kernel, prec, rtol):
+    """min rho and min (E - |m|^2 / (2 rho)) of the current state against the oracle's."""
+    p = W.quadrant_riemann(70, 45, seed=5, bc=(1, 1, 2, 2))
+    got, mon = gpu_run(p, V.LIM_PP, prec, nsteps=25, kernel=kernel)
+    ref = oracle_run(p, V.LIM_PP, nsteps=25)["state"]
+    rhoe = ref[3] - 0.5 * (ref[1] ** 2 + ref[2] ** 2) / ref[0]
+    assert abs(mon["min_rho"] - ref[0].min()) <= rtol * ref[0].min()
+    assert abs(mon["min_internal_energy"] - rhoe.min()) <= 10 * rtol * rhoe.min()
