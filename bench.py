@@ -354,7 +354,9 @@ def bench_batched(dev, steps: int = 500, count: int = 256):
     e1.record(b.stream)
     torch.cuda.synchronize(dev)
     ms_b = e0.elapsed_time(e1)
-    status = [b.monitors(i)["status"] for i in range(count)]
+    mons = [b.monitors(i) for i in range(count)]
+    status = [m["status"] for m in mons]
+    fp64_faces = sum(m["theta_p_fp64_faces"] for m in mons)
     b.close()
     del b
     solvers = [V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, gamma=p.gamma, limiter=V.LIM_PP, precision=V.FP32,
@@ -380,7 +382,8 @@ def bench_batched(dev, steps: int = 500, count: int = 256):
             "sequential_mlups": cells * steps / (ms_s / 1e3) / 1e6,
             "ratio": ms_s / ms_b, "batched_ms_per_step": ms_b / steps,
             "sequential_ms_per_step": ms_s / steps, "tuning": tuning,
-            "statuses_nonzero": sum(1 for x in status if x)}
+            "statuses_nonzero": sum(1 for x in status if x),
+            "fp64_theta_p_faces_last_step": fp64_faces}
 
 
 def bench_adjoint(dev, n: int = 512, steps: int = 500, every: int = 50):
