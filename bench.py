@@ -132,6 +132,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The maximum of x over all ranks (x itself without a process group)."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, cells: int, steps: int, seconds: float) -> float:
+    """Cell updates of all ranks (each advances its own replica) over the slowest rank's time."""
+    return world * cells * steps / seconds / 1e6
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -254,12 +270,9 @@ def run_ours(args):
     kernel_ms, launches = solver.profile_read()
     solver.profile(False)
     mon = solver.monitors()
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, dev)
     cells = p.nx * p.ny
-    value = world * cells * args.steps / (ms_max / 1e3) / 1e6
+    value = whole_job_mlups(world, cells, args.steps, ms_max / 1e3)
 
     # ---------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -280,11 +293,8 @@ def run_ours(args):
         out_dev = torch.cat([rho[None], mom, E[None]])
         out_host.copy_(out_dev, non_blocking=True)
         torch.cuda.synchronize(dev)
-        t_e2e = time.perf_counter() - t0
-        t_t = torch.tensor([t_e2e], device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(t_t, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": world * cells * args.steps / float(t_t.item()) / 1e6, "unit": "MLUPS",
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": whole_job_mlups(world, cells, args.steps, t_e2e), "unit": "MLUPS",
                "h2d_bytes_per_step": host.numel() * 4 / args.steps,
                "d2h_bytes_per_step": (out_host.numel() * 4) / args.steps + CTL_BYTES,
                "positivity_violations": int(bad)}

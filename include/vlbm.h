@@ -77,8 +77,11 @@ extern "C" {
 #define VLBM_BC_REFLECTIVE 2
 
 /* Arithmetic of the state. FP32: populations, collision and density bounds
- * in float; the internal-energy bound theta_p is solved in double wherever a
- * float evaluation cannot prove it inactive; conservation sums in double. */
+ * in float; the internal-energy bound theta_p is settled per face by a float
+ * screen (theta_p >= min(1, theta_rho) proved with rigorous error bounds), else
+ * by a tight float interval (a certified lower bound), else by a solve whose
+ * cancelling quantities are formed in double -- theta never exceeds the exact
+ * theta_p; conservation sums in double. FP64: every formula in double. */
 #define VLBM_FP64 0
 #define VLBM_FP32 1
 
@@ -120,8 +123,9 @@ typedef struct {
     int64_t first_bad_step;    /* first step whose output left G (or went non-finite); -1 if none */
     double min_rho;            /* min density of the current state */
     double sum[4];             /* FP64 sums of rho, m1, m2, E over the cells of the current state */
-    int64_t theta_p_fp64_faces; /* faces of the last step whose theta_p needed the FP64 solve
-                                   (FP32 state; every face for an FP64 state) */
+    int64_t theta_p_fp64_faces; /* faces of the last step whose theta_p needed the FP64 solve: FP32
+                                   state, where neither the float screen nor a tight float interval
+                                   settled it; FP64 state, every face */
     int32_t done;              /* 1 once vlbm_step_to has reached its final time */
     int32_t status;            /* sticky VLBM_OK / VLBM_E_* of the device */
     double min_internal_energy; /* min of E - |m|^2 / (2 rho) over the cells of the current state,

@@ -1,0 +1,70 @@
+"""The paper's 1D validation cases on the GPU (needs a GB300): the near-vacuum
+isentropic wave (gamma = 3, density down to 5e-7, Sec. 4.4) and the LeBlanc
+tube (gamma = 5/3, pressure ratio 1e6, Sec. 4.5). FP64: bit for bit the oracle's
+run to the final time. FP32: every step admissible (the monitors' exact test) and
+the final density within L1 1e-3 of the oracle's.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from paper_2411_15001_gb300 import workloads as W
+from tests.gpu_helpers import l1_rel, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_15001_gb300 import vlbm as V  # noqa: E402
+
+
+def _gpu_to(p, lim, prec, t_end, kernel, sponge=0):
+    dt = torch.float64 if prec == V.FP64 else torch.float32
+    s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, gamma=p.gamma, limiter=lim, precision=prec, kernel=kernel,
+               device="cuda:0", sponge=sponge)
+    c = torch.tensor(p.conserved(), dtype=dt, device="cuda:0")
+    s.set_conserved(c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+    s.step_to(t_end, 10 ** 6)
+    planes = s.state_planes().double().cpu().numpy()
+    m = s.monitors()            # first_bad_step covers every step of the run
+    s.close()
+    return planes, m
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(case, lim):
+    make, t_end, sponge = CASES[case]
+    return oracle_run(make(), lim, t_end=t_end, sponge=sponge)
+
+
+CASES = {
+    "near_vacuum": (lambda: W.near_vacuum_wave(200), 0.1, 0),
+    "leblanc": (lambda: W.leblanc(1000), 6.0, 5),
+}
+
+
+@pytest.mark.parametrize("kernel", [V.KERNEL_SIMPLE, V.KERNEL_FUSED])
+@pytest.mark.parametrize("lim", [V.LIM_PP, V.LIM_RLMP])
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp64_equals_oracle(case, lim, kernel):
+    make, t_end, sponge = CASES[case]
+    p = make()
+    got, mon = _gpu_to(p, lim, V.FP64, t_end, kernel, sponge)
+    ref = _oracle(case, lim)
+    assert mon["status"] == 0 and mon["first_bad_step"] == -1
+    assert mon["n"] == ref["n"] and mon["t"] == ref["t"]
+    assert np.array_equal(got, ref["state"])
+
+
+@pytest.mark.parametrize("lim", [V.LIM_PP, V.LIM_LMP, V.LIM_RLMP])
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp32_admissible_and_close(case, lim):
+    make, t_end, sponge = CASES[case]
+    p = make()
+    got, mon = _gpu_to(p, lim, V.FP32, t_end, V.KERNEL_FUSED, sponge)
+    assert mon["status"] == 0 and mon["first_bad_step"] == -1
+    ref = _oracle(case, lim)
+    assert l1_rel(got[0], ref["state"][0]) <= 1e-3
