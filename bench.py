@@ -39,7 +39,7 @@ BYTES_PER_LU = 160           # 20 FP32 values read + 20 written per cell update
 N_SIDE = 4096
 EPS = 1e-13
 FALLBACK_HBM_GBS = 6800.0
-CTL_BYTES = 280              # device control block read back by vlbm_monitors
+CTL_BYTES = 472              # device control block read back by vlbm_monitors
 SPONGE = 5                   # theta = 0 layer at zero-gradient sides, as the paper pairs them (Sec. 4.2)
 
 
@@ -369,21 +369,27 @@ def bench_batched(dev, steps: int = 500, count: int = 256):
     fp64_faces = sum(m["theta_p_fp64_faces"] for m in mons)
     b.close()
     del b
-    solvers = [V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, gamma=p.gamma, limiter=V.LIM_PP, precision=V.FP32,
-                      eps=EPS, device=dev, sponge=SPONGE) for p in probs]
-    load(lambda i, r, m, e: solvers[i].set_conserved(r, m, e))
-    for s in solvers:
-        s.step(3)
-    torch.cuda.synchronize(dev)
-    stream = solvers[0].stream
-    e0.record(stream)
-    for s in solvers:
-        s.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_s = e0.elapsed_time(e1)
-    for s in solvers:
-        s.close()
+    def sequential(kernel):
+        """The same problems one after another (500 steps each, graph replays), one
+        solver per grid, on one stream."""
+        solvers = [V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, gamma=p.gamma, limiter=V.LIM_PP, precision=V.FP32,
+                          eps=EPS, device=dev, sponge=SPONGE, kernel=kernel) for p in probs]
+        load(lambda i, r, m, e: solvers[i].set_conserved(r, m, e))
+        for s in solvers:
+            s.step(3)
+        torch.cuda.synchronize(dev)
+        stream = solvers[0].stream
+        e0.record(stream)
+        for s in solvers:
+            s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        for s in solvers:
+            s.close()
+        return e0.elapsed_time(e1)
+
+    ms_s = sequential(V.KERNEL_FUSED)      # the row-marching kernel, as the batch uses
+    ms_a = sequential(V.KERNEL_AUTO)       # each grid with the kernel that is faster for it
     return {"workload": f"{count} quadrant Riemann problems, sides in {{64..1024}} step 64 (seed 1), "
                         f"FP32 PP eps=1e-13, zero-gradient sides with a {SPONGE}-cell theta = 0 sponge "
                         f"(Sec. 4.2), {steps} steps each",
@@ -391,7 +397,12 @@ def bench_batched(dev, steps: int = 500, count: int = 256):
             "batched_mlups": cells * steps / (ms_b / 1e3) / 1e6,
             "sequential_mlups": cells * steps / (ms_s / 1e3) / 1e6,
             "ratio": ms_s / ms_b, "batched_ms_per_step": ms_b / steps,
-            "sequential_ms_per_step": ms_s / steps, "tuning": tuning,
+            "sequential_ms_per_step": ms_s / steps,
+            "sequential": "each grid alone with the same row-marching kernel, CUDA graph replays of 64 steps",
+            "sequential_auto_mlups": cells * steps / (ms_a / 1e3) / 1e6, "ratio_vs_auto": ms_a / ms_b,
+            "sequential_auto": "each grid alone with the kernel the library picks for its size (the "
+                               "one-thread-per-cell kernel below 2^19 cells)",
+            "tuning": tuning,
             "statuses_nonzero": sum(1 for x in status if x),
             "fp64_theta_p_faces_last_step": fp64_faces}
 

@@ -108,7 +108,8 @@ typedef struct {
     int32_t kernel;   /* VLBM_KERNEL_*; default AUTO */
     int32_t sponge;   /* sponge layer of Sec. 4.2: theta = 0 on every face of the cells within
                          `sponge` cells of a zero-gradient side (the paper uses 5 with its
-                         zero-gradient boundaries); 0 = none, at most min(nx, ny) / 2 */
+                         zero-gradient boundaries); 0 = none; at most n / 2 along every axis
+                         that has a zero-gradient side */
 } vlbm_opts;
 
 /* Host copy of the device-side step state and monitors. */
@@ -253,7 +254,7 @@ VLBM_API int vlbm_batch_monitors(vlbm_batch *b, int32_t i, vlbm_monitor_t *out);
 VLBM_API int vlbm_batch_get_tuning(const vlbm_batch *b, vlbm_batch_tuning *t);
 VLBM_API int vlbm_batch_set_tuning(vlbm_batch *b, const vlbm_batch_tuning *t);
 
-/* Autotuner: times every decomposition (chunk 16/32/64 rows x 1..max CTAs per SM
+/* Autotuner: times every decomposition (chunk 16/32/64/128 rows x 1..max CTAs per SM
  * x both item orders) over trial_steps steps each with CUDA events, keeps the
  * fastest and returns it with its time per step. The decomposition does not
  * change any cell's arithmetic, so the trial steps are real steps: the grids

@@ -284,8 +284,8 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
     if (!(o.eps >= 0.0 && o.eps < 1e-3)) return fail(nullptr, VLBM_E_INVAL, "eps must be in [0, 1e-3)");
     if (o.kernel < VLBM_KERNEL_AUTO || o.kernel > VLBM_KERNEL_FUSED)
         return fail(nullptr, VLBM_E_INVAL, "kernel out of range");
-    if (o.sponge < 0 || 2 * o.sponge > grid->nx || 2 * o.sponge > grid->ny)
-        return fail(nullptr, VLBM_E_INVAL, "sponge must be in [0, min(nx, ny) / 2]");
+    if (!sponge_ok(o.sponge, *grid))
+        return fail(nullptr, VLBM_E_INVAL, "sponge must be in [0, n / 2] along every axis with a zero-gradient side");
     if (!(lambda == lambda)) return fail(nullptr, VLBM_E_INVAL, "lambda is NaN");
     const Layout L = make_layout(grid->nx, grid->ny, elem);
     if (!d_workspace || ((uintptr_t)d_workspace & 255))

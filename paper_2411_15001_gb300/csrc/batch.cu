@@ -289,8 +289,9 @@ int vlbm_batch_init(int32_t n, const vlbm_grid *grids, double gamma, int32_t lim
     if (!(o.alpha >= 0.5 && o.alpha < 1.0) || !(o.eps >= 0.0 && o.eps < 1e-3))
         return bfail(nullptr, VLBM_E_INVAL, "alpha or eps out of range");
     for (int i = 0; i < n; ++i)
-        if (o.sponge < 0 || 2 * o.sponge > grids[i].nx || 2 * o.sponge > grids[i].ny)
-            return bfail(nullptr, VLBM_E_INVAL, "sponge must be in [0, min(nx, ny) / 2] for grid %d", i);
+        if (!sponge_ok(o.sponge, grids[i]))
+            return bfail(nullptr, VLBM_E_INVAL, "sponge of grid %d: at most n / 2 along an axis with a "
+                                                "zero-gradient side", i);
     if (!d_workspace || ((uintptr_t)d_workspace & 255))
         return bfail(nullptr, VLBM_E_NOMEM, "workspace NULL or not 256-byte aligned");
     vlbm_batch *b = new (std::nothrow) vlbm_batch();
@@ -447,7 +448,7 @@ int vlbm_batch_autotune(vlbm_batch *b, int32_t trial_steps, vlbm_batch_tuning *b
     BDeviceGuard g(b->device);
     const int maxc = b->precision == VLBM_FP64 ? fused_occupancy<double>(b->limiter)
                                                : fused_occupancy<float>(b->limiter);
-    const int chunks[] = {16, 32, 64};
+    const int chunks[] = {16, 32, 64, 128};
     const int orders[] = {VLBM_ORDER_LPT, VLBM_ORDER_INDEX};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

@@ -214,7 +214,7 @@ extern "C" int vlbm_step_noalloc(const vlbm_grid *grid, double gamma, double a, 
         sponge = opts->sponge;
     }
     if (!(alpha >= 0.5 && alpha < 1.0) || !(eps >= 0.0 && eps < 1e-3)) return VLBM_E_INVAL;
-    if (sponge < 0 || 2 * sponge > grid->nx || 2 * sponge > grid->ny) return VLBM_E_INVAL;
+    if (!sponge_ok(sponge, *grid)) return VLBM_E_INVAL;
     if (!d_in || !d_out || d_in == d_out || !result) return VLBM_E_INVAL;
     const long long blocks =
         (long long)((grid->nx + kNaBX - 1) / kNaBX) * ((grid->ny + kNaBY - 1) / kNaBY);

@@ -69,7 +69,8 @@ struct StepConsts {
     T gamma, gm1;             // gamma, gamma - 1
     T eps;                    // epsilon of the PP and pressure bounds
     float eps_margin;         // 2 eps as float, the FP32 screen's allowance for epsilon
-    float rmax1;              // FP32 screen: a lower bound of kappa / (1 + eps) (see below)
+    float T1;                 // FP32 screen: an upper bound of (1 + 2 eps) / kappa, raised by 64 u
+    float inv_kappa;          // 1 / kappa
     double kappa64, eps64;    // FP64 copies for the internal-energy solve
 };
 
@@ -114,7 +115,7 @@ struct DevCtl {
     StepConsts<double> kd;
 };
 
-static_assert(sizeof(DevCtl) == 464, "bench.py reads the control block size");
+static_assert(sizeof(DevCtl) == 472, "bench.py reads the control block size");
 
 // One grid as the row-marching kernel sees it (device memory, 64-byte aligned).
 template <typename T>
@@ -129,6 +130,15 @@ struct InstDesc {
     DevCtl *ctl;
     int sponge;           // width of the theta = 0 layer at zero-gradient sides (Sec. 4.2)
 };
+
+// A sponge width fits a grid when it is >= 0 and at most half the cells along every
+// axis that has a zero-gradient side (the layer exists only next to such sides).
+inline bool sponge_ok(int w, const vlbm_grid &g) {
+    if (w < 0) return false;
+    const bool tx = g.bc[0] == VLBM_BC_TRANSMISSIVE || g.bc[1] == VLBM_BC_TRANSMISSIVE;
+    const bool ty = g.bc[2] == VLBM_BC_TRANSMISSIVE || g.bc[3] == VLBM_BC_TRANSMISSIVE;
+    return !(tx && 2 * w > g.nx) && !(ty && 2 * w > g.ny);
+}
 
 // Sponge layer of Sec. 4.2: theta = 0 on every face of a cell that lies within
 // `w` cells of a zero-gradient side (ghost cells included); w = 0 disables it.

@@ -1,0 +1,114 @@
+"""Parity at the full sizes of the measured workloads (needs a GB300), on sampled
+cells: after the GPU has run a while, one more GPU step is compared cell by cell
+with the oracle's step of a 9 x 9 patch of the GPU's own state around each sampled
+cell (the update of a cell reads only cells within distance 2, so the patch edge
+never reaches the centre), at the kinetic speed the GPU used.
+
+The GPU arithmetic is FP32 and the oracle's FP64 on the same (FP32) inputs; the
+tolerance, 1e-4 of the largest magnitude of that plane in the patch, covers FP32
+rounding (~1e-6 of that scale, more where terms cancel) and the FP32 theta_p,
+which may sit up to 6.1e-5 below the exact value where the limiter acts (a
+certified lower bound, tight to 2^-14). Workloads:
+the 4096^2 near-vacuum blast with PP (the bench's configuration, row-marching
+kernel), the 1024^2 quadrant problem with LMP, and grids of the batched workload
+stepped by the batch.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_15001_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_15001_gb300 import vlbm as V  # noqa: E402
+
+R = 4   # patch radius
+
+
+def _check_samples(before, after, cells, a, limiter, gamma, eps, tol=1e-4):
+    """before/after: (20, ny, nx) float arrays; cells: interior (j, i) at distance > R."""
+    worst = 0.0
+    n = 2 * R + 1
+    cfg = O.Config(n, n, (1, 1, 1, 1), limiter, gamma, 0.5, eps)
+    for (j, i) in cells:
+        patch = np.ascontiguousarray(before[:, j - R:j + R + 1, i - R:i + R + 1], dtype=np.float64)
+        ref = O.step(cfg, patch, a)[:, R, R]
+        got = after[:, j, i].astype(np.float64)
+        scale = np.abs(patch).reshape(20, -1).max(axis=1)
+        err = float((np.abs(got - ref) / np.maximum(scale, 1e-300)).max())
+        worst = max(worst, err)
+        assert err <= tol, (j, i, err, got, ref)
+    return worst
+
+
+def _cells(before, nsample, seed, focus_plane=0):
+    """Random interior cells plus the cells of the largest |gradient| of one plane."""
+    ny, nx = before.shape[1:]
+    rng = np.random.default_rng(seed)
+    cells = [(int(rng.integers(R + 1, ny - R - 1)), int(rng.integers(R + 1, nx - R - 1)))
+             for _ in range(nsample)]
+    q = before[focus_plane].astype(np.float64)
+    g = np.abs(np.diff(q, axis=1))[R + 1:ny - R - 1, R + 1:nx - R - 2]
+    flat = np.argsort(g, axis=None)[-nsample:]
+    for k in flat:
+        j, i = np.unravel_index(k, g.shape)
+        cells.append((int(j) + R + 1, int(i) + R + 1))
+    return cells
+
+
+def _step_and_sample(s, limiter, gamma, eps, nsample, seed):
+    before = s.state_planes().cpu().numpy()
+    a = s.monitors()["a"]
+    s.step(1)
+    after = s.state_planes().cpu().numpy()
+    assert s.monitors()["status"] == 0
+    return _check_samples(before, after, _cells(before, nsample, seed), a, limiter, gamma, eps)
+
+
+def test_blast_4096_pp_sampled():
+    p = W.blast(4096)
+    s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, limiter=V.LIM_PP, precision=V.FP32, eps=1e-13,
+               kernel=V.KERNEL_FUSED, device="cuda:0")
+    c = torch.tensor(p.conserved(), dtype=torch.float32, device="cuda:0")
+    s.set_conserved(c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+    s.step(300)
+    _step_and_sample(s, O.LIM_PP, p.gamma, 1e-13, 150, 1)
+    s.close()
+
+
+def test_quadrant_1024_lmp_sampled():
+    p = W.quadrant_riemann(1024, seed=0)
+    s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, limiter=V.LIM_LMP, precision=V.FP32, kernel=V.KERNEL_FUSED,
+               device="cuda:0")
+    c = torch.tensor(p.conserved(), dtype=torch.float32, device="cuda:0")
+    s.set_conserved(c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+    s.step(400)
+    _step_and_sample(s, O.LIM_LMP, p.gamma, 1e-16, 150, 2)
+    s.close()
+
+
+def test_batch_grids_sampled():
+    probs = W.batch_instances(256, seed=1)
+    b = V.VLBMBatch([(p.nx, p.ny, p.dx, p.bc) for p in probs], limiter=V.LIM_PP, precision=V.FP32,
+                    eps=1e-13, device="cuda:0", sponge=5)
+    for i, p in enumerate(probs):
+        c = torch.tensor(p.conserved(), dtype=torch.float32, device="cuda:0")
+        b.set_conserved(i, c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+    b.step(200)
+    picks = [0, 37, 185, 255]
+    before = {i: b.state_planes(i).cpu().numpy() for i in picks}
+    a = {i: b.monitors(i)["a"] for i in picks}
+    b.step(1)
+    for i in picks:
+        after = b.state_planes(i).cpu().numpy()
+        assert b.monitors(i)["status"] == 0
+        # cells away from the zero-gradient sides' 5-cell sponge and from the boundary
+        cells = [(j, k) for (j, k) in _cells(before[i], 40, 10 + i)
+                 if min(j, k) > 7 and j < probs[i].ny - 8 and k < probs[i].nx - 8]
+        _check_samples(before[i], after, cells, a[i], O.LIM_PP, probs[i].gamma, 1e-13)
+    b.close()

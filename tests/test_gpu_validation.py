@@ -2,13 +2,15 @@
 isentropic wave (gamma = 3, density down to 5e-7, Sec. 4.4) and the LeBlanc
 tube (gamma = 5/3, pressure ratio 1e6, Sec. 4.5). FP64: bit for bit the oracle's
 run to the final time. FP32: every step admissible (the monitors' exact test) and
-the final density within L1 1e-3 of the oracle's.
+the final density within L1 max(1e-3, 4x the oracle's sensitivity to
+float rounding of u_0) of the oracle's.
 """
 import functools
 
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2411_15001_gb300 import workloads as W
 from tests.gpu_helpers import l1_rel, oracle_run
 
@@ -59,12 +61,38 @@ def test_fp64_equals_oracle(case, lim, kernel):
     assert np.array_equal(got, ref["state"])
 
 
+@functools.lru_cache(maxsize=None)
+def _rounding_sensitivity(case, lim):
+    """Largest L1 change of the oracle's final density when u_0 is moved by float
+    rounding: u_0 rounded to float, and that plus two seeded relative shifts of
+    2^-24 per column (the same in every row, so the 1D problem stays 1D)."""
+    make, t_end, sponge = CASES[case]
+    p = make()
+    u0 = p.conserved()
+    cfg = O.Config(p.nx, p.ny, p.bc, lim, p.gamma, 0.5, 1e-16, sponge)
+    ref = _oracle(case, lim)["state"][0]
+    worst = 0.0
+    for seed in (None, 1, 2):
+        u = u0.astype(np.float32).astype(np.float64)
+        if seed is not None:
+            rng = np.random.default_rng(seed)
+            u = u * (1.0 + 2.0 ** -24 * rng.choice([-1.0, 1.0], size=(u.shape[0], 1, u.shape[2])))
+        worst = max(worst, l1_rel(O.run(cfg, u, p.dx, t_end=t_end)["state"][0], ref))
+    return worst
+
+
 @pytest.mark.parametrize("lim", [V.LIM_PP, V.LIM_LMP, V.LIM_RLMP])
 @pytest.mark.parametrize("case", list(CASES))
 def test_fp32_admissible_and_close(case, lim):
+    """The bound is 4x the oracle's own sensitivity to float rounding of u_0, at least
+    1e-3. Both cases are ill-conditioned in places: LMP's theta_rho jumps where
+    dF^rho crosses 0 (near-vacuum wave: ~5.6e-4 from rounding u_0 alone; PP 1.6e-8),
+    and on the LeBlanc tube the PP limiter's switching near the contact moves the
+    FP64 result by ~2.8e-3 under the same rounding."""
     make, t_end, sponge = CASES[case]
     p = make()
     got, mon = _gpu_to(p, lim, V.FP32, t_end, V.KERNEL_FUSED, sponge)
     assert mon["status"] == 0 and mon["first_bad_step"] == -1
     ref = _oracle(case, lim)
-    assert l1_rel(got[0], ref["state"][0]) <= 1e-3
+    tol = max(1e-3, 4.0 * _rounding_sensitivity(case, lim))
+    assert l1_rel(got[0], ref["state"][0]) <= tol
