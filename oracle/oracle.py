@@ -31,16 +31,26 @@ BC_PERIODIC, BC_ZEROGRAD, BC_REFLECT = range(3)
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, OpenMP)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC[:-2] + ".h"))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
                                _SRC, "-o", _LIB_PATH, "-lm"])
     return _LIB_PATH
 
 
+class _Field(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_double * 4), ("out", ctypes.c_double * 4), ("nplanes", ctypes.c_int),
+                ("nx", ctypes.c_double * 2), ("ny", ctypes.c_double * 2), ("c0", ctypes.c_double * 2),
+                ("c1", ctypes.c_double * 2)]
+
+
 class _Cfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("bc", ctypes.c_int * 4),
                 ("limiter", ctypes.c_int), ("gamma", ctypes.c_double),
-                ("alpha", ctypes.c_double), ("eps", ctypes.c_double), ("sponge", ctypes.c_int)]
+                ("alpha", ctypes.c_double), ("eps", ctypes.c_double), ("sponge", ctypes.c_int),
+                ("bc_hi", ctypes.c_int * 4), ("split", ctypes.c_int * 4),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("dx", ctypes.c_double),
+                ("field", ctypes.POINTER(_Field))]
 
 
 _DBG_FIELDS = ["theta_x", "theta_y", "theta_rho_x", "theta_rho_y", "theta_p_x", "theta_p_y",
@@ -62,8 +72,9 @@ def lib():
         _lib.orc_max_speed.restype = D
         _lib.orc_max_speed.argtypes = [P, P]
         _lib.orc_init_populations.argtypes = [P, D, P]
-        _lib.orc_step.argtypes = [P, D, P, P, P]
-        _lib.orc_step_fv.argtypes = [P, D, P, P]
+        _lib.orc_step.argtypes = [P, D, D, P, P, P]
+        _lib.orc_step_fv.argtypes = [P, D, D, P, P]
+        _lib.orc_fill_ghosts.argtypes = [P, D, D, P, P]
         _lib.orc_theta_p.restype = D
         _lib.orc_theta_p.argtypes = [D, D, P, P]
         _lib.orc_gql_radius.restype = D
@@ -94,6 +105,25 @@ def _ptr(a: np.ndarray):
 
 
 @dataclass
+class Field:
+    """Prescribed boundary field (BC_DIRICHLET parts): at time t the ghost cell with
+    centre (x, y) holds conserved state `inside` if nx[k] x + ny[k] y >= c0[k] + c1[k] t
+    for every half-plane k, else `outside`."""
+    inside: tuple
+    outside: tuple
+    planes: tuple = ()    # up to two (nx, ny, c0, c1)
+
+    def c(self) -> _Field:
+        f = _Field()
+        f.in_[:] = [float(v) for v in self.inside]
+        f.out[:] = [float(v) for v in self.outside]
+        f.nplanes = len(self.planes)
+        for k, (a, b, c0, c1) in enumerate(self.planes):
+            f.nx[k], f.ny[k], f.c0[k], f.c1[k] = a, b, c0, c1
+        return f
+
+
+@dataclass
 class Config:
     nx: int
     ny: int
@@ -103,10 +133,22 @@ class Config:
     alpha: float = 0.5
     eps: float = 1e-16
     sponge: int = 0       # Sec. 4.2: theta = 0 within `sponge` cells of a zero-gradient side
+    bc_hi: tuple | None = None     # per side: type at and past split[s] (None: = bc)
+    split: tuple = (0, 0, 0, 0)    # per side: index along it where the type switches (0: none)
+    x0: float = 0.0
+    y0: float = 0.0
+    dx: float = 1.0
+    field: Field | None = None
 
     def c(self) -> _Cfg:
-        return _Cfg(self.nx, self.ny, (ctypes.c_int * 4)(*self.bc), self.limiter,
-                    self.gamma, self.alpha, self.eps, self.sponge)
+        hi = self.bc if self.bc_hi is None else self.bc_hi
+        cf = _Cfg(self.nx, self.ny, (ctypes.c_int * 4)(*self.bc), self.limiter,
+                  self.gamma, self.alpha, self.eps, self.sponge, (ctypes.c_int * 4)(*hi),
+                  (ctypes.c_int * 4)(*self.split), self.x0, self.y0, self.dx, None)
+        if self.field is not None:
+            cf._field_keep = self.field.c()      # keep the struct alive with the config
+            cf.field = ctypes.pointer(cf._field_keep)
+        return cf
 
 
 def kinetic_speed(lam: float, alpha: float) -> float:
@@ -176,14 +218,15 @@ def init_populations(cfg: Config, state: np.ndarray, a: float) -> np.ndarray:
     return s
 
 
-def step(cfg: Config, state: np.ndarray, a: float, debug: bool = False, fv: bool = False):
-    """One time step with kinetic speed a. Returns the new state (and a dict of
-    per-face / per-cell intermediate values if debug)."""
+def step(cfg: Config, state: np.ndarray, a: float, debug: bool = False, fv: bool = False, t: float = 0.0):
+    """One time step from time t (which only places the Dirichlet field) with kinetic
+    speed a. Returns the new state (and a dict of per-face / per-cell intermediate
+    values if debug)."""
     s = np.ascontiguousarray(state, dtype=np.float64)
     out = np.empty_like(s)
     c = cfg.c()
     if fv:
-        rc = lib().orc_step_fv(ctypes.byref(c), a, _ptr(s), _ptr(out))
+        rc = lib().orc_step_fv(ctypes.byref(c), a, t, _ptr(s), _ptr(out))
         if rc:
             raise ValueError("oracle rejected the configuration")
         return out
@@ -201,10 +244,19 @@ def step(cfg: Config, state: np.ndarray, a: float, debug: bool = False, fv: bool
         d = _Debug(*[dbg_arrays[k].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
                      for k in _DBG_FIELDS])
         dbg_ptr = ctypes.byref(d)
-    rc = lib().orc_step(ctypes.byref(c), a, _ptr(s), _ptr(out), dbg_ptr)
+    rc = lib().orc_step(ctypes.byref(c), a, t, _ptr(s), _ptr(out), dbg_ptr)
     if rc:
         raise ValueError("oracle rejected the configuration")
     return (out, dbg_arrays) if debug else out
+
+
+def fill_ghosts(cfg: Config, state: np.ndarray, a: float, t: float = 0.0) -> np.ndarray:
+    """The ghost fill alone: (20, ny + 4, nx + 4), cell (i, j) at [:, j + 2, i + 2]."""
+    s = np.ascontiguousarray(state, dtype=np.float64)
+    ext = np.empty((20, cfg.ny + 4, cfg.nx + 4))
+    if lib().orc_fill_ghosts(ctypes.byref(cfg.c()), a, t, _ptr(s), _ptr(ext)):
+        raise ValueError("oracle rejected the configuration")
+    return ext
 
 
 def run(cfg: Config, cons: np.ndarray, dx: float, nsteps: int | None = None,
@@ -245,7 +297,7 @@ def run(cfg: Config, cons: np.ndarray, dx: float, nsteps: int | None = None,
                 dt = t_end - t
                 a = dx / dt
                 last = True
-        state = step(cfg, state, a, fv=fv)
+        state = step(cfg, state, a, fv=fv, t=t)
         hist.append(a)
         t = t + dt
         n += 1

@@ -24,6 +24,10 @@
  *    cell into both ghost layers; a reflective wall mirrors the cells, negates the
  *    normal momentum, and swaps the populations moving towards / away from it.
  *    Corners apply the x rule first, then the y rule.
+ *  - Dirichlet parts (Sec. 4.7, 4.8 set the distributions of boundary cells to the
+ *    Maxwellians of prescribed states): a ghost cell holds the prescribed state
+ *    at its centre at the step's start time, with populations M_k of that state
+ *    at the step's kinetic speed; lambda^n also covers the prescribed states.
  */
 #include "vlbm_oracle.h"
 
@@ -42,14 +46,39 @@ static int g_threads = 1;
 void orc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
 int orc_get_threads(void) { return g_threads; }
 
+static int state_in_G(const double u[4]) {
+    return u[0] > 0.0 && u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0] > 0.0;
+}
+
+static int has_dirichlet(const orc_cfg *c) {
+    for (int s = 0; s < 4; ++s)
+        if (c->bc[s] == ORC_BC_DIRICHLET || c->bc_hi[s] == ORC_BC_DIRICHLET) return 1;
+    return 0;
+}
+
 int orc_check_cfg(const orc_cfg *c) {
     if (!c || c->nx < 2 || c->ny < 2) return -1;
-    for (int s = 0; s < 4; ++s)
-        if (c->bc[s] < 0 || c->bc[s] > 2) return -1;
+    for (int s = 0; s < 4; ++s) {
+        const int n = s < 2 ? c->ny : c->nx;   /* cells along side s */
+        if (c->bc[s] < 0 || c->bc[s] > 3 || c->bc_hi[s] < 0 || c->bc_hi[s] > 3) return -1;
+        if (c->split[s] == 0) {
+            if (c->bc_hi[s] != c->bc[s]) return -1;
+        } else if (c->split[s] < 2 || c->split[s] > n - 2) {
+            return -1;
+        }
+        if ((c->bc[s] == ORC_BC_PERIODIC || c->bc_hi[s] == ORC_BC_PERIODIC) &&
+            (c->bc[s] != c->bc_hi[s] || c->split[s] != 0))
+            return -1;
+    }
     if ((c->bc[0] == ORC_BC_PERIODIC) != (c->bc[1] == ORC_BC_PERIODIC)) return -1;
     if ((c->bc[2] == ORC_BC_PERIODIC) != (c->bc[3] == ORC_BC_PERIODIC)) return -1;
     if (c->limiter < 0 || c->limiter > 4 || c->sponge < 0) return -1;
     if (!(c->alpha >= 0.0 && c->alpha < 1.0) || !(c->gamma > 1.0)) return -1;
+    if (has_dirichlet(c)) {
+        const orc_field *f = c->field;
+        if (!f || f->nplanes < 0 || f->nplanes > 2 || !(c->dx > 0.0)) return -1;
+        if (!state_in_G(f->in) || !state_in_G(f->out)) return -1;
+    }
     return 0;
 }
 
@@ -91,17 +120,32 @@ void orc_maxwellians(double gamma, double alpha, double a, const double u[4], do
     }
 }
 
-/* lambda^n of the numerical section: max of sqrt(v1^2+v2^2) + sqrt(gamma p / rho). */
+/* |v| + sqrt(gamma p / rho) of one state; NaN outside G. */
+static double cell_speed(double gamma, double rho, double m1, double m2, double E) {
+    double v1 = m1 / rho, v2 = m2 / rho;
+    double p = (gamma - 1.0) * (E - 0.5 * rho * (v1 * v1 + v2 * v2));
+    if (!(rho > 0.0) || !(p >= 0.0)) return NAN;
+    return sqrt(v1 * v1 + v2 * v2) + sqrt(gamma * p / rho);
+}
+
+/* lambda^n of the numerical section: max of sqrt(v1^2+v2^2) + sqrt(gamma p / rho)
+ * over the cells, and over the Dirichlet field's two states if the boundary has a
+ * Dirichlet part (reading: the prescribed states are cells of the flow too). */
 double orc_max_speed(const orc_cfg *c, const double *s) {
     size_t N = (size_t)c->nx * c->ny;
     double lam = 0.0;
     for (size_t k = 0; k < N; ++k) {
-        double rho = s[k], v1 = s[N + k] / rho, v2 = s[2 * N + k] / rho;
-        double p = (c->gamma - 1.0) * (s[3 * N + k] - 0.5 * rho * (v1 * v1 + v2 * v2));
-        if (!(rho > 0.0) || !(p >= 0.0)) return NAN;
-        double sp = sqrt(v1 * v1 + v2 * v2) + sqrt(c->gamma * p / rho);
+        double sp = cell_speed(c->gamma, s[k], s[N + k], s[2 * N + k], s[3 * N + k]);
         if (!(sp == sp)) return NAN;
         if (sp > lam) lam = sp;
+    }
+    if (has_dirichlet(c) && c->field) {
+        const double *st[2] = {c->field->in, c->field->out};
+        for (int k = 0; k < 2; ++k) {
+            double sp = cell_speed(c->gamma, st[k][0], st[k][1], st[k][2], st[k][3]);
+            if (!(sp == sp)) return NAN;
+            if (sp > lam) lam = sp;
+        }
     }
     return lam;
 }
@@ -180,6 +224,20 @@ static int src_index(int i, int n, int bc) {
     return i < 0 ? -1 - i : 2 * n - 1 - i;        /* reflective mirror */
 }
 
+/* Type of side s (0 west, 1 east, 2 south, 3 north) at index k along it. */
+static int side_type(const orc_cfg *c, int s, int k) {
+    return k < c->split[s] ? c->bc[s] : c->bc_hi[s];
+}
+
+/* The Dirichlet field's state at the centre of cell (i, j) at time t. */
+static const double *field_state(const orc_cfg *c, double t, int i, int j) {
+    const orc_field *f = c->field;
+    double x = c->x0 + (i + 0.5) * c->dx, y = c->y0 + (j + 0.5) * c->dx;
+    for (int k = 0; k < f->nplanes; ++k)
+        if (!(f->nx[k] * x + f->ny[k] * y >= f->c0[k] + f->c1[k] * t)) return f->out;
+    return f->in;
+}
+
 /* Copy the 20 values of ext cell (si, sj) into ext cell (di, dj), applying the
  * mirror transform across an x-wall (axis 0) or a y-wall (axis 1) if asked. */
 static void copy_cell(ext_t *e, int di, int dj, int si, int sj, int mirror_axis) {
@@ -209,8 +267,34 @@ static int ext_alloc(ext_t *e, int nx, int ny) {
 
 static void ext_free(ext_t *e) { free(e->p[0]); }
 
-/* Interior copy, then x ghosts of interior rows, then y ghosts of all columns. */
-static void fill_ext(const orc_cfg *c, const double *in, ext_t *e) {
+/* Ghost cell (i, j) of a Dirichlet part: the field's state and its Maxwellians
+ * (populations at equilibrium) at kinetic speed a. */
+static void set_dirichlet(const orc_cfg *c, double a, double t, ext_t *e, int i, int j) {
+    const double *u = field_state(c, t, i, j);
+    double M[5][4];
+    orc_maxwellians(c->gamma, c->alpha, a, u, M);
+    size_t id = (size_t)(j + G) * e->ex + (i + G);
+    for (int cc = 0; cc < 4; ++cc) {
+        e->p[cc][id] = u[cc];
+        for (int k = 0; k < 4; ++k) e->p[4 * (k + 1) + cc][id] = M[k][cc];
+    }
+}
+
+/* One ghost cell (i, j) of side s, index k along it: its type's rule. */
+static void fill_ghost(const orc_cfg *c, double a, double t, ext_t *e, int s, int i, int j, int k) {
+    const int type = side_type(c, s, k);
+    if (type == ORC_BC_DIRICHLET) {
+        set_dirichlet(c, a, t, e, i, j);
+    } else if (s < 2) {
+        copy_cell(e, i + G, j + G, src_index(i, c->nx, type) + G, j + G, type == ORC_BC_REFLECT ? 0 : -1);
+    } else {
+        copy_cell(e, i + G, j + G, i + G, src_index(j, c->ny, type) + G, type == ORC_BC_REFLECT ? 1 : -1);
+    }
+}
+
+/* Interior copy, then x ghosts of interior rows, then y ghosts of all columns
+ * (corners take the y rule applied to the x ghosts). */
+static void fill_ext(const orc_cfg *c, double a, double t, const double *in, ext_t *e) {
     int nx = c->nx, ny = c->ny;
     size_t N = (size_t)nx * ny;
     for (int q = 0; q < NPLANE; ++q)
@@ -219,20 +303,25 @@ static void fill_ext(const orc_cfg *c, const double *in, ext_t *e) {
                 e->p[q][(size_t)(j + G) * e->ex + (i + G)] = in[q * N + (size_t)j * nx + i];
     for (int j = 0; j < ny; ++j)
         for (int k = 1; k <= G; ++k) {
-            int iw = -k, ie = nx - 1 + k;
-            copy_cell(e, iw + G, j + G, src_index(iw, nx, c->bc[0]) + G, j + G,
-                      c->bc[0] == ORC_BC_REFLECT ? 0 : -1);
-            copy_cell(e, ie + G, j + G, src_index(ie, nx, c->bc[1]) + G, j + G,
-                      c->bc[1] == ORC_BC_REFLECT ? 0 : -1);
+            fill_ghost(c, a, t, e, 0, -k, j, j);
+            fill_ghost(c, a, t, e, 1, nx - 1 + k, j, j);
         }
-    for (int I = 0; I < e->ex; ++I)
+    for (int i = -G; i < nx + G; ++i)
         for (int k = 1; k <= G; ++k) {
-            int js = -k, jn = ny - 1 + k;
-            copy_cell(e, I, js + G, I, src_index(js, ny, c->bc[2]) + G,
-                      c->bc[2] == ORC_BC_REFLECT ? 1 : -1);
-            copy_cell(e, I, jn + G, I, src_index(jn, ny, c->bc[3]) + G,
-                      c->bc[3] == ORC_BC_REFLECT ? 1 : -1);
+            fill_ghost(c, a, t, e, 2, i, -k, i);
+            fill_ghost(c, a, t, e, 3, i, ny - 1 + k, i);
         }
+}
+
+int orc_fill_ghosts(const orc_cfg *c, double a, double t, const double *in, double *ext) {
+    if (orc_check_cfg(c) || !(a > 0.0)) return -1;
+    ext_t e;
+    if (ext_alloc(&e, c->nx, c->ny)) return -1;
+    fill_ext(c, a, t, in, &e);
+    size_t n = (size_t)e.ex * e.ey;
+    for (int q = 0; q < NPLANE; ++q) memcpy(ext + (size_t)q * n, e.p[q], n * sizeof(double));
+    ext_free(&e);
+    return 0;
 }
 
 /* ---------------------------------------------------------------- one step */
@@ -266,12 +355,14 @@ static int work_alloc(work_t *w, size_t n) {
 }
 
 /* Cell (i, j) (ghost cells included) lies in the sponge layer of Sec. 4.2: within
- * c->sponge cells of a zero-gradient side. */
+ * c->sponge cells of a zero-gradient side (a side that is zero-gradient along its
+ * whole length). */
 static int in_sponge(const orc_cfg *c, int i, int j) {
     const int s = c->sponge;
     if (s <= 0) return 0;
-    return (c->bc[0] == ORC_BC_ZEROGRAD && i < s) || (c->bc[1] == ORC_BC_ZEROGRAD && i >= c->nx - s) ||
-           (c->bc[2] == ORC_BC_ZEROGRAD && j < s) || (c->bc[3] == ORC_BC_ZEROGRAD && j >= c->ny - s);
+    int zg[4];
+    for (int k = 0; k < 4; ++k) zg[k] = c->bc[k] == ORC_BC_ZEROGRAD && c->bc_hi[k] == ORC_BC_ZEROGRAD;
+    return (zg[0] && i < s) || (zg[1] && i >= c->nx - s) || (zg[2] && j < s) || (zg[3] && j >= c->ny - s);
 }
 
 /* Steps a3-a8 of the scheme on the extended grid: equilibria, face states u* and
@@ -416,13 +507,13 @@ static void export_debug(const orc_cfg *c, const ext_t *e, const work_t *w, orc_
 
 /* a9, kinetic form: eq. (blending_u1) pulls u_1..u_4 from the upwind neighbour;
  * eq. (blending_u) updates u with the local terms of the eliminated u_5. */
-int orc_step(const orc_cfg *c, double a, const double *in, double *out, orc_debug *dbg) {
+int orc_step(const orc_cfg *c, double a, double t, const double *in, double *out, orc_debug *dbg) {
     if (orc_check_cfg(c) || !(a > 0.0)) return -1;
     ext_t e;
     work_t w;
     if (ext_alloc(&e, c->nx, c->ny)) return -1;
     if (work_alloc(&w, (size_t)e.ex * e.ey)) { ext_free(&e); return -1; }
-    fill_ext(c, in, &e);
+    fill_ext(c, a, t, in, &e);
     compute_theta(c, a, &e, &w);
     export_debug(c, &e, &w, dbg);
 
@@ -460,13 +551,13 @@ int orc_step(const orc_cfg *c, double a, const double *in, double *out, orc_debu
 /* a9, flux form of Sec. 3.2: u^{n+1} = u - (1/a)[F_{i+1/2} - F_{i-1/2} + G_{j+1/2} - G_{j-1/2}]
  * with F = F^(1) + theta dF (eq. 1st-order_flux), and the blended moments
  * v_1, v_2, w_1, w_2 mapped back to u_1..u_4 by the first four rows of Q^{-1}. */
-int orc_step_fv(const orc_cfg *c, double a, const double *in, double *out) {
+int orc_step_fv(const orc_cfg *c, double a, double t, const double *in, double *out) {
     if (orc_check_cfg(c) || !(a > 0.0)) return -1;
     ext_t e;
     work_t w;
     if (ext_alloc(&e, c->nx, c->ny)) return -1;
     if (work_alloc(&w, (size_t)e.ex * e.ey)) { ext_free(&e); return -1; }
-    fill_ext(c, in, &e);
+    fill_ext(c, a, t, in, &e);
     compute_theta(c, a, &e, &w);
 
     const int nx = c->nx, ny = c->ny, ex = e.ex;

@@ -27,7 +27,19 @@
 extern "C" {
 #endif
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_ZEROGRAD = 1, ORC_BC_REFLECT = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_ZEROGRAD = 1, ORC_BC_REFLECT = 2, ORC_BC_DIRICHLET = 3 };
+
+/* Prescribed boundary field of the Dirichlet parts of the boundary (the double
+ * Mach reflection of Sec. 4.7 and the jets of Sec. 4.8 set the distributions of
+ * boundary cells to the Maxwellians of given states). At time t a Dirichlet ghost
+ * cell with centre (x, y) holds the conserved state `in` if
+ * nx[k] x + ny[k] y >= c0[k] + c1[k] t for every k < nplanes, else `out`; its
+ * populations are M_1..M_4 of that state at the step's kinetic speed. */
+typedef struct {
+    double in[4], out[4];     /* conserved (rho, m1, m2, E), both inside G */
+    int nplanes;              /* 0..2 half-planes */
+    double nx[2], ny[2], c0[2], c1[2];
+} orc_field;
 enum { ORC_LIM_FIRST = 0, ORC_LIM_SECOND = 1, ORC_LIM_PP = 2, ORC_LIM_LMP = 3, ORC_LIM_RLMP = 4 };
 
 typedef struct {
@@ -39,6 +51,16 @@ typedef struct {
     double eps;       /* epsilon subtracted in the PP and pressure bounds (1e-16 in Sec. 3.3.3) */
     int sponge;       /* Sec. 4.2: theta = 0 on every face of the cells within `sponge` cells
                          of a zero-gradient side (0 = none) */
+    /* A side may switch type once along its length (a partial wall, Sec. 4.7): the
+     * ghost cells of side s whose index along the side (column i for south/north,
+     * row j for west/east, ghost indices included) is below split[s] take type
+     * bc[s], the others bc_hi[s]. split[s] = 0 with bc_hi[s] = bc[s] is a uniform
+     * side; otherwise 2 <= split[s] <= n - 2, so that both ends of the side, with
+     * the corner ghosts beyond them, are uniform. A periodic side does not switch. */
+    int bc_hi[4];
+    int split[4];
+    double x0, y0, dx;        /* cell (i, j) has centre (x0 + (i + 1/2) dx, y0 + (j + 1/2) dx) */
+    const orc_field *field;   /* required when some part of a side is ORC_BC_DIRICHLET */
 } orc_cfg;
 
 /* Optional per-face / per-cell outputs of one step. Any pointer may be NULL.
@@ -64,7 +86,9 @@ void   orc_flux_y(double gamma, const double u[4], double g[4]);
 void   orc_maxwellians(double gamma, double alpha, double a, const double u[4], double M[5][4]);
 
 /* lambda = max over cells of |v| + sqrt(gamma p / rho) (Sec. 4 preamble); NaN if a
- * cell is outside the admissible set G. */
+ * cell is outside the admissible set G. With a Dirichlet part on the boundary the
+ * max also covers the field's two states, so that the kinetic speed satisfies
+ * Bouchut's condition on the boundary faces too. */
 double orc_max_speed(const orc_cfg *c, const double *state);
 
 /* Populations u_k = M_k(u) (k = 1..4) from the conserved planes (Sec. 4 preamble). */
@@ -78,15 +102,21 @@ double orc_theta_p(double kappa, double eps, const double ustar[4], const double
 /* spectral radius of B^{-1/2} A B^{-1/2} for the pair (ustar, dflux), closed form */
 double orc_gql_radius(const double ustar[4], const double dflux[4]);
 
-/* One time step with kinetic speed a (Delta t = dx / a), kinetic form:
- * eq. (blending_u1) for u_1..u_4 and eq. (blending_u) for u. Returns 0, or -1 on a
- * bad configuration. in and out must not alias. */
-int    orc_step(const orc_cfg *c, double a, const double *in, double *out, orc_debug *dbg);
+/* One time step from time t with kinetic speed a (Delta t = dx / a), kinetic form:
+ * eq. (blending_u1) for u_1..u_4 and eq. (blending_u) for u. t only places the
+ * Dirichlet field. Returns 0, or -1 on a bad configuration. in and out must not
+ * alias. */
+int    orc_step(const orc_cfg *c, double a, double t, const double *in, double *out, orc_debug *dbg);
 
 /* The same step through the flux form and the moments of Sec. 3.2: u by the
  * blended finite-volume update with F = F^(1) + theta dF, populations from the
  * blended moments v_1, v_2, w_1, w_2 by Q^{-1} (eq. moments_matrix). */
-int    orc_step_fv(const orc_cfg *c, double a, const double *in, double *out);
+int    orc_step_fv(const orc_cfg *c, double a, double t, const double *in, double *out);
+
+/* The extended state of the ghost fill alone (x ghosts of interior rows, then y
+ * ghosts of every column): 20 planes of (nx + 4) x (ny + 4) doubles, cell (i, j)
+ * (ghosts included, i, j >= -2) at (j + 2) (nx + 4) + i + 2. */
+int    orc_fill_ghosts(const orc_cfg *c, double a, double t, const double *in, double *ext);
 
 #ifdef __cplusplus
 }

@@ -35,13 +35,43 @@ class Problem:
     m1: np.ndarray
     m2: np.ndarray
     E: np.ndarray
-    bc: tuple = (0, 0, 0, 0)  # west, east, south, north: 0 periodic, 1 zero-gradient, 2 reflective
+    bc: tuple = (0, 0, 0, 0)  # west, east, south, north: 0 periodic, 1 zero-gradient, 2 reflective,
+    #                           3 prescribed (Dirichlet) state
     gamma: float = GAMMA
     meta: dict = field(default_factory=dict)
+    # a side that switches type along its length: ghost cells with index along the
+    # side (column for south/north, row for west/east) >= split[s] take bc_hi[s]
+    bc_hi: tuple | None = None
+    split: tuple = (0, 0, 0, 0)
+    bfield: "BoundaryField | None" = None
 
     def conserved(self) -> np.ndarray:
         """(4, ny, nx) float64 stack of rho, m1, m2, E."""
         return np.stack([self.rho, self.m1, self.m2, self.E])
+
+
+@dataclass
+class BoundaryField:
+    """State prescribed on the Dirichlet parts of the boundary: at time t, the cell
+    with centre (x, y) holds the conserved state `inside` if
+    nx x + ny y >= c0 + c1 t for each half-plane (nx, ny, c0, c1), else `outside`."""
+
+    inside: tuple
+    outside: tuple
+    planes: tuple = ()
+
+    def state_at(self, x, y, t: float = 0.0) -> np.ndarray:
+        """(4, *x.shape) conserved field; the half-plane test in the operation order
+        of the library and the oracle (products, then the sums)."""
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        inside = np.ones(x.shape, dtype=bool)
+        for (a, b, c0, c1) in self.planes:
+            inside &= (a * x + b * y) >= (c0 + c1 * t)
+        out = np.empty((4,) + x.shape)
+        for q in range(4):
+            out[q] = np.where(inside, self.inside[q], self.outside[q])
+        return out
 
 
 def cell_centres(nx: int, ny: int, dx: float, x0: float = 0.0, y0: float = 0.0):
@@ -277,3 +307,58 @@ def random_cells(nx: int, ny: int, seed: int, bc=(0, 0, 0, 0), rho_range=(0.1, 2
     v2 = rng.uniform(*v_range, size=(ny, nx))
     p = rng.uniform(*p_range, size=(ny, nx))
     return _make("random_cells", nx, ny, 1.0 / max(nx, ny), 0.0, 0.0, (rho, v1, v2, p), bc, gamma)
+
+
+# --------------------------------------------------------------------------
+# Prescribed-state boundaries: double Mach reflection (Sec. 4.7) and
+# astrophysical jets (Sec. 4.8)
+# --------------------------------------------------------------------------
+def _conserved_state(rho, v1, v2, p, gamma):
+    r, m1, m2, E = primitive_to_conserved(np.array(rho), v1, v2, p, gamma=gamma)
+    return (float(r), float(m1), float(m2), float(E))
+
+
+def double_mach_reflection(ny: int) -> Problem:
+    """[0, 3] x [0, 1], gamma = 1.4, a Mach 10 shock through (1/6, 0) at 60 degrees
+    to the x-axis moving right: pre-shock (rho, v1, v2, p) = (1.4, 0, 0, 1) where
+    x >= 1/6 + (y + 20 t) / sqrt(3), post-shock (8, 8.25 cos(pi/6), -8.25 sin(pi/6),
+    116.5) elsewhere. Every side holds that exact moving-shock field (Maxwellian
+    populations), except the bottom for x >= 1/6, a reflective wall. nx = 3 ny;
+    the paper's grids are 1500 x 500 and 3000 x 1000 to t = 0.2."""
+    g = 1.4
+    nx = 3 * ny
+    dx = 1.0 / ny
+    pre = _conserved_state(1.4, 0.0, 0.0, 1.0, g)
+    post = _conserved_state(8.0, 8.25 * math.cos(math.pi / 6), -8.25 * math.sin(math.pi / 6), 116.5, g)
+    s3 = math.sqrt(3.0)
+    bf = BoundaryField(pre, post, ((1.0, -1.0 / s3, 1.0 / 6.0, 20.0 / s3),))
+    X, Y = cell_centres(nx, ny, dx)
+    u = bf.state_at(X, Y, 0.0)
+    xc = (np.arange(nx) + 0.5) * dx
+    split = int(np.count_nonzero(xc < 1.0 / 6.0))      # bottom cells left of the wall
+    return Problem("double_mach_reflection", nx, ny, dx, 0.0, 0.0, u[0], u[1], u[2], u[3],
+                   (3, 3, 3, 3), g, {"t_end": 0.2}, bc_hi=(3, 3, 2, 3), split=(0, 0, split, 0), bfield=bf)
+
+
+def astro_jet(ny: int, mach: int = 80) -> Problem:
+    """High Mach number jet: gamma = 5/3, ambient (rho, v1, v2, p) = (0.5, 0, 0, 0.4127);
+    through |y| < 0.05 of the left side the state (5, 30, 0, 0.4127) enters (Mach 80,
+    domain [0, 2] x [-0.5, 0.5], t = 0.07) or (5, 800, 0, 0.4127) (Mach 2000, domain
+    [0, 1] x [-0.25, 0.25], t = 0.001); elsewhere on the left side the ambient state,
+    zero gradient on the other sides. nx = 2 ny (the paper: 800 x 400)."""
+    g = 5.0 / 3.0
+    if mach == 80:
+        length, v_jet, t_end = 2.0, 30.0, 0.07
+    elif mach == 2000:
+        length, v_jet, t_end = 1.0, 800.0, 0.001
+    else:
+        raise ValueError("mach is 80 or 2000")
+    nx = 2 * ny
+    dx = length / nx
+    y0 = -length / 4.0
+    amb = _conserved_state(0.5, 0.0, 0.0, 0.4127, g)
+    jet = _conserved_state(5.0, v_jet, 0.0, 0.4127, g)
+    bf = BoundaryField(jet, amb, ((0.0, 1.0, -0.05, 0.0), (0.0, -1.0, -0.05, 0.0)))
+    rho = np.full((ny, nx), amb[0])
+    return Problem(f"astro_jet_mach{mach}", nx, ny, dx, 0.0, y0, rho, np.zeros_like(rho), np.zeros_like(rho),
+                   np.full((ny, nx), amb[3]), (3, 1, 1, 1), g, {"t_end": t_end}, bfield=bf)

@@ -29,8 +29,17 @@ def gpu_run(p, limiter, precision, nsteps=None, t_end=None, lam=0.0, eps=1e-16, 
     return planes, mon
 
 
+def oracle_cfg(p, limiter, eps=1e-16, sponge=0):
+    """The oracle's configuration of a workload, boundary field and split sides included."""
+    bf = getattr(p, "bfield", None)
+    field = O.Field(bf.inside, bf.outside, bf.planes) if bf is not None else None
+    return O.Config(p.nx, p.ny, p.bc, limiter, p.gamma, 0.5, eps, sponge,
+                    bc_hi=getattr(p, "bc_hi", None), split=getattr(p, "split", (0, 0, 0, 0)),
+                    x0=p.x0, y0=p.y0, dx=p.dx, field=field)
+
+
 def oracle_run(p, limiter, nsteps=None, t_end=None, lam=0.0, eps=1e-16, sponge=0):
-    cfg = O.Config(p.nx, p.ny, p.bc, limiter, p.gamma, 0.5, eps, sponge)
+    cfg = oracle_cfg(p, limiter, eps, sponge)
     return O.run(cfg, p.conserved(), p.dx, nsteps=nsteps, t_end=t_end,
                  lam_fixed=lam if lam > 0 else None)
 
