@@ -39,7 +39,7 @@ BYTES_PER_LU = 160           # 20 FP32 values read + 20 written per cell update
 N_SIDE = 4096
 EPS = 1e-13
 FALLBACK_HBM_GBS = 6800.0
-CTL_BYTES = 472              # device control block read back by vlbm_monitors
+CTL_BYTES = 480              # device control block read back by vlbm_monitors
 SPONGE = 5                   # theta = 0 layer at zero-gradient sides, as the paper pairs them (Sec. 4.2)
 
 

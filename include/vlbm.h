@@ -70,11 +70,15 @@ extern "C" {
 #define VLBM_LIM_RLMP 4
 
 /* Boundary rule per side (Sec. 4: periodic; zero gradient of all
- * distributions; reflective (symmetry) wall). A periodic side must face a
- * periodic side. */
+ * distributions; reflective (symmetry) wall; a prescribed state whose
+ * distributions are its Maxwellians, as the double Mach reflection of Sec. 4.7
+ * and the jets of Sec. 4.8 use at their boundaries). A periodic side must face
+ * a periodic side. VLBM_BC_DIRICHLET needs a vlbm_boundary (vlbm_opts) for its
+ * field. */
 #define VLBM_BC_PERIODIC 0
 #define VLBM_BC_TRANSMISSIVE 1
 #define VLBM_BC_REFLECTIVE 2
+#define VLBM_BC_DIRICHLET 3
 
 /* Arithmetic of the state. FP32: populations, collision and density bounds
  * in float; the internal-energy bound theta_p is settled per face by a float
@@ -100,6 +104,35 @@ typedef struct {
     int32_t bc[4];
 } vlbm_grid;
 
+/* Field of the prescribed (VLBM_BC_DIRICHLET) parts of the boundary. At the
+ * start time t of a step, the ghost cell with centre (x, y) holds the conserved
+ * state `in` if nx[k] x + ny[k] y >= c0[k] + c1[k] t for every k < nplanes, and
+ * `out` otherwise (each side of the test evaluated in double, products first);
+ * its populations are the Maxwellians M_1..M_4 of that state at the step's
+ * kinetic speed. Both states must lie in G. The kinetic speed lambda^n also
+ * covers both states (so that Bouchut's condition holds on the boundary faces). */
+typedef struct {
+    double in[4], out[4];            /* conserved (rho, m1, m2, E) */
+    int32_t nplanes;                 /* 0, 1 or 2 half-planes (0: `in` everywhere) */
+    double nx[2], ny[2], c0[2], c1[2];
+} vlbm_field;
+
+/* Boundary beyond vlbm_grid.bc: sides that switch type once along their length
+ * (a partial wall, Sec. 4.7) and the prescribed field. The ghost cells of side s
+ * (0 west, 1 east, 2 south, 3 north) whose index along the side -- column i for
+ * south/north, row j for west/east, ghost indices included -- is below split[s]
+ * follow grid.bc[s], the others bc_hi[s]. split[s] = 0: a uniform side (bc_hi[s]
+ * must equal bc[s]); otherwise 2 <= split[s] <= n - 2 along that side, so that
+ * the two cells at either end, and the corner ghosts beyond them, share a type.
+ * A periodic side does not switch. Cell (i, j) has centre
+ * (x0 + (i + 1/2) dx, y0 + (j + 1/2) dx). */
+typedef struct {
+    int32_t bc_hi[4];
+    int32_t split[4];
+    double x0, y0;
+    vlbm_field field;
+} vlbm_boundary;
+
 /* Optional settings; pass NULL for the defaults. */
 typedef struct {
     double alpha;     /* D2Q5 rest weight M_5 = alpha u; 1/2 <= alpha < 1 (Prop. convex
@@ -109,7 +142,10 @@ typedef struct {
     int32_t sponge;   /* sponge layer of Sec. 4.2: theta = 0 on every face of the cells within
                          `sponge` cells of a zero-gradient side (the paper uses 5 with its
                          zero-gradient boundaries); 0 = none; at most n / 2 along every axis
-                         that has a zero-gradient side */
+                         that has a zero-gradient side. A side counts as zero-gradient when
+                         it is so along its whole length */
+    const vlbm_boundary *boundary;   /* NULL: uniform sides, no prescribed state. Copied by
+                                        vlbm_init; the batch applies it to every grid */
 } vlbm_opts;
 
 /* Host copy of the device-side step state and monitors. */
@@ -328,7 +364,8 @@ typedef struct {
  *   d_in, d_out: caller-owned device buffers of 20 compact planes each (u, then
  *     u_1..u_4, 4 planes each, plane q at q * nx * ny, cell (i, j) at j * nx + i)
  *     in the given precision; they must not overlap. Boundaries are applied on
- *     the fly from grid->bc.
+ *     the fly from grid->bc; opts->boundary must be NULL (a prescribed field
+ *     needs the time, which this call does not keep: VLBM_E_UNSUPPORTED).
  *   a: the kinetic speed of this step (Delta t = dx / a); result->a_next is the
  *     dynamic speed for the next one.
  * The only scratch, one reduction record per CTA of 32 x 8 cells, lives in a

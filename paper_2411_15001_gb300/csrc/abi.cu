@@ -58,7 +58,7 @@ static bool grid_ok(const vlbm_grid *g) {
     if (!g || g->nx < 4 || g->ny < 4 || !(g->dx > 0.0)) return false;
     if ((long long)g->nx * g->ny > (1ll << 31)) return false;
     for (int k = 0; k < 4; ++k)
-        if (g->bc[k] < VLBM_BC_PERIODIC || g->bc[k] > VLBM_BC_REFLECTIVE) return false;
+        if (g->bc[k] < VLBM_BC_PERIODIC || g->bc[k] > VLBM_BC_DIRICHLET) return false;
     if ((g->bc[0] == VLBM_BC_PERIODIC) != (g->bc[1] == VLBM_BC_PERIODIC)) return false;
     if ((g->bc[2] == VLBM_BC_PERIODIC) != (g->bc[3] == VLBM_BC_PERIODIC)) return false;
     return true;
@@ -96,7 +96,8 @@ static void build_desc(vlbm_state *s) {
     d.pitch = s->L.pitch;
     d.nx = s->grid.nx;
     d.ny = s->grid.ny;
-    for (int q = 0; q < 4; ++q) d.bc[q] = s->grid.bc[q];
+    uniform_types(s->bd, d.bc);
+    d.bd = s->bd;
     d.strips = s->strips;
     d.chunk = s->chunk;
     d.item0 = 0;
@@ -272,7 +273,7 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
     if (!out) return fail(nullptr, VLBM_E_INVAL, "out is NULL");
     *out = nullptr;
     if (!grid_ok(grid))
-        return fail(nullptr, VLBM_E_INVAL, "grid: need nx, ny >= 4, dx > 0, bc in 0..2, periodic sides paired");
+        return fail(nullptr, VLBM_E_INVAL, "grid: need nx, ny >= 4, dx > 0, bc in 0..3, periodic sides paired");
     if (!(gamma > 1.0)) return fail(nullptr, VLBM_E_INVAL, "gamma must be > 1");
     if (limiter < VLBM_LIM_FIRST_ORDER || limiter > VLBM_LIM_RLMP)
         return fail(nullptr, VLBM_E_INVAL, "limiter out of range");
@@ -284,6 +285,8 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
     if (!(o.eps >= 0.0 && o.eps < 1e-3)) return fail(nullptr, VLBM_E_INVAL, "eps must be in [0, 1e-3)");
     if (o.kernel < VLBM_KERNEL_AUTO || o.kernel > VLBM_KERNEL_FUSED)
         return fail(nullptr, VLBM_E_INVAL, "kernel out of range");
+    Bound bd;
+    if (const char *why = make_bound(*grid, o.boundary, &bd)) return fail(nullptr, VLBM_E_INVAL, "boundary: %s", why);
     if (!sponge_ok(o.sponge, *grid))
         return fail(nullptr, VLBM_E_INVAL, "sponge must be in [0, n / 2] along every axis with a zero-gradient side");
     if (!(lambda == lambda)) return fail(nullptr, VLBM_E_INVAL, "lambda is NaN");
@@ -315,11 +318,13 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
     s->alpha = o.alpha;
     s->eps = o.eps;
     s->sponge = o.sponge;
+    s->bd = bd;
     s->a_fixed = lambda > 0.0 ? 2.0 * lambda / (1.0 - o.alpha) : 0.0;
     s->L = L;
     s->ws = d_workspace;
     s->stream = (cudaStream_t)stream;
     s->ctl = (DevCtl *)((char *)d_workspace + L.ctl_offset);
+    s->bd.ctl = s->ctl;
     s->device = pa.device;
     {
         DeviceGuard g(s->device);

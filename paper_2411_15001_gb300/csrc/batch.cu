@@ -34,6 +34,7 @@ struct vlbm_batch {
     double gamma = 1.4, alpha = 0.5, eps = 1e-16;
     int sponge = 0;
     std::vector<vlbm_grid> grids;
+    std::vector<Bound> bds;   // per grid: split sides and the prescribed field (opts->boundary)
     std::vector<Layout> L;
     std::vector<size_t> buf_off;       // per grid: offset of its two state buffers
     std::vector<CUtensorMap> tmaps;
@@ -69,7 +70,7 @@ static int bfail(vlbm_batch *b, int code, const char *fmt, ...) {
 static bool grid_ok(const vlbm_grid &g) {
     if (g.nx < 4 || g.ny < 4 || !(g.dx > 0.0)) return false;
     for (int k = 0; k < 4; ++k)
-        if (g.bc[k] < VLBM_BC_PERIODIC || g.bc[k] > VLBM_BC_REFLECTIVE) return false;
+        if (g.bc[k] < VLBM_BC_PERIODIC || g.bc[k] > VLBM_BC_DIRICHLET) return false;
     if ((g.bc[0] == VLBM_BC_PERIODIC) != (g.bc[1] == VLBM_BC_PERIODIC)) return false;
     if ((g.bc[2] == VLBM_BC_PERIODIC) != (g.bc[3] == VLBM_BC_PERIODIC)) return false;
     return true;
@@ -110,13 +111,15 @@ static StepArgs<T> inst_args(const vlbm_batch *b, int i) {
     A.pitch = b->L[i].pitch;
     A.nx = b->grids[i].nx;
     A.ny = b->grids[i].ny;
-    for (int k = 0; k < 4; ++k) A.bc[k] = b->grids[i].bc[k];
+    uniform_types(b->bds[i], A.bc);
     A.limiter = b->limiter;
     A.gamma = b->gamma;
     A.alpha = b->alpha;
     A.eps = b->eps;
     A.ctl = (DevCtl *)((char *)b->ws + b->ctl_off + (size_t)i * kCtlStride);
     A.sponge = b->sponge;
+    A.bd = b->bds[i];
+    A.bd.ctl = A.ctl;
     return A;
 }
 
@@ -144,6 +147,7 @@ static void build_items(vlbm_batch *b) {
         d.nx = A.nx;
         d.ny = A.ny;
         for (int k = 0; k < 4; ++k) d.bc[k] = A.bc[k];
+        d.bd = A.bd;
         d.strips = (A.nx + kFusedOut - 1) / kFusedOut;
         d.chunk = b->chunk;
         d.item0 = (int)b->items_host.size();
@@ -288,6 +292,10 @@ int vlbm_batch_init(int32_t n, const vlbm_grid *grids, double gamma, int32_t lim
     if (opts) o = *opts;
     if (!(o.alpha >= 0.5 && o.alpha < 1.0) || !(o.eps >= 0.0 && o.eps < 1e-3))
         return bfail(nullptr, VLBM_E_INVAL, "alpha or eps out of range");
+    std::vector<Bound> bds(n);
+    for (int i = 0; i < n; ++i)
+        if (const char *why = make_bound(grids[i], o.boundary, &bds[i]))
+            return bfail(nullptr, VLBM_E_INVAL, "boundary of grid %d: %s", i, why);
     for (int i = 0; i < n; ++i)
         if (!sponge_ok(o.sponge, grids[i]))
             return bfail(nullptr, VLBM_E_INVAL, "sponge of grid %d: at most n / 2 along an axis with a "
@@ -317,6 +325,7 @@ int vlbm_batch_init(int32_t n, const vlbm_grid *grids, double gamma, int32_t lim
     b->eps = o.eps;
     b->sponge = o.sponge;
     b->grids.assign(grids, grids + n);
+    b->bds = bds;
     b->ws = d_workspace;
     b->stream = (cudaStream_t)stream;
     b->device = pa.device;

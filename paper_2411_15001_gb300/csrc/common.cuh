@@ -196,7 +196,8 @@ __device__ __forceinline__ void plan_next(DevCtl *C, double t, double a_free) {
 // the step's Delta t, monitors are published, sticky errors recorded.
 __device__ inline void finalize_step(DevCtl *C) {
     volatile DevCtl *V = C;
-    const double lam = key_to_double(V->lam_key);
+    const double lam_cells = key_to_double(V->lam_key);
+    const double lam = C->lam_bc > lam_cells ? C->lam_bc : lam_cells;   // NaN stays NaN
     const double minrho = key_to_double(V->minrho_key);
     const double minrhoe = key_to_double(V->minrhoe_key);
     const unsigned long long bad = V->bad, nonfin = V->nonfinite;
@@ -258,9 +259,66 @@ __device__ __forceinline__ int ghost_source(int i, int n, int bc_lo, int bc_hi, 
     return i < 0 ? -1 - i : 2 * n - 1 - i;
 }
 
+// Source of ghost index i (outside [0, n)) under side type `type` (not Dirichlet).
+__device__ __forceinline__ int ghost_source_typed(int i, int n, int type, bool *mirror) {
+    *mirror = type == VLBM_BC_REFLECTIVE;
+    if (type == VLBM_BC_PERIODIC) return i < 0 ? i + n : i - n;
+    if (type == VLBM_BC_TRANSMISSIVE) return i < 0 ? 0 : n - 1;
+    return i < 0 ? -1 - i : 2 * n - 1 - i;
+}
+
+// The prescribed field at the centre of cell (i, j) at time t (vlbm_field): both
+// sides of each half-plane test rounded after every operation, products first,
+// in double whatever the state's precision.
+template <typename T>
+__device__ __forceinline__ void field_state(const Bound &B, int i, int j, double t, T u[4]) {
+    const double x = __dadd_rn(B.x0, __dmul_rn((double)i + 0.5, B.dx));
+    const double y = __dadd_rn(B.y0, __dmul_rn((double)j + 0.5, B.dx));
+    bool inside = true;
+    for (int k = 0; k < B.nplanes; ++k)
+        if (!(__dadd_rn(__dmul_rn(B.pnx[k], x), __dmul_rn(B.pny[k], y)) >= __dadd_rn(B.c0[k], __dmul_rn(B.c1[k], t))))
+            inside = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[q] = (T)(inside ? B.in[q] : B.out[q]);
+}
+
+template <typename T>
+struct GhostState {
+    T u[4];
+    int hit;   // the cell holds a prescribed state (populations at equilibrium)
+};
+
+// Ghost cell (i, j) as the boundary prescribes it: a Dirichlet part of a side
+// (the field at the cell's centre), or a corner that takes the y rule of a
+// Dirichlet x ghost (its copy or mirror image). hit = 0 for every other cell.
+// The x rule applies first, then the y rule, as for the other ghost cells.
+template <typename T>
+__device__ __noinline__ GhostState<T> dirichlet_ghost(const Bound *B, int nx, int ny, int i, int j) {
+    GhostState<T> g;
+    g.hit = 0;
+    const bool gx = i < 0 || i >= nx, gy = j < 0 || j >= ny;
+    int sj = j;
+    bool flip = false;
+    if (gy) {
+        const int ty = side_type(*B, j < 0 ? 2 : 3, i);
+        if (ty != VLBM_BC_DIRICHLET) {
+            if (!gx) return g;
+            sj = ghost_source_typed(j, ny, ty, &flip);
+            if (side_type(*B, i < 0 ? 0 : 1, sj) != VLBM_BC_DIRICHLET) return g;
+        }
+    } else {
+        if (!gx || side_type(*B, i < 0 ? 0 : 1, j) != VLBM_BC_DIRICHLET) return g;
+    }
+    field_state(*B, i, sj, B->ctl->t, g.u);
+    if (flip) g.u[2] = -g.u[2];
+    g.hit = 1;
+    return g;
+}
+
 // Fill the two ghost layers of buffer (n & 1): periodic wrap, zero-gradient copy
 // of u and u_1..u_4, or the mirror image (normal momentum negated in u and all
-// populations, u_1 <-> u_2 across an x-wall, u_3 <-> u_4 across a y-wall).
+// populations, u_1 <-> u_2 across an x-wall, u_3 <-> u_4 across a y-wall); a
+// prescribed state with its Maxwellians at the next step's kinetic speed.
 // Corners take the x rule, then the y rule.
 template <typename T>
 __global__ void k_ghosts(StepArgs<T> A) {
@@ -280,10 +338,39 @@ __global__ void k_ghosts(StepArgs<T> A) {
         gj = (int)(q % ny);
         gi = c < 2 ? c - 2 : nx + (c - 2);
     }
-    bool mx, my;
-    const int si = ghost_source(gi, nx, A.bc[0], A.bc[1], &mx);
-    const int sj = ghost_source(gj, ny, A.bc[2], A.bc[3], &my);
     T *buf = (A.ctl->n & 1) ? A.buf1 : A.buf0;
+    if (A.bd.has_dir) {
+        const GhostState<T> gs = dirichlet_ghost<T>(&A.bd, nx, ny, gi, gj);
+        if (gs.hit) {
+            const StepConsts<T> k = consts_of<T>(A.ctl);
+            T f[4], g[4], M1[4], M2[4], M3[4], M4[4];
+            euler_fluxes(gs.u, k.gm1, f, g);
+            maxwell_pm(gs.u, f, k, M1, M2);
+            maxwell_pm(gs.u, g, k, M3, M4);
+            const long long dst = cidx(A, gi, gj);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                buf[q * A.plane + dst] = gs.u[q];
+                buf[(4 + q) * A.plane + dst] = M1[q];
+                buf[(8 + q) * A.plane + dst] = M2[q];
+                buf[(12 + q) * A.plane + dst] = M3[q];
+                buf[(16 + q) * A.plane + dst] = M4[q];
+            }
+            return;
+        }
+    }
+    // source cell: the y rule (type at column gi) applied to the x rule (type at the
+    // source row); uniform sides skip the look-up
+    bool mx = false, my = false;
+    int sj = gj, si = gi;
+    if (gj < 0 || gj >= ny) {
+        const int s = gj < 0 ? 2 : 3;
+        sj = ghost_source_typed(gj, ny, A.bc[s] >= 0 ? A.bc[s] : side_type(A.bd, s, gi), &my);
+    }
+    if (gi < 0 || gi >= nx) {
+        const int s = gi < 0 ? 0 : 1;
+        si = ghost_source_typed(gi, nx, A.bc[s] >= 0 ? A.bc[s] : side_type(A.bd, s, sj), &mx);
+    }
     const long long src = cidx(A, si, sj), dst = cidx(A, gi, gj);
     T v[kNPlane];
 #pragma unroll
@@ -328,7 +415,19 @@ __global__ void k_init_load(StepArgs<T> A, const T *__restrict__ rho, const T *_
     if (last_block(C, gridDim.x * gridDim.y)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             volatile DevCtl *V = C;
-            const double lam = key_to_double(V->lam_key);
+            // lambda^0 also covers the prescribed boundary states (as every later lambda^n)
+            double lam_bc = 0.0;
+            if (A.bd.has_dir) {
+                T st[4];
+                for (int q = 0; q < 4; ++q) st[q] = (T)A.bd.in[q];
+                lam_bc = (double)cell_speed(st, gamma, gm1);
+                for (int q = 0; q < 4; ++q) st[q] = (T)A.bd.out[q];
+                const double l2 = (double)cell_speed(st, gamma, gm1);
+                if (l2 > lam_bc) lam_bc = l2;
+            }
+            C->lam_bc = lam_bc;
+            const double lam_cells = key_to_double(V->lam_key);
+            const double lam = lam_bc > lam_cells ? lam_bc : lam_cells;
             const unsigned long long bad = V->bad + V->nonfinite;
             C->invalid_init = bad ? 1 : 0;
             C->lambda = lam;

@@ -2,7 +2,62 @@
 // checkpoint header) and their launchers.
 #include "common.cuh"
 
+#include <math.h>
+
 namespace vlbm {
+
+static bool state_in_G(const double u[4]) {
+    for (int q = 0; q < 4; ++q)
+        if (!(u[q] == u[q]) || u[q] == HUGE_VAL || u[q] == -HUGE_VAL) return false;
+    return u[0] > 0.0 && u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0] > 0.0;
+}
+
+const char *make_bound(const vlbm_grid &g, const vlbm_boundary *b, Bound *out) {
+    Bound B;
+    memset(&B, 0, sizeof B);
+    for (int s = 0; s < 4; ++s) {
+        const int n = s < 2 ? g.ny : g.nx;   // cells along side s
+        B.lo[s] = g.bc[s];
+        B.hi[s] = b ? b->bc_hi[s] : g.bc[s];
+        B.split[s] = b ? b->split[s] : 0;
+        if (B.lo[s] < VLBM_BC_PERIODIC || B.lo[s] > VLBM_BC_DIRICHLET || B.hi[s] < VLBM_BC_PERIODIC ||
+            B.hi[s] > VLBM_BC_DIRICHLET)
+            return "boundary type out of range";
+        if (B.split[s] == 0 ? B.hi[s] != B.lo[s] : (B.split[s] < 2 || B.split[s] > n - 2))
+            return "split: 0 with bc_hi = bc, or 2 <= split <= n - 2 along the side";
+        if ((B.lo[s] == VLBM_BC_PERIODIC || B.hi[s] == VLBM_BC_PERIODIC) && B.split[s] != 0)
+            return "a periodic side cannot switch type";
+        if (B.lo[s] == VLBM_BC_DIRICHLET || B.hi[s] == VLBM_BC_DIRICHLET) B.has_dir = 1;
+    }
+    if ((B.lo[0] == VLBM_BC_PERIODIC) != (B.lo[1] == VLBM_BC_PERIODIC) ||
+        (B.lo[2] == VLBM_BC_PERIODIC) != (B.lo[3] == VLBM_BC_PERIODIC))
+        return "a periodic side must face a periodic side";
+    if (B.has_dir) {
+        if (!b) return "VLBM_BC_DIRICHLET needs opts->boundary for its field";
+        const vlbm_field &f = b->field;
+        if (f.nplanes < 0 || f.nplanes > 2) return "field: nplanes must be 0, 1 or 2";
+        if (!state_in_G(f.in) || !state_in_G(f.out)) return "field: both states must be finite and in G";
+        B.nplanes = f.nplanes;
+        for (int k = 0; k < 2; ++k) {
+            B.pnx[k] = f.nx[k];
+            B.pny[k] = f.ny[k];
+            B.c0[k] = f.c0[k];
+            B.c1[k] = f.c1[k];
+        }
+        for (int q = 0; q < 4; ++q) {
+            B.in[q] = f.in[q];
+            B.out[q] = f.out[q];
+        }
+    }
+    if (b) {
+        B.x0 = b->x0;
+        B.y0 = b->y0;
+    }
+    B.dx = g.dx;
+    B.ctl = nullptr;
+    *out = B;
+    return nullptr;
+}
 
 __global__ void k_ctl_reset(DevCtl *C, double dx, double alpha, double a_fixed, double eps,
                             double gamma) {
@@ -25,6 +80,7 @@ __global__ void k_ctl_reset(DevCtl *C, double dx, double alpha, double a_fixed, 
     C->a_fixed = a_fixed;
     C->eps = eps;
     C->gamma = gamma;
+    C->lam_bc = 0.0;
 }
 
 // Final time for vlbm_step_to (t_end > 0) or none (t_end <= 0).

@@ -198,8 +198,12 @@ extern "C" int vlbm_step_noalloc(const vlbm_grid *grid, double gamma, double a, 
                                  int32_t precision, const vlbm_opts *opts, const void *d_in, void *d_out,
                                  vlbm_step_result *result, void *stream) {
     if (!grid || grid->nx < 4 || grid->ny < 4 || !(grid->dx > 0.0)) return VLBM_E_INVAL;
-    for (int q = 0; q < 4; ++q)
+    // a prescribed field needs the time, which this call does not keep
+    if (opts && opts->boundary) return VLBM_E_UNSUPPORTED;
+    for (int q = 0; q < 4; ++q) {
+        if (grid->bc[q] == VLBM_BC_DIRICHLET) return VLBM_E_UNSUPPORTED;
         if (grid->bc[q] < VLBM_BC_PERIODIC || grid->bc[q] > VLBM_BC_REFLECTIVE) return VLBM_E_INVAL;
+    }
     if ((grid->bc[0] == VLBM_BC_PERIODIC) != (grid->bc[1] == VLBM_BC_PERIODIC) ||
         (grid->bc[2] == VLBM_BC_PERIODIC) != (grid->bc[3] == VLBM_BC_PERIODIC))
         return VLBM_E_INVAL;

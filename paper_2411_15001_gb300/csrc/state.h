@@ -14,6 +14,7 @@ struct vlbm_state {
     int precision, limiter, kernel;
     double gamma, lambda, alpha, eps, a_fixed;
     int sponge;
+    vlbm::Bound bd;     // split sides and the prescribed field (ctl set)
     vlbm::Layout L;
     void *ws;
     cudaStream_t stream;
@@ -69,13 +70,14 @@ inline StepArgs<T> args_of(const vlbm_state *s) {
     A.pitch = s->L.pitch;
     A.nx = s->grid.nx;
     A.ny = s->grid.ny;
-    for (int k = 0; k < 4; ++k) A.bc[k] = s->grid.bc[k];
+    uniform_types(s->bd, A.bc);
     A.limiter = s->limiter;
     A.gamma = s->gamma;
     A.alpha = s->alpha;
     A.eps = s->eps;
     A.ctl = s->ctl;
     A.sponge = s->sponge;
+    A.bd = s->bd;
     return A;
 }
 

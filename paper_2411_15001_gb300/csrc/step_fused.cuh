@@ -65,10 +65,17 @@ struct Geo {
 
 // Write the ghost images of interior cell (c, O) into `out`: its periodic
 // copies, zero-gradient copies or mirror images on the other side of every
-// boundary it sits next to (the inverse of the ghost_source map).
+// boundary it sits next to (the inverse of the ghost_source map). Prescribed
+// (Dirichlet) parts get no images: the step that reads them evaluates the field.
+// A side that switches type does so at least two cells from its ends, so the
+// types at (c, O) hold for the corner images too.
 template <typename T>
 __device__ __forceinline__ void write_ghost_images(const Geo &D, T *out, int c, int O,
-                                                   const T nv[kNPlane]) {
+                                                   const T nv[kNPlane], const Bound *bd) {
+    const int tW = D.bc[0] >= 0 ? D.bc[0] : side_type(*bd, 0, O);
+    const int tE = D.bc[1] >= 0 ? D.bc[1] : side_type(*bd, 1, O);
+    const int tS = D.bc[2] >= 0 ? D.bc[2] : side_type(*bd, 2, c);
+    const int tN = D.bc[3] >= 0 ? D.bc[3] : side_type(*bd, 3, c);
     int gx[3], gy[3];
     bool mxs[3], mys[3];
     int ngx = 1, ngy = 1;
@@ -77,35 +84,35 @@ __device__ __forceinline__ void write_ghost_images(const Geo &D, T *out, int c, 
     gy[0] = O;
     mys[0] = false;
     const int nx = D.nx, ny = D.ny;
-    if (D.bc[0] == VLBM_BC_PERIODIC) {
+    if (tW == VLBM_BC_PERIODIC) {
         if (c >= nx - 2) { gx[ngx] = c - nx; mxs[ngx++] = false; }
         if (c <= 1) { gx[ngx] = c + nx; mxs[ngx++] = false; }
     } else {
-        if (c == 0 && D.bc[0] == VLBM_BC_TRANSMISSIVE) {
+        if (c == 0 && tW == VLBM_BC_TRANSMISSIVE) {
             gx[ngx] = -1; mxs[ngx++] = false;
             gx[ngx] = -2; mxs[ngx++] = false;
         }
-        if (c <= 1 && D.bc[0] == VLBM_BC_REFLECTIVE) { gx[ngx] = -1 - c; mxs[ngx++] = true; }
-        if (c == nx - 1 && D.bc[1] == VLBM_BC_TRANSMISSIVE) {
+        if (c <= 1 && tW == VLBM_BC_REFLECTIVE) { gx[ngx] = -1 - c; mxs[ngx++] = true; }
+        if (c == nx - 1 && tE == VLBM_BC_TRANSMISSIVE) {
             gx[ngx] = nx; mxs[ngx++] = false;
             gx[ngx] = nx + 1; mxs[ngx++] = false;
         }
-        if (c >= nx - 2 && D.bc[1] == VLBM_BC_REFLECTIVE) { gx[ngx] = 2 * nx - 1 - c; mxs[ngx++] = true; }
+        if (c >= nx - 2 && tE == VLBM_BC_REFLECTIVE) { gx[ngx] = 2 * nx - 1 - c; mxs[ngx++] = true; }
     }
-    if (D.bc[2] == VLBM_BC_PERIODIC) {
+    if (tS == VLBM_BC_PERIODIC) {
         if (O >= ny - 2) { gy[ngy] = O - ny; mys[ngy++] = false; }
         if (O <= 1) { gy[ngy] = O + ny; mys[ngy++] = false; }
     } else {
-        if (O == 0 && D.bc[2] == VLBM_BC_TRANSMISSIVE) {
+        if (O == 0 && tS == VLBM_BC_TRANSMISSIVE) {
             gy[ngy] = -1; mys[ngy++] = false;
             gy[ngy] = -2; mys[ngy++] = false;
         }
-        if (O <= 1 && D.bc[2] == VLBM_BC_REFLECTIVE) { gy[ngy] = -1 - O; mys[ngy++] = true; }
-        if (O == ny - 1 && D.bc[3] == VLBM_BC_TRANSMISSIVE) {
+        if (O <= 1 && tS == VLBM_BC_REFLECTIVE) { gy[ngy] = -1 - O; mys[ngy++] = true; }
+        if (O == ny - 1 && tN == VLBM_BC_TRANSMISSIVE) {
             gy[ngy] = ny; mys[ngy++] = false;
             gy[ngy] = ny + 1; mys[ngy++] = false;
         }
-        if (O >= ny - 2 && D.bc[3] == VLBM_BC_REFLECTIVE) { gy[ngy] = 2 * ny - 1 - O; mys[ngy++] = true; }
+        if (O >= ny - 2 && tN == VLBM_BC_REFLECTIVE) { gy[ngy] = 2 * ny - 1 - O; mys[ngy++] = true; }
     }
     for (int a = 0; a < ngx; ++a)
         for (int e = 0; e < ngy; ++e) {
@@ -143,6 +150,11 @@ struct FusedCtx {
     Hist<T> h1, h2;         // rows R-1, R-2 of the own column
     T p3n[4];               // u_3 of row R-2 after the step (pulled from row R-3)
 
+    // The grid's descriptor (the tensor map is its first member).
+    __device__ __forceinline__ const InstDesc<T> *desc() const {
+        return reinterpret_cast<const InstDesc<T> *>(tmap);
+    }
+
     __device__ __forceinline__ void issue(int row) {
         const int slot = nissued % kRawSlots;
         mbar_expect_tx(&S.bar[slot], (uint32_t)(kNPlane * kFB * sizeof(T)));
@@ -174,6 +186,20 @@ struct FusedCtx {
         T u[4], f[4], g[4], M1[4], M2[4], M3[4], M4[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) u[q] = S.raw[slot][q][b];
+        // a prescribed ghost (Dirichlet part of the boundary): the field's state with
+        // its populations at equilibrium, i.e. d_k = 0
+        bool dg = false;
+        if ((unsigned)c >= (unsigned)D.nx || (unsigned)R >= (unsigned)D.ny) {
+            const Bound *bd = &desc()->bd;
+            if (bd->has_dir) {
+                const GhostState<T> gs = dirichlet_ghost<T>(bd, D.nx, D.ny, c, R);
+                if (gs.hit) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) u[q] = gs.u[q];
+                    dg = true;
+                }
+            }
+        }
         euler_fluxes(u, k.gm1, f, g);
         maxwell_pm(u, f, k, M1, M2);
         maxwell_pm(u, g, k, M3, M4);
@@ -190,6 +216,13 @@ struct FusedCtx {
             S.X[xs][4 + q][b] = f[q];
             S.X[xs][8 + q][b] = d1;
             S.X[xs][12 + q][b] = d2;
+        }
+        if (dg) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                S.X[xs][8 + q][b] = S.X[xs][12 + q][b] = T(0);
+                h0.d3[q] = h0.d4[q] = T(0);
+            }
         }
         const T rsy_new = face_star(h1.u[0], h1.g[0], u[0], g[0], k);  // y-face R - 1/2
         __syncthreads();                                                  // S1
@@ -289,7 +322,7 @@ struct FusedCtx {
             const long long d = (long long)(O + kOY) * D.pitch + (c + kOX);
 #pragma unroll
             for (int q = 0; q < kNPlane; ++q) out[q * D.plane + d] = nv[q];
-            if (c < 2 || c >= D.nx - 2 || O < 2 || O >= D.ny - 2) write_ghost_images(D, out, c, O, nv);
+            if (c < 2 || c >= D.nx - 2 || O < 2 || O >= D.ny - 2) write_ghost_images(D, out, c, O, nv, &desc()->bd);
             mon.add_cell(nv, k.gamma, k.gm1);
         }
         // shift the register history

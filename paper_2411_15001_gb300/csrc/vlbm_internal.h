@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -110,16 +111,46 @@ struct DevCtl {
     double sum_last[4];
     // constants
     double dx, alpha, a_fixed, eps, gamma;
+    double lam_bc;         // cell speed of the prescribed boundary states (0: none), in lambda^n
     // the next step's constants (derived from a), set whenever a is
     StepConsts<float> kf;
     StepConsts<double> kd;
 };
 
-static_assert(sizeof(DevCtl) == 472, "bench.py reads the control block size");
+static_assert(sizeof(DevCtl) == 480, "bench.py reads the control block size");
+
+// Boundary beyond one uniform rule per side (vlbm_boundary): side s switches from
+// type lo[s] to hi[s] at index split[s] along it (0: uniform), and the prescribed
+// field of the VLBM_BC_DIRICHLET parts. Built on the host, read by the kernels on
+// their rare boundary paths only.
+struct Bound {
+    int lo[4], hi[4], split[4];
+    int has_dir;                       // some part of a side is VLBM_BC_DIRICHLET
+    int nplanes;
+    double x0, y0, dx;
+    double pnx[2], pny[2], c0[2], c1[2];
+    double in[4], out[4];              // conserved states of the field
+    const DevCtl *ctl;                 // the grid's control block (the field reads t)
+};
+
+// Type of side s at index k along it (column for south / north, row for west / east).
+__host__ __device__ inline int side_type(const Bound &B, int s, int k) {
+    return k < B.split[s] ? B.lo[s] : B.hi[s];
+}
+
+// Validate grid.bc with the optional vlbm_boundary and build the Bound of a grid
+// (ctl left NULL). Returns NULL, or a static message naming what is wrong.
+const char *make_bound(const vlbm_grid &g, const vlbm_boundary *b, Bound *out);
+
+// The uniform type of each side, -1 where the side switches type: what the hot
+// paths test (zero-gradient sides for the sponge, the ghost images' fast path).
+inline void uniform_types(const Bound &B, int bc[4]) {
+    for (int s = 0; s < 4; ++s) bc[s] = B.split[s] == 0 ? B.lo[s] : -1;
+}
 
 // One grid as the row-marching kernel sees it (device memory, 64-byte aligned).
 template <typename T>
-struct InstDesc {
+struct alignas(256) InstDesc {
     CUtensorMap tmap;     // 3D view [40 planes][ny + 4 rows][pitch] of both state buffers
     T *buf0, *buf1;
     long long plane;
@@ -129,7 +160,11 @@ struct InstDesc {
     int item0, nitems;    // this grid's work items in the launch
     DevCtl *ctl;
     int sponge;           // width of the theta = 0 layer at zero-gradient sides (Sec. 4.2)
+    Bound bd;             // split sides and the prescribed field
 };
+
+static_assert(offsetof(InstDesc<float>, tmap) == 0 && offsetof(InstDesc<double>, tmap) == 0,
+              "the row-marching kernel finds the descriptor from its tensor map");
 
 // A sponge width fits a grid when it is >= 0 and at most half the cells along every
 // axis that has a zero-gradient side (the layer exists only next to such sides).
@@ -173,13 +208,14 @@ struct StepArgs {
     long long plane;    // plane stride (elements)
     int pitch;
     int nx, ny;
-    int bc[4];          // west, east, south, north
+    int bc[4];          // west, east, south, north: the uniform type, -1 where a side switches
     int limiter;
     double gamma;
     double alpha;
     double eps;
     DevCtl *ctl;
     int sponge;         // width of the theta = 0 layer at zero-gradient sides (Sec. 4.2)
+    Bound bd;           // split sides and the prescribed field
 };
 
 // Host launchers (stream-ordered; return cudaError_t of the launch).

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libvlbm.so")
 
 OK, E_INVAL, E_CUDA, E_POSITIVITY, E_NONFINITE, E_TIMEOUT, E_UNSUPPORTED, E_NOMEM = 0, -1, -2, -3, -4, -5, -6, -7
 LIM_FIRST_ORDER, LIM_NONE, LIM_PP, LIM_LMP, LIM_RLMP = range(5)
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = range(3)
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_DIRICHLET = range(4)
 FP64, FP32 = 0, 1
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_FUSED = range(3)
 
@@ -27,9 +27,47 @@ class vlbm_grid(ctypes.Structure):
                 ("bc", ctypes.c_int32 * 4)]
 
 
+class vlbm_field(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_double * 4), ("out", ctypes.c_double * 4), ("nplanes", ctypes.c_int32),
+                ("nx", ctypes.c_double * 2), ("ny", ctypes.c_double * 2), ("c0", ctypes.c_double * 2),
+                ("c1", ctypes.c_double * 2)]
+
+
+class vlbm_boundary(ctypes.Structure):
+    _fields_ = [("bc_hi", ctypes.c_int32 * 4), ("split", ctypes.c_int32 * 4), ("x0", ctypes.c_double),
+                ("y0", ctypes.c_double), ("field", vlbm_field)]
+
+
 class vlbm_opts(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("eps", ctypes.c_double), ("kernel", ctypes.c_int32),
-                ("sponge", ctypes.c_int32)]
+                ("sponge", ctypes.c_int32), ("boundary", ctypes.POINTER(vlbm_boundary))]
+
+
+def make_boundary(bc, bc_hi=None, split=(0, 0, 0, 0), x0=0.0, y0=0.0, field=None):
+    """vlbm_boundary from per-side types and an optional prescribed field: `field` is
+    (inside, outside, planes) with conserved 4-tuples and up to two half-planes
+    (nx, ny, c0, c1), or an object with those attributes."""
+    b = vlbm_boundary()
+    b.bc_hi[:] = list(bc if bc_hi is None else bc_hi)
+    b.split[:] = list(split)
+    b.x0, b.y0 = float(x0), float(y0)
+    if field is not None:
+        inside, outside, planes = ((field.inside, field.outside, field.planes)
+                                   if hasattr(field, "inside") else field)
+        b.field.in_[:] = [float(v) for v in inside]
+        b.field.out[:] = [float(v) for v in outside]
+        b.field.nplanes = len(planes)
+        for k, (a, c, c0, c1) in enumerate(planes):
+            b.field.nx[k], b.field.ny[k], b.field.c0[k], b.field.c1[k] = a, c, c0, c1
+    return b
+
+
+def _opts(alpha, eps, kernel, sponge, boundary):
+    o = vlbm_opts(alpha, eps, kernel, sponge, None)
+    if boundary is not None:
+        o._boundary_keep = boundary          # the struct must outlive the call that reads it
+        o.boundary = ctypes.pointer(boundary)
+    return o
 
 
 class vlbm_monitor_t(ctypes.Structure):
@@ -298,7 +336,8 @@ class VLBM:
 
     def __init__(self, nx: int, ny: int, dx: float, bc=(0, 0, 0, 0), gamma: float = 1.4,
                  lam: float = 0.0, limiter=LIM_PP, precision=FP32, alpha: float = 0.5,
-                 eps: float = 1e-16, kernel=KERNEL_AUTO, device=None, stream=None, sponge: int = 0):
+                 eps: float = 1e-16, kernel=KERNEL_AUTO, device=None, stream=None, sponge: int = 0,
+                 boundary: "vlbm_boundary | None" = None):
         import torch
 
         self.torch = torch
@@ -311,7 +350,7 @@ class VLBM:
         self.precision = precision
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self.grid = vlbm_grid(nx, ny, dx, (ctypes.c_int32 * 4)(*bc))
-        self.opts = vlbm_opts(alpha, eps, kernel, sponge)
+        self.opts = _opts(alpha, eps, kernel, sponge, boundary)
         nbytes = vlbm_workspace_bytes(self.grid, precision)
         if nbytes == 0:
             raise VLBMError(E_INVAL, "invalid grid")
@@ -427,8 +466,9 @@ class VLBMBatch:
     """Independent grids of uneven sizes advanced together (vlbm_batch_*)."""
 
     def __init__(self, grids, gamma: float = 1.4, limiter=LIM_PP, precision=FP32,
-                 alpha: float = 0.5, eps: float = 1e-16, device=None, stream=None, sponge: int = 0):
-        """grids: sequence of (nx, ny, dx, bc) tuples."""
+                 alpha: float = 0.5, eps: float = 1e-16, device=None, stream=None, sponge: int = 0,
+                 boundary: "vlbm_boundary | None" = None):
+        """grids: sequence of (nx, ny, dx, bc) tuples; `boundary` applies to every grid."""
         import torch
 
         self.torch = torch
@@ -442,7 +482,7 @@ class VLBMBatch:
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self._grids = [vlbm_grid(int(g[0]), int(g[1]), float(g[2]), (ctypes.c_int32 * 4)(*g[3]))
                        for g in grids]
-        self.opts = vlbm_opts(alpha, eps, 0, sponge)
+        self.opts = _opts(alpha, eps, 0, sponge, boundary)
         nbytes = vlbm_batch_workspace_bytes(self._grids, precision)
         if nbytes == 0:
             raise VLBMError(E_INVAL, "invalid grids")

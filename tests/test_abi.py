@@ -60,7 +60,9 @@ def test_workspace_bytes(V):
     assert V.vlbm_workspace_bytes(g, 7) == 0
 
 
-@pytest.mark.parametrize("case", ["grid", "gamma", "limiter", "precision", "alpha", "workspace", "small"])
+@pytest.mark.parametrize("case", ["grid", "gamma", "limiter", "precision", "alpha", "workspace", "small",
+                                  "dirichlet_without_field", "split_near_corner", "periodic_split",
+                                  "types_differ_without_split", "field_state_outside_G", "field_planes"])
 def test_init_rejects_bad_arguments(V, case):
     g = _grid(V)
     gamma, lim, prec = 1.4, V.LIM_PP, V.FP32
@@ -80,6 +82,25 @@ def test_init_rejects_bad_arguments(V, case):
         ws = 256 * 1024 + 8        # misaligned
     elif case == "small":
         nbytes = 100
+    elif case == "dirichlet_without_field":
+        g = _grid(V, bc=(3, 1, 1, 1))
+    else:
+        g = _grid(V, bc=(3, 1, 2, 1))
+        good = ((1.0, 0.0, 0.0, 2.5), (0.5, 0.1, 0.0, 1.0), ((1.0, 0.0, 0.3, 0.0),))
+        kw = dict(bc_hi=(3, 1, 3, 1), split=(0, 0, 5, 0), field=good)
+        if case == "split_near_corner":
+            kw["split"] = (0, 0, 1, 0)
+        elif case == "periodic_split":
+            g = _grid(V, bc=(0, 0, 2, 1))
+            kw = dict(bc_hi=(0, 1, 2, 1), split=(0, 4, 0, 0))
+        elif case == "types_differ_without_split":
+            kw["split"] = (0, 0, 0, 0)
+        elif case == "field_state_outside_G":
+            kw["field"] = ((1.0, 3.0, 0.0, 2.5), good[1], good[2])   # E < |m|^2 / (2 rho)
+        b = V.make_boundary((3, 1, 2, 1), **kw)
+        if case == "field_planes":
+            b.field.nplanes = 3
+        opts = V._opts(0.5, 1e-16, 0, 0, b)
     rc, s = V.vlbm_init(g, gamma, 0.0, lim, prec, opts, ws, nbytes, None)
     assert rc in (V.E_INVAL, V.E_NOMEM) and not s.value
     assert V.vlbm_last_error_detail()
@@ -100,3 +121,26 @@ def test_calls_on_null_state(V):
     assert V.vlbm_moments(None, None, None, None) == V.E_INVAL
     assert V.vlbm_checkpoint_bytes(None) == 0
     V.vlbm_destroy(None)
+
+
+def test_struct_layouts_match_the_header(V, tmp_path):
+    """ctypes mirrors of the ABI structs have the C compiler's sizes and offsets."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text("""#include <stddef.h>
+#include <stdio.h>
+#include "vlbm.h"
+int main(void) {
+    printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(vlbm_opts), offsetof(vlbm_opts, boundary),
+           sizeof(vlbm_boundary), offsetof(vlbm_boundary, field), sizeof(vlbm_field),
+           offsetof(vlbm_field, nplanes), offsetof(vlbm_field, c1), sizeof(vlbm_grid));
+    return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(V.vlbm_opts), V.vlbm_opts.boundary.offset, ctypes.sizeof(V.vlbm_boundary),
+            V.vlbm_boundary.field.offset, ctypes.sizeof(V.vlbm_field), V.vlbm_field.nplanes.offset,
+            V.vlbm_field.c1.offset, ctypes.sizeof(V.vlbm_grid)]
+    assert got == want

@@ -1,0 +1,212 @@
+"""Prescribed-state (Dirichlet) boundaries and sides that switch type (partial walls)
+on the GPU (needs a GB300), against the oracle: the double Mach reflection of
+Sec. 4.7, the jets of Sec. 4.8 and a grid on which every side switches type.
+FP64: bit for bit the oracle's run (both kernels, and the batch). FP32: every step
+admissible and the density within max(1e-4, 4x the oracle's sensitivity to float
+rounding noise) in L1. The paper's own grids: every step admissible to the final
+time, then a step checked cell by cell on sampled 9 x 9 patches.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2411_15001_gb300 import workloads as W
+from tests.gpu_helpers import l1_rel, oracle_cfg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2411_15001_gb300 import vlbm as V  # noqa: E402
+
+
+def _boundary(p):
+    return V.make_boundary(p.bc, p.bc_hi, p.split, p.x0, p.y0, p.bfield)
+
+
+def _solver(p, lim, prec, kernel=V.KERNEL_AUTO, lam=0.0):
+    dt = torch.float64 if prec == V.FP64 else torch.float32
+    s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, gamma=p.gamma, lam=lam, limiter=lim, precision=prec,
+               kernel=kernel, device="cuda:0", boundary=_boundary(p))
+    c = torch.tensor(p.conserved(), dtype=dt, device="cuda:0")
+    s.set_conserved(c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+    return s
+
+
+def _switching_grid():
+    """Random admissible cells; every side switches type; a moving two-plane field."""
+    p = W.random_cells(40, 30, seed=7, bc=(1, 2, 3, 1))
+    p.bc_hi, p.split = (3, 1, 2, 3), (12, 9, 20, 25)
+    p.x0, p.y0 = -0.4, 0.2
+    p.bfield = W.BoundaryField(inside=W._conserved_state(1.2, 0.3, -0.2, 0.9, p.gamma),
+                               outside=W._conserved_state(0.7, -0.1, 0.25, 0.4, p.gamma),
+                               planes=((1.0, -0.6, 0.1, 0.8), (-0.2, 1.0, -0.4, -0.3)))
+    return p
+
+
+CASES = {
+    "dmr": (lambda: W.double_mach_reflection(24), V.LIM_LMP, 80),
+    "dmr_rlmp": (lambda: W.double_mach_reflection(30), V.LIM_RLMP, 60),
+    "jet80": (lambda: W.astro_jet(24), V.LIM_RLMP, 40),
+    "jet2000": (lambda: W.astro_jet(20, mach=2000), V.LIM_PP, 60),
+    "switching": (_switching_grid, V.LIM_PP, 50),
+    "switching_lmp": (_switching_grid, V.LIM_LMP, 50),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(case):
+    make, lim, steps = CASES[case]
+    p = make()
+    return O.run(oracle_cfg(p, lim), p.conserved(), p.dx, nsteps=steps)
+
+
+@pytest.mark.parametrize("kernel", [V.KERNEL_SIMPLE, V.KERNEL_FUSED])
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp64_equals_oracle(case, kernel):
+    make, lim, steps = CASES[case]
+    p = make()
+    s = _solver(p, lim, V.FP64, kernel)
+    s.step(steps)
+    got = s.state_planes().cpu().numpy()
+    m = s.monitors()
+    s.close()
+    ref = _oracle(case)
+    assert m["status"] == 0 and m["n"] == steps and m["t"] == ref["t"]
+    assert np.array_equal(got, ref["state"])
+
+
+def _sensitivity(case):
+    """Largest L1 change of the oracle's density when every value is perturbed by a
+    relative 2^-24 (seeded noise) after every step: what float rounding alone can do.
+    The jet is the touchy one: 1.4e-6 after 40 steps, ~1e-2 after 80."""
+    make, lim, steps = CASES[case]
+    p = make()
+    worst = 0.0
+    for seed in (1, 2):
+        rng = np.random.default_rng(seed)
+
+        def jitter(n, st):
+            st *= 1.0 + 5.96e-8 * rng.standard_normal(st.shape)
+
+        r = O.run(oracle_cfg(p, lim), p.conserved(), p.dx, nsteps=steps, callback=jitter)
+        worst = max(worst, l1_rel(r["state"][0], _oracle(case)["state"][0]))
+    return worst
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c != "jet2000"])
+def test_fp32_admissible_and_close(case):
+    """(The Mach 2000 jet's internal energy is 3e-7 of its kinetic energy, below the
+    resolution of a float state: FP64 only.)"""
+    make, lim, steps = CASES[case]
+    p = make()
+    s = _solver(p, lim, V.FP32, V.KERNEL_FUSED)
+    s.step(steps)
+    got = s.state_planes().double().cpu().numpy()
+    m = s.monitors()
+    s.close()
+    assert m["status"] == 0 and m["first_bad_step"] == -1
+    tol = max(1e-4, 4.0 * _sensitivity(case))
+    assert l1_rel(got[0], _oracle(case)["state"][0]) <= tol
+
+
+def test_lambda_covers_the_prescribed_states():
+    p = W.astro_jet(24)
+    s = _solver(p, V.LIM_RLMP, V.FP64)
+    lam_gpu = s.monitors()["lambda"]
+    s.close()
+    assert lam_gpu == O.max_speed(oracle_cfg(p, V.LIM_RLMP), O.new_state(p.conserved()))
+    assert lam_gpu > 30.0
+
+
+def test_batch_with_a_boundary_equals_oracle():
+    """Every grid of a batch takes the same vlbm_boundary (split index and field)."""
+    shapes = [(40, 30), (64, 20), (33, 41)]
+    probs = []
+    for k, (nx, ny) in enumerate(shapes):
+        p = W.random_cells(nx, ny, seed=20 + k, bc=(3, 1, 2, 3))
+        p.bc_hi, p.split, p.x0, p.y0 = (3, 1, 3, 3), (0, 0, 9, 0), -0.1, 0.0
+        p.bfield = _switching_grid().bfield
+        probs.append(p)
+    b = V.VLBMBatch([(p.nx, p.ny, p.dx, p.bc) for p in probs], limiter=V.LIM_LMP, precision=V.FP64,
+                    device="cuda:0", boundary=_boundary(probs[0]))
+    for i, p in enumerate(probs):
+        c = torch.tensor(p.conserved(), dtype=torch.float64, device="cuda:0")
+        b.set_conserved(i, c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+    b.step(30)
+    for i, p in enumerate(probs):
+        ref = O.run(oracle_cfg(p, V.LIM_LMP), p.conserved(), p.dx, nsteps=30)
+        assert b.monitors(i)["status"] == 0
+        assert np.array_equal(b.state_planes(i).cpu().numpy(), ref["state"])
+    b.close()
+
+
+def test_noalloc_rejects_a_boundary():
+    p = W.double_mach_reflection(24)
+    g = V.vlbm_grid(p.nx, p.ny, p.dx, (V.ctypes.c_int32 * 4)(*p.bc))
+    x = torch.zeros(20 * p.nx * p.ny, dtype=torch.float32, device="cuda:0")
+    y = torch.zeros_like(x)
+    rc, _ = V.vlbm_step_noalloc(g, 1.4, 40.0, V.LIM_PP, V.FP32, None, x.data_ptr(), y.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+    assert rc == V.E_UNSUPPORTED
+
+
+R = 4
+
+
+def _sampled_step(s, p, lim, cells, tol=1e-4):
+    """One more GPU step checked on 9 x 9 interior patches against the oracle."""
+    before = s.state_planes().cpu().numpy()
+    a = s.monitors()["a"]
+    s.step(1)
+    after = s.state_planes().cpu().numpy()
+    n = 2 * R + 1
+    cfg = O.Config(n, n, (1, 1, 1, 1), lim, p.gamma, 0.5, 1e-16)
+    for (j, i) in cells:
+        patch = np.ascontiguousarray(before[:, j - R:j + R + 1, i - R:i + R + 1], dtype=np.float64)
+        ref = O.step(cfg, patch, a)[:, R, R]
+        scale = np.abs(patch).reshape(20, -1).max(axis=1)
+        err = float((np.abs(after[:, j, i] - ref) / np.maximum(scale, 1e-300)).max())
+        assert err <= tol, (j, i, err)
+
+
+def _cells(before, nsample, seed):
+    ny, nx = before.shape[1:]
+    rng = np.random.default_rng(seed)
+    cells = [(int(rng.integers(R + 1, ny - R - 1)), int(rng.integers(R + 1, nx - R - 1))) for _ in range(nsample)]
+    g = np.abs(np.diff(before[0], axis=1))[R + 1:ny - R - 1, R + 1:nx - R - 2]
+    for k in np.argsort(g, axis=None)[-nsample:]:
+        j, i = np.unravel_index(k, g.shape)
+        cells.append((int(j) + R + 1, int(i) + R + 1))
+    return cells
+
+
+@pytest.mark.parametrize("lim", [V.LIM_LMP, V.LIM_RLMP])
+def test_double_mach_reflection_paper_grid(lim):
+    """1500 x 500 to t = 0.2 (FP32, every step admissible), then a sampled step."""
+    p = W.double_mach_reflection(500)
+    s = _solver(p, lim, V.FP32)
+    s.step_to(0.2 - 1e-3, 10 ** 6)
+    m = s.monitors()
+    assert m["status"] == 0 and m["first_bad_step"] == -1
+    before = s.state_planes().cpu().numpy()
+    _sampled_step(s, p, lim, _cells(before, 60, 3))
+    s.close()
+
+
+@pytest.mark.parametrize("mach,prec", [(80, V.FP32), (2000, V.FP64)])
+def test_jets_paper_grid(mach, prec):
+    """800 x 400 to the paper's final time, RLMP, every step admissible (the Mach 2000
+    jet in FP64: its internal energy is 3e-7 of the kinetic energy, below what a
+    float state resolves)."""
+    p = W.astro_jet(400, mach=mach)
+    s = _solver(p, V.LIM_RLMP, prec)
+    s.step_to(p.meta["t_end"], 10 ** 6)
+    m = s.monitors()
+    assert m["status"] == 0 and m["first_bad_step"] == -1 and m["done"] == 1
+    assert abs(m["t"] - p.meta["t_end"]) < 1e-12
+    s.close()
