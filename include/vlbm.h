@@ -311,10 +311,13 @@ VLBM_API const char *vlbm_batch_last_error(const vlbm_batch *b);
  * scheme (Sec. 3.2, eq. blending_u1 / blending_u, theta of Sec. 3.2-3.4) and the
  * equilibrium initialisation u_k^0 = M_k(u_0) (Sec. 4 preamble). The transpose
  * of each step is differentiated piecewise: theta on the branch the forward step
- * took (1, the density bound, the internal-energy bound, or the clamp at 0); the
- * kinetic speeds a^n are held as the forward run produced them (the fixed speed
- * of a state made with lambda > 0, else the recorded dynamic a^n, whose own
- * dependence on u through max lambda is not differentiated). Covered: the
+ * took (1, the density bound, the internal-energy bound, or the clamp at 0). The
+ * kinetic speeds a^n: with a fixed speed (a state made with lambda > 0) they are
+ * constants; with the dynamic speed a^n = 2 lambda^n / (1 - alpha) of Sec. 4,
+ * lambda^n = max over the cells of |v| + sqrt(gamma p / rho), they are held as
+ * the forward run produced them (VLBM_ADJOINT_HOLD_A, the default) or
+ * differentiated too (VLBM_ADJOINT_DIFF_A: the subgradient of the max taken at
+ * the first cell, in index order j nx + i, where it is reached). Covered: the
  * first-order, unlimited and PP schemes on fully periodic grids; other limiters
  * or boundaries return VLBM_E_UNSUPPORTED.
  *
@@ -324,6 +327,14 @@ VLBM_API const char *vlbm_batch_last_error(const vlbm_batch *b);
  * one forward run, one recomputation of every step but the last of each
  * segment, and one adjoint kernel per step. */
 VLBM_API size_t vlbm_adjoint_scratch_bytes(const vlbm_state *s, int64_t nsteps, int32_t ckpt_every);
+
+/* How vlbm_adjoint treats a dynamic kinetic speed (see above); the mode applies
+ * to later calls. With a fixed speed both modes give the same gradient. Cost of
+ * VLBM_ADJOINT_DIFF_A: two reads of the conserved planes per step (the argmax of
+ * lambda) and one reduction. VLBM_E_INVAL for an unknown mode. */
+#define VLBM_ADJOINT_HOLD_A 0
+#define VLBM_ADJOINT_DIFF_A 1
+VLBM_API int vlbm_adjoint_set_mode(vlbm_state *s, int32_t mode);
 
 /* Forward run with checkpoints: from the state vlbm_set_conserved left (n = 0),
  * advance nsteps steps with the state's kernel, storing a checkpoint before

@@ -13,7 +13,10 @@
 // population cotangents into the conserved planes.
 // a^n is held as the forward run produced it: a constant when the state was made
 // with a fixed lambda, else the step constants are recorded per step during the
-// recomputation.
+// recomputation. In VLBM_ADJOINT_DIFF_A mode (dynamic a only) the sweep also
+// carries dL/da^n of every step, and hands it to the state s^n through
+// a^n = 2 lambda^n / (1 - alpha), lambda^n = max over cells: the gradient of the
+// cell speed at the (first) cell where the max is taken.
 #include <stddef.h>
 #include <stdio.h>
 #include <string.h>
@@ -28,23 +31,48 @@ using namespace vlbm::api;
 
 namespace vlbm {
 
-template <typename T>
-static cudaError_t launch_adjoint_step(const AdjArgs<T> &A, int limiter, cudaStream_t s) {
+template <typename T, bool DA>
+static cudaError_t launch_adjoint_step_da(const AdjArgs<T> &A, int limiter, cudaStream_t s) {
     const dim3 blk(32, 8), grd((A.nx + 31) / 32, (A.ny + 7) / 8);
     switch (limiter) {
-        case VLBM_LIM_FIRST_ORDER: k_adjoint_step<T, VLBM_LIM_FIRST_ORDER><<<grd, blk, 0, s>>>(A); break;
-        case VLBM_LIM_NONE: k_adjoint_step<T, VLBM_LIM_NONE><<<grd, blk, 0, s>>>(A); break;
-        case VLBM_LIM_PP: k_adjoint_step<T, VLBM_LIM_PP><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_FIRST_ORDER: k_adjoint_step<T, VLBM_LIM_FIRST_ORDER, DA><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_NONE: k_adjoint_step<T, VLBM_LIM_NONE, DA><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_PP: k_adjoint_step<T, VLBM_LIM_PP, DA><<<grd, blk, 0, s>>>(A); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 template <typename T>
+static cudaError_t launch_adjoint_step(const AdjArgs<T> &A, int limiter, cudaStream_t s) {
+    return A.abar ? launch_adjoint_step_da<T, true>(A, limiter, s) : launch_adjoint_step_da<T, false>(A, limiter, s);
+}
+
+template <typename T>
 static cudaError_t launch_adjoint_init(const T *init_state, const Layout &L, const StepConsts<T> *kc, const T *cot,
-                                       T *grad, cudaStream_t s) {
+                                       T *grad, double *abar, cudaStream_t s) {
     const dim3 blk(32, 8), grd((L.nx + 31) / 32, (L.ny + 7) / 8);
-    k_adjoint_init<T><<<grd, blk, 0, s>>>(init_state, L.plane, L.pitch, L.nx, L.ny, kc, cot, grad);
+    k_adjoint_init<T><<<grd, blk, 0, s>>>(init_state, L.plane, L.pitch, L.nx, L.ny, kc, cot, grad, abar);
+    return cudaGetLastError();
+}
+
+// Slots of the dL/da hand-over (256 bytes of the scratch).
+struct ARed {
+    double abar;
+    unsigned long long key;
+    unsigned int idx;
+};
+
+// dL/da^n accumulated in the slots goes to the conserved planes of cot at the
+// cell where lambda(st) is largest; the slots are reset for the next step.
+template <typename T>
+static cudaError_t hand_over_abar(const T *st, const Layout &L, double gamma, double alpha, ARed *red, T *cot,
+                                  cudaStream_t s) {
+    const dim3 blk(32, 8), grd((L.nx + 31) / 32, (L.ny + 7) / 8);
+    k_lambda_max<T><<<grd, blk, 0, s>>>(st, L.plane, L.pitch, L.nx, L.ny, (T)gamma, &red->key);
+    k_lambda_argmax<T><<<grd, blk, 0, s>>>(st, L.plane, L.pitch, L.nx, L.ny, (T)gamma, &red->key, &red->idx);
+    k_lambda_apply<T><<<1, 1, 0, s>>>(st, L.plane, L.pitch, L.nx, gamma, alpha, &red->abar, &red->key, &red->idx, cot,
+                                      (long long)L.nx * L.ny);
     return cudaGetLastError();
 }
 
@@ -73,6 +101,7 @@ struct Plan {
     size_t khist_off;     // the step constants (a^n) of each step of a segment
     size_t cot_off;       // two cotangent buffers of 20 compact planes
     size_t cot_bytes;
+    size_t red_off;       // the dL/da hand-over slots
     size_t total;
 };
 
@@ -93,6 +122,8 @@ Plan plan_of(const vlbm_state *s, int64_t nsteps, int32_t every) {
     p.cot_bytes = round256((size_t)kNPlane * s->grid.nx * s->grid.ny * s->L.elem);
     p.cot_off = off;
     off += 2 * p.cot_bytes;
+    p.red_off = off;
+    off += 256;
     p.total = off;
     return p;
 }
@@ -182,11 +213,17 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     const size_t buf = s->L.buf_bytes;
     const long long N = (long long)s->grid.nx * s->grid.ny;
     const bool fixed_a = s->a_fixed > 0.0;
+    const bool diff_a = !fixed_a && s->adj_mode == VLBM_ADJOINT_DIFF_A;
+    ARed *red = (ARed *)(scratch + p.red_off);
     T *cot[2] = {(T *)(scratch + p.cot_off), (T *)(scratch + p.cot_off + p.cot_bytes)};
     DevCtl *segctl = (DevCtl *)(scratch + p.segctl_off);
     char *khist = scratch + p.khist_off;
     cudaError_t e = cudaMemcpyAsync(cot[0], dLduN, (size_t)4 * N * sizeof(T), cudaMemcpyDeviceToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(cot[0] + 4 * N, 0, (size_t)(kNPlane - 4) * N * sizeof(T), s->stream);
+    if (e == cudaSuccess && diff_a) {
+        e = cudaMemsetAsync(red, 0, sizeof(ARed), s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&red->idx, 0xff, sizeof(unsigned int), s->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(s, e, "cotangent seed");
     std::vector<unsigned char> descs;
     if (use_fused(s)) {
@@ -201,6 +238,7 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     A.pitch = s->L.pitch;
     A.nx = s->grid.nx;
     A.ny = s->grid.ny;
+    A.abar = diff_a ? &red->abar : nullptr;
     for (int64_t c = nsteps > 0 ? p.nckpt - 1 : -1; c >= 0; --c) {
         const int64_t s0 = c * every;
         const int64_t e0 = (s0 + every < nsteps ? s0 + every : nsteps) - 1;
@@ -223,11 +261,17 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
             e = launch_adjoint_step<T>(A, s->limiter, s->stream);
             if (e != cudaSuccess) return cuda_fail(s, e, "adjoint step launch");
             cur ^= 1;
+            if (diff_a && m > 0) {   // a^m came from lambda of s^m (a^0 waits for the init map)
+                e = hand_over_abar<T>(A.fwd, s->L, s->gamma, s->alpha, red, cot[cur], s->stream);
+                if (e != cudaSuccess) return cuda_fail(s, e, "kinetic-speed cotangent launch");
+            }
         }
     }
     const char *ck0 = scratch;
     e = launch_adjoint_init<T>((const T *)ck0, s->L, ctl_consts<T>((const DevCtl *)(ck0 + round256(buf))), cot[cur],
-                               (T *)dLdu0, s->stream);
+                               (T *)dLdu0, diff_a ? &red->abar : nullptr, s->stream);
+    if (e == cudaSuccess && diff_a)
+        e = hand_over_abar<T>((const T *)ck0, s->L, s->gamma, s->alpha, red, (T *)dLdu0, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "initialisation adjoint launch");
     return VLBM_OK;
 }
@@ -252,6 +296,13 @@ int vlbm_rollout(vlbm_state *s, int64_t nsteps, int32_t ckpt_every, void *d_scra
     int rc = check_scratch(s, d_scratch, scratch_bytes, p);
     if (rc) return rc;
     return rollout(s, nsteps, ckpt_every, (char *)d_scratch, p);
+}
+
+int vlbm_adjoint_set_mode(vlbm_state *s, int32_t mode) {
+    if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
+    if (mode != VLBM_ADJOINT_HOLD_A && mode != VLBM_ADJOINT_DIFF_A) return fail(s, VLBM_E_INVAL, "mode out of range");
+    s->adj_mode = mode;
+    return VLBM_OK;
 }
 
 int vlbm_adjoint(vlbm_state *s, const void *d_u0, int64_t nsteps, int32_t ckpt_every, const void *d_dLduN,

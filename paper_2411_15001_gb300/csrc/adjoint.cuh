@@ -14,6 +14,12 @@
 //    Jacobians of the Euler fluxes.
 // The forward state is read from a padded buffer with its ghost frame; the
 // cotangents are compact planes and the grid is periodic.
+//
+// Optionally (DA) the kernel also accumulates abar = dL/da^n, the cotangent of
+// the step's kinetic speed: a enters the Maxwellians (f / 2a), kappa = a (1 -
+// alpha) / 2 (u* and both bounds of theta) and dF = a (d_L - d_R). With a^n =
+// 2 lambda^n / (1 - alpha) and lambda^n the max over the cells of s^n (Sec. 4
+// preamble), k_lambda_* below hand abar on to the cell where the max is taken.
 #pragma once
 
 #include "common.cuh"
@@ -29,6 +35,7 @@ struct AdjArgs {
     const T *cot_in;       // cotangent of s^{n+1}: 20 compact planes
     T *cot_out;            // cotangent of s^n: 20 compact planes
     const StepConsts<T> *k;  // constants of the step (kinetic speed a^n as the forward run used it)
+    double *abar;          // DA: accumulates dL/da^n
 };
 
 // w^T df/du for the Euler x-flux (dir 0) or y-flux (dir 1) at state u.
@@ -54,9 +61,12 @@ __device__ __forceinline__ void flux_vjp(const T u[4], T gm1, int dir, const T w
 
 // Forward theta of a face (as combine_theta computes it) and its gradient with
 // respect to (u*, dF) on the active branch. Density bounds of the PP kind only.
+// *active: theta is one of the two bounds (not 1, not clamped), both of the form
+// kappa X - eps, so that d theta / d kappa = (theta + eps) / kappa at fixed (u*, dF).
 template <typename T, int LIM>
 __device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const StepConsts<T> &k,
-                                            T gus[4], T gdf[4]) {
+                                            T gus[4], T gdf[4], bool *active) {
+    *active = false;
 #pragma unroll
     for (int c = 0; c < 4; ++c) gus[c] = gdf[c] = T(0);
     if (LIM == VLBM_LIM_FIRST_ORDER) return T(0);
@@ -65,6 +75,7 @@ __device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const 
     unsigned int dummy = 0;
     const T th = combine_theta(tr, us, df, k, dummy);
     if (!(th > T(0)) || !(th < T(1))) return th;    // clamped: no gradient
+    *active = true;
     if (th == tr) {                                  // density bound active (Sec. 3.3.3)
         const T ad = fabs(df[0]);
         gus[0] = k.kappa / ad;
@@ -120,11 +131,9 @@ __device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const 
     return th;
 }
 
-template <typename T, int LIM>
-__global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= A.nx || j >= A.ny) return;
+// The transpose for cell (i, j); returns its part of dL/da^n (DA) or 0.
+template <typename T, int LIM, bool DA>
+__device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j) {
     const StepConsts<T> k = *A.k;
     CellLoad<T> L{A.fwd, A.plane, A.pitch};
     const long long N = (long long)A.nx * A.ny;
@@ -166,8 +175,9 @@ __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
         df[3][c] = face_dflux(d3C[c], d4N[c], k);
     }
     T th[4], gus[4][4], gdf[4][4];
+    bool act[4];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) th[f] = theta_and_grad<T, LIM>(us[f], df[f], k, gus[f], gdf[f]);
+    for (int f = 0; f < 4; ++f) th[f] = theta_and_grad<T, LIM>(us[f], df[f], k, gus[f], gdf[f], &act[f]);
     // ---------------------------------------------------------- cotangents (periodic)
     const int iw = i > 0 ? i - 1 : A.nx - 1, ie = i < A.nx - 1 ? i + 1 : 0;
     const int js = j > 0 ? j - 1 : A.ny - 1, jn = j < A.ny - 1 ? j + 1 : 0;
@@ -230,34 +240,168 @@ __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
     for (int c = 0; c < 4; ++c) out[c] += rx[c] + ry[c];
 #pragma unroll
     for (int q = 0; q < kNPlane; ++q) A.cot_out[q * N + cC] = out[q];
+    if constexpr (!DA) {
+        return 0.0;
+    } else {
+        // d/da of the face states: u* = (uL + uR)/2 - (fR - fL)/(2 kappa) with kappa ~ a,
+        // dF = a (dL - dR) with dM_{1,3}/da = -F/(2a^2), dM_{2,4}/da = +F/(2a^2)
+        const T ia = T(1) / k.a, h = k.inv2a * ia;
+        T dth[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) dth[f] = act[f] ? (th[f] + k.eps) * ia : T(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            dth[0] += gus[0][c] * (fC[c] - fW[c]) * k.inv2k * ia + gdf[0][c] * ((d1W[c] - d2C[c]) - (fW[c] + fC[c]) * k.inv2a);
+            dth[1] += gus[1][c] * (fE[c] - fC[c]) * k.inv2k * ia + gdf[1][c] * ((d1C[c] - d2E[c]) - (fC[c] + fE[c]) * k.inv2a);
+            dth[2] += gus[2][c] * (gC[c] - gS[c]) * k.inv2k * ia + gdf[2][c] * ((d3S[c] - d4C[c]) - (gS[c] + gC[c]) * k.inv2a);
+            dth[3] += gus[3][c] * (gN[c] - gC[c]) * k.inv2k * ia + gdf[3][c] * ((d3C[c] - d4N[c]) - (gC[c] + gN[c]) * k.inv2a);
+        }
+        double ab = 0.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            // outputs of this cell: the four pulled populations and u'
+            const T du1 = -(T(1) + th[0]) * fW[c] * h + d1W[c] * dth[0];
+            const T du2 = (T(1) + th[1]) * fE[c] * h + d2E[c] * dth[1];
+            const T du3 = -(T(1) + th[2]) * gS[c] * h + d3S[c] * dth[2];
+            const T du4 = (T(1) + th[3]) * gN[c] * h + d4N[c] * dth[3];
+            const T loc = dth[0] * d2C[c] + th[0] * fC[c] * h + dth[1] * d1C[c] - th[1] * fC[c] * h +
+                          dth[2] * d4C[c] + th[2] * gC[c] * h + dth[3] * d3C[c] - th[3] * gC[c] * h;
+            ab += (double)(cot(4 + c, cC) * du1 + cot(8 + c, cC) * du2 + cot(12 + c, cC) * du3 +
+                           cot(16 + c, cC) * du4) +
+                  (double)(ubC[c] * (du1 + du2 + du3 + du4 - loc));
+        }
+        return ab;
+    }
+}
+
+
+// Sum of v over the CTA's warps into *dst (every thread of the CTA calls it).
+__device__ __forceinline__ void warp_sum_atomic(double v, double *dst) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+}
+
+template <typename T, int LIM, bool DA>
+__global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    double abar = 0.0;
+    if (i < A.nx && j < A.ny) abar = adjoint_cell<T, LIM, DA>(A, i, j);
+    if constexpr (DA) warp_sum_atomic(abar, A.abar);   // blocks are 32 x 8: whole warps
 }
 
 // Cotangent of the initialisation u_k^0 = M_k(u_0) (Sec. 4 preamble) folded into
 // the conserved planes: ubar_0 = ubar^0 + sum_k (dM_k/du)^T pbar_k^0, with u_0
 // read from the padded initial state and a^0 held fixed.
+// With abar (not NULL), also the init map's part of dL/da^0: u_k^0 = M_k(u_0; a^0).
 template <typename T>
 __global__ void __launch_bounds__(256) k_adjoint_init(const T *init_state, long long plane, int pitch, int nx,
-                                                      int ny, const StepConsts<T> *kc, const T *cot, T *grad) {
+                                                      int ny, const StepConsts<T> *kc, const T *cot, T *grad,
+                                                      double *abar) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    double ab = 0.0;
+    if (i < nx && j < ny) {
+        const long long N = (long long)nx * ny, c = (long long)j * nx + i;
+        const T w = kc->w, inv2a = kc->inv2a, gm1 = kc->gm1;
+        const CellLoad<T> L{init_state, plane, pitch};
+        T u[4], wx[4], wy[4], rx[4], ry[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            u[q] = L.v(q, i, j);
+            const T p1 = cot[(4 + q) * N + c], p2 = cot[(8 + q) * N + c];
+            const T p3 = cot[(12 + q) * N + c], p4 = cot[(16 + q) * N + c];
+            grad[q * N + c] = cot[q * N + c] + w * (p1 + p2 + p3 + p4);
+            wx[q] = (p1 - p2) * inv2a;
+            wy[q] = (p3 - p4) * inv2a;
+        }
+        flux_vjp(u, gm1, 0, wx, rx);
+        flux_vjp(u, gm1, 1, wy, ry);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) grad[q * N + c] += rx[q] + ry[q];
+        if (abar) {   // dM_{1,3}/da = -F/(2a^2), dM_{2,4}/da = +F/(2a^2), F = f or g
+            T f[4], g[4];
+            euler_fluxes(u, gm1, f, g);
+            const T h = inv2a / kc->a;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const T p1 = cot[(4 + q) * N + c], p2 = cot[(8 + q) * N + c];
+                const T p3 = cot[(12 + q) * N + c], p4 = cot[(16 + q) * N + c];
+                ab -= (double)(((p1 - p2) * f[q] + (p3 - p4) * g[q]) * h);
+            }
+        }
+    }
+    if (abar) warp_sum_atomic(ab, abar);
+}
+
+// ------------------------------------------------ lambda^n and its argmax cell
+
+// Pass 1: *key = max over the cells of s (padded) of the ordered key of lambda,
+// computed as the forward run's monitors compute it.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lambda_max(const T *st, long long plane, int pitch, int nx, int ny, T gamma,
+                                                    unsigned long long *key) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    unsigned long long kk = 0ull;
+    if (i < nx && j < ny) {
+        const CellLoad<T> L{st, plane, pitch};
+        T u[4];
+        L.u4(0, i, j, u);
+        kk = ordered_key((double)cell_speed(u, gamma, gamma - T(1)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, kk, off);
+        kk = o > kk ? o : kk;
+    }
+    if ((threadIdx.x & 31) == 0 && kk) atomicMax(key, kk);
+}
+
+// Pass 2: *idx = the smallest cell index j nx + i whose lambda is the max (the
+// subgradient of the max taken at one of its cells).
+template <typename T>
+__global__ void __launch_bounds__(256) k_lambda_argmax(const T *st, long long plane, int pitch, int nx, int ny, T gamma,
+                                                       const unsigned long long *key, unsigned int *idx) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= nx || j >= ny) return;
-    const long long N = (long long)nx * ny, c = (long long)j * nx + i;
-    const T w = kc->w, inv2a = kc->inv2a, gm1 = kc->gm1;
-    const CellLoad<T> L{init_state, plane, pitch};
-    T u[4], wx[4], wy[4], rx[4], ry[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        u[q] = L.v(q, i, j);
-        const T p1 = cot[(4 + q) * N + c], p2 = cot[(8 + q) * N + c];
-        const T p3 = cot[(12 + q) * N + c], p4 = cot[(16 + q) * N + c];
-        grad[q * N + c] = cot[q * N + c] + w * (p1 + p2 + p3 + p4);
-        wx[q] = (p1 - p2) * inv2a;
-        wy[q] = (p3 - p4) * inv2a;
-    }
-    flux_vjp(u, gm1, 0, wx, rx);
-    flux_vjp(u, gm1, 1, wy, ry);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) grad[q * N + c] += rx[q] + ry[q];
+    const CellLoad<T> L{st, plane, pitch};
+    T u[4];
+    L.u4(0, i, j, u);
+    if (ordered_key((double)cell_speed(u, gamma, gamma - T(1))) == *key) atomicMin(idx, (unsigned)(j * nx + i));
+}
+
+// One thread: cot[q][idx] += abar * 2 / (1 - alpha) * d lambda / d u_q at the argmax
+// cell (lambda = |v| + sqrt(gamma p / rho)); then the slots are reset.
+template <typename T>
+__global__ void k_lambda_apply(const T *st, long long plane, int pitch, int nx, double gamma, double alpha,
+                               double *abar, unsigned long long *key, unsigned int *idx, T *cot, long long N) {
+    const unsigned int id = *idx;
+    const double ab = *abar;
+    *abar = 0.0;
+    *key = 0ull;
+    *idx = 0xffffffffu;
+    if (id == 0xffffffffu || ab == 0.0) return;
+    const int i = (int)(id % (unsigned)nx), j = (int)(id / (unsigned)nx);
+    const CellLoad<T> L{st, plane, pitch};
+    T ut[4];
+    L.u4(0, i, j, ut);
+    const double r = ut[0], m1 = ut[1], m2 = ut[2], E = ut[3];
+    const double v1 = m1 / r, v2 = m2 / r, s2 = v1 * v1 + v2 * v2, sp = sqrt(s2);
+    const double p = (gamma - 1.0) * (E - 0.5 * r * s2);
+    const double c = sqrt(gamma * p / r);
+    // |v|: d/dm_i = v_i / (|v| rho), d/drho = -|v| / rho (0 at rest: a subgradient)
+    double g[4] = {sp > 0.0 ? -sp / r : 0.0, sp > 0.0 ? v1 / (sp * r) : 0.0, sp > 0.0 ? v2 / (sp * r) : 0.0, 0.0};
+    // c = sqrt(gamma p / rho): dc = gamma / (2 c rho) (dp - p drho / rho)
+    const double kc = gamma / (2.0 * c * r);
+    const double dp[4] = {0.5 * (gamma - 1.0) * s2, -(gamma - 1.0) * v1, -(gamma - 1.0) * v2, gamma - 1.0};
+    g[0] += kc * (dp[0] - p / r);
+    for (int q = 1; q < 4; ++q) g[q] += kc * dp[q];
+    const double s = ab * 2.0 / (1.0 - alpha);
+    const long long cc = (long long)j * nx + i;
+    for (int q = 0; q < 4; ++q) cot[q * N + cc] += (T)(s * g[q]);
 }
 
 }  // namespace vlbm

@@ -38,6 +38,7 @@ struct vlbm_state {
     const void *roll_scratch;
     int64_t roll_steps;
     int32_t roll_every;
+    int adj_mode;       // VLBM_ADJOINT_HOLD_A or VLBM_ADJOINT_DIFF_A
     char err[256];
 };
 

@@ -17,6 +17,7 @@ OK, E_INVAL, E_CUDA, E_POSITIVITY, E_NONFINITE, E_TIMEOUT, E_UNSUPPORTED, E_NOME
 LIM_FIRST_ORDER, LIM_NONE, LIM_PP, LIM_LMP, LIM_RLMP = range(5)
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_DIRICHLET = range(4)
 FP64, FP32 = 0, 1
+ADJOINT_HOLD_A, ADJOINT_DIFF_A = 0, 1
 KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_FUSED = range(3)
 
 LIMITERS = {"first": LIM_FIRST_ORDER, "none": LIM_NONE, "pp": LIM_PP, "lmp": LIM_LMP, "rlmp": LIM_RLMP}
@@ -129,6 +130,7 @@ _SIGS = {
     "vlbm_adjoint_scratch_bytes": (_SZ, [_P, _I64, _I32]),
     "vlbm_rollout": (ctypes.c_int, [_P, _I64, _I32, _P, _SZ]),
     "vlbm_adjoint": (ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _P, _SZ]),
+    "vlbm_adjoint_set_mode": (ctypes.c_int, [_P, _I32]),
     "vlbm_batch_workspace_bytes": (_SZ, [_I32, ctypes.POINTER(vlbm_grid), _I32]),
     "vlbm_batch_init": (ctypes.c_int, [_I32, ctypes.POINTER(vlbm_grid), _D, _I32, _I32,
                                        ctypes.POINTER(vlbm_opts), _P, _SZ, _P, ctypes.POINTER(_P)]),
@@ -238,6 +240,10 @@ def vlbm_adjoint_scratch_bytes(s, nsteps: int, ckpt_every: int) -> int:
 
 def vlbm_rollout(s, nsteps: int, ckpt_every: int, d_scratch, scratch_bytes: int) -> int:
     return _lib.vlbm_rollout(s, nsteps, ckpt_every, d_scratch, scratch_bytes)
+
+
+def vlbm_adjoint_set_mode(s, mode: int) -> int:
+    return _lib.vlbm_adjoint_set_mode(s, mode)
 
 
 def vlbm_adjoint(s, d_u0, nsteps: int, ckpt_every: int, d_dLduN, d_dLdu0, d_scratch, scratch_bytes: int) -> int:
@@ -440,6 +446,11 @@ class VLBM:
         _check(vlbm_rollout(self._s, int(nsteps), int(ckpt_every), scratch.data_ptr(), scratch.numel()),
                self._s)
 
+    def set_adjoint_mode(self, mode: int):
+        """ADJOINT_HOLD_A (default) or ADJOINT_DIFF_A: whether the adjoint differentiates
+        the dynamic kinetic speed a^n = 2 max lambda / (1 - alpha)."""
+        _check(vlbm_adjoint_set_mode(self._s, int(mode)), self._s)
+
     def adjoint(self, dLduN, nsteps: int, ckpt_every: int, scratch, u0=None):
         """dL/du_0 (4, ny, nx) from dL/du^N (4, ny, nx): planes rho, m1, m2, E.
 
@@ -565,7 +576,8 @@ def _rollout_function():
 
         forward(rho, mom, E, solver, nsteps, ckpt_every) -> (rho^N, mom^N, E^N); the
         backward pass is the library's adjoint (vlbm_adjoint) over the checkpoints
-        the forward pass stored. a^n is held as the forward run produced it."""
+        the forward pass stored; a dynamic a^n is held or differentiated as the
+        solver's set_adjoint_mode says."""
 
         @staticmethod
         def forward(ctx, rho, mom, E, solver, nsteps, ckpt_every):

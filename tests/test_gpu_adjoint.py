@@ -338,3 +338,54 @@ def test_adjoint_rejects_unsupported():
     with pytest.raises(V.VLBMError):             # rollout must start at n = 0
         s.rollout(4, 2, s.adjoint_scratch(4, 2))
     s.close()
+
+
+@pytest.mark.parametrize("kernel", [V.KERNEL_SIMPLE, V.KERNEL_FUSED])
+@pytest.mark.parametrize("limiter", [V.LIM_NONE, V.LIM_PP])
+def test_adjoint_dynamic_speed_matches_autograd(limiter, kernel):
+    """ADJOINT_DIFF_A: the dynamic a^n = 4 lambda(s^n) differentiated through the max
+    (its argmax cell), against autograd of the PyTorch restatement (FP64), and
+    different from the gradient that holds a^n."""
+    cons, dx = _bumps(32)
+    nsteps, every = 24, 7
+    p = W.Problem("bumps", 32, 32, dx, 0.0, 0.0, cons[0], cons[1], cons[2], cons[3])
+    w, tgt = _setup(p, 0.0)
+    s = _solver(p, limiter, V.FP64, 0.0, kernel)
+    u0 = torch.tensor(cons, dtype=torch.float64, device=DEV)
+    _, g_hold = _adjoint(s, u0, nsteps, every, w, tgt)
+    s.set_adjoint_mode(V.ADJOINT_DIFF_A)
+    uN, g = _adjoint(s, u0, nsteps, every, w, tgt)
+    assert s.monitors()["status"] == 0
+    s.close()
+    x = torch.tensor(cons, dtype=torch.float64, requires_grad=True)
+    sN = TR.rollout_dynamic(x, nsteps, limiter)
+    assert np.abs(sN[:4].detach().numpy() - uN.cpu().numpy()).max() <= 1e-12 * np.abs(cons).max()
+    (0.5 * (w.cpu() * (sN[:4] - tgt.cpu()) ** 2).sum()).backward()
+    g_ref = x.grad.numpy()
+    err = np.abs(g.cpu().numpy() - g_ref)
+    assert err.max() <= 1e-9 * np.abs(g_ref).max(), (err.max(), np.unravel_index(err.argmax(), err.shape))
+    assert np.abs(g_hold.cpu().numpy() - g_ref).max() > 1e-6 * np.abs(g_ref).max()
+
+
+def test_adjoint_dynamic_speed_fp32_close_to_fp64():
+    cons, dx = _bumps(32)
+    p = W.Problem("bumps", 32, 32, dx, 0.0, 0.0, cons[0], cons[1], cons[2], cons[3])
+    w, tgt = _setup(p, 0.0)
+    gs = {}
+    for prec, dt in ((V.FP64, torch.float64), (V.FP32, torch.float32)):
+        s = _solver(p, V.LIM_PP, prec, 0.0, V.KERNEL_FUSED)
+        s.set_adjoint_mode(V.ADJOINT_DIFF_A)
+        u0 = torch.tensor(cons, dtype=dt, device=DEV)
+        _, gs[prec] = _adjoint(s, u0, 20, 6, w, tgt)
+        s.close()
+    ref = gs[V.FP64].cpu().numpy()
+    assert np.abs(gs[V.FP32].cpu().numpy() - ref).max() <= 5e-3 * np.abs(ref).max()
+
+
+def test_adjoint_mode_is_checked():
+    cons, dx = _bumps(16)
+    p = W.Problem("bumps", 16, 16, dx, 0.0, 0.0, cons[0], cons[1], cons[2], cons[3])
+    s = _solver(p, V.LIM_PP, V.FP64, 0.0)
+    with pytest.raises(V.VLBMError):
+        s.set_adjoint_mode(7)
+    s.close()

@@ -57,3 +57,38 @@ def test_autograd_matches_oracle_differences():
         B = O.run(cfg, dn, p.dx, nsteps=15, lam_fixed=lam)["state"][:4]
         fd = 0.5 * float((w * (A - B) * (A + B)).sum()) / (2 * h)
         assert abs(fd - g[c, j, i]) <= 1e-6 * abs(g[c, j, i]), (j, i, c, fd, g[c, j, i])
+
+
+def test_dynamic_speed_rollout_matches_oracle_and_its_differences():
+    """The dynamic kinetic speed a^n = 4 lambda(s^n): the forward map equals the
+    oracle's dynamic run, and autograd through the max equals central differences
+    of the oracle's run (smooth data, a unique argmax that stays put within h)."""
+    p = W.vortex_with_bumps(20)
+    cfg = O.Config(20, 20, (0, 0, 0, 0), O.LIM_PP, 1.4, 0.5, 1e-16)
+    nsteps = 8
+    ref = O.run(cfg, p.conserved(), p.dx, nsteps=nsteps)["state"]
+    u0 = torch.tensor(p.conserved(), requires_grad=True)
+    sN = TR.rollout_dynamic(u0, nsteps, O.LIM_PP)
+    assert np.abs(sN.detach().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+    rng = np.random.default_rng(4)
+    w = rng.uniform(0.5, 1.5, size=(4, 20, 20))
+    (torch.tensor(w) * sN[:4]).sum().backward()
+    g = u0.grad.numpy()
+    # the gradient of the max reaches the state: holding a^n fixed gives another gradient
+    a_seq = O.run(cfg, p.conserved(), p.dx, nsteps=nsteps)["a"]
+    u0h = torch.tensor(p.conserved(), requires_grad=True)
+    s = TR.init_populations(u0h, a_seq[0], 0.5, 1.4)
+    for a in a_seq:
+        s = TR.step(s, a, O.LIM_PP)
+    (torch.tensor(w) * s[:4]).sum().backward()
+    assert np.abs(u0h.grad.numpy() - g).max() > 1e-6 * np.abs(g).max()
+    for k in range(6):
+        d = rng.standard_normal((4, 20, 20)) * np.abs(p.conserved()) * 1e-2
+        h = 1e-4
+
+        def L(x):
+            return float((w * O.run(cfg, p.conserved() + x * d, p.dx, nsteps=nsteps)["state"][:4]).sum())
+
+        fd = (4.0 * (L(h) - L(-h)) / (2 * h) - (L(2 * h) - L(-2 * h)) / (4 * h)) / 3.0
+        ad = float((g * d).sum())
+        assert abs(fd - ad) <= 1e-7 * abs(ad), (k, fd, ad)

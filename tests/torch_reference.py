@@ -107,3 +107,23 @@ def rollout(u0, nsteps, a, limiter, alpha=0.5, gamma=1.4, eps=1e-16):
     for _ in range(nsteps):
         s = step(s, a, limiter, alpha, gamma, eps)
     return s
+
+
+def speed_max(u, gamma):
+    """lambda = max over the cells of |v| + sqrt(gamma p / rho), differentiable (the
+    gradient of a max goes to the cell where it is reached)."""
+    r = u[0]
+    v1, v2 = u[1] / r, u[2] / r
+    p = (gamma - 1.0) * (u[3] - 0.5 * r * (v1 * v1 + v2 * v2))
+    return (torch.sqrt(v1 * v1 + v2 * v2) + torch.sqrt(gamma * p / r)).max()
+
+
+def rollout_dynamic(u0, nsteps, limiter, alpha=0.5, gamma=1.4, eps=1e-16):
+    """As rollout, with the dynamic kinetic speed of Sec. 4: a^n = 2 lambda(s^n) / (1 - alpha)
+    before every step (a^0 from u_0, which also sets the initial populations)."""
+    a = 2.0 * speed_max(u0, gamma) / (1.0 - alpha)
+    s = init_populations(u0, a, alpha, gamma)
+    for _ in range(nsteps):
+        s = step(s, a, limiter, alpha, gamma, eps)
+        a = 2.0 * speed_max(s[0:4], gamma) / (1.0 - alpha)
+    return s
