@@ -84,6 +84,14 @@ static cudaError_t ghosts(vlbm_state *s) {
     return launch_ghosts<float>(args_of<float>(s), s->stream);
 }
 
+// Before a row-marching step of a grid with a prescribed part: its ghosts at the
+// step's t^n and a^n (the kernel writes every other ghost itself).
+static cudaError_t dirichlet_pass(vlbm_state *s) {
+    if (!use_fused(s) || !s->bd.has_dir) return cudaSuccess;
+    if (s->precision == VLBM_FP64) return launch_dirichlet_ghosts<double>(args_of<double>(s), s->stream);
+    return launch_dirichlet_ghosts<float>(args_of<float>(s), s->stream);
+}
+
 // Descriptor of this grid for the row-marching kernel, built on the host.
 template <typename T>
 static void build_desc(vlbm_state *s) {
@@ -136,12 +144,14 @@ cudaError_t vlbm::api::step_once(vlbm_state *s) {
                 s->ev.push_back(e);
             }
         }
-        r = cudaEventRecord(s->ev[s->ev_used], s->stream);
+        r = dirichlet_pass(s);
+        if (r == cudaSuccess) r = cudaEventRecord(s->ev[s->ev_used], s->stream);
         if (r == cudaSuccess) r = step_kernel_only(s);
         if (r == cudaSuccess) r = cudaEventRecord(s->ev[s->ev_used + 1], s->stream);
         s->ev_used += 2;
     } else {
-        r = step_kernel_only(s);
+        r = dirichlet_pass(s);
+        if (r == cudaSuccess) r = step_kernel_only(s);
     }
     if (r != cudaSuccess) return r;
     return use_fused(s) ? cudaSuccess : ghosts(s);   // the fused kernel writes the ghost frame
@@ -195,6 +205,12 @@ static cudaError_t build_graph(vlbm_state *s) {
     void *pa[] = {&A};
     cudaKernelNodeParams kg;
     memset(&kg, 0, sizeof kg);
+    const bool dir = fused && s->bd.has_dir;   // prescribed ghosts before each fused step
+    if (dir) {
+        kg.func = const_cast<void *>(dirichlet_ghosts_kernel_fn<T>());
+        ghosts_launch_shape(s->grid.nx, s->grid.ny, &kg.gridDim, &kg.blockDim);
+        kg.kernelParams = pa;
+    }
     if (fused) {
         size_t smem = 0;
         kp.func = const_cast<void *>(fused_kernel_fn<T>(s->limiter, &smem));
@@ -213,6 +229,11 @@ static cudaError_t build_graph(vlbm_state *s) {
     cudaGraphNode_t prev = nullptr;
     for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
         cudaGraphNode_t node;
+        if (dir) {
+            e = cudaGraphAddKernelNode(&node, s->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kg);
+            prev = node;
+            if (e != cudaSuccess) break;
+        }
         e = cudaGraphAddKernelNode(&node, s->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
         prev = node;
         if (e == cudaSuccess && !fused) {

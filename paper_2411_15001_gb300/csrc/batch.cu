@@ -208,6 +208,12 @@ static cudaError_t launch_steps(vlbm_batch *b, int64_t nsteps) {
     if (e != cudaSuccess) return e;
     FusedBatchArgs<T> B = batch_args<T>(b);
     const int ctas = grid_ctas(b);
+    // grids with a prescribed part get their Dirichlet ghosts before every step
+    std::vector<StepArgs<T>> dir;
+    for (int i = 0; i < b->n; ++i)
+        if (b->bds[i].has_dir) dir.push_back(inst_args<T>(b, i));
+    std::vector<void *> dparams(dir.size());
+    for (size_t q = 0; q < dir.size(); ++q) dparams[q] = &dir[q];
     if (nsteps >= kGraphSteps && !b->gexec) {
         size_t smem = 0;
         const void *fn = fused_kernel_fn<T>(b->limiter, &smem);
@@ -224,6 +230,16 @@ static cudaError_t launch_steps(vlbm_batch *b, int64_t nsteps) {
         cudaGraphNode_t prev = nullptr;
         for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
             cudaGraphNode_t node;
+            for (size_t q = 0; q < dir.size() && e == cudaSuccess; ++q) {
+                cudaKernelNodeParams kd;
+                memset(&kd, 0, sizeof kd);
+                kd.func = const_cast<void *>(dirichlet_ghosts_kernel_fn<T>());
+                ghosts_launch_shape(dir[q].nx, dir[q].ny, &kd.gridDim, &kd.blockDim);
+                kd.kernelParams = &dparams[q];
+                e = cudaGraphAddKernelNode(&node, b->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kd);
+                prev = node;
+            }
+            if (e != cudaSuccess) break;
             e = cudaGraphAddKernelNode(&node, b->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
             prev = node;
         }
@@ -240,7 +256,8 @@ static cudaError_t launch_steps(vlbm_batch *b, int64_t nsteps) {
         left -= kGraphSteps;
     }
     for (; left > 0; --left) {
-        e = launch_step_fused<T>(B, b->limiter, ctas, b->stream);
+        for (size_t q = 0; q < dir.size() && e == cudaSuccess; ++q) e = launch_dirichlet_ghosts<T>(dir[q], b->stream);
+        if (e == cudaSuccess) e = launch_step_fused<T>(B, b->limiter, ctas, b->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

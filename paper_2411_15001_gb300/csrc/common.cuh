@@ -315,6 +315,58 @@ __device__ __noinline__ GhostState<T> dirichlet_ghost(const Bound *B, int nx, in
     return g;
 }
 
+// Ghost index of thread t of a ghost pass: the 2 x (nx + 4) cells of the top and
+// bottom layers first, then the 2 x ny of the left and right ones.
+template <typename T>
+__device__ __forceinline__ bool ghost_of_thread(const StepArgs<T> &A, long long t, int *gi, int *gj) {
+    const int nx = A.nx, ny = A.ny;
+    const long long rowpart = 4ll * (nx + 4);
+    if (t >= rowpart + 4ll * ny) return false;
+    if (t < rowpart) {
+        const int r = (int)(t / (nx + 4));
+        *gi = (int)(t % (nx + 4)) - 2;
+        *gj = r < 2 ? r - 2 : ny + (r - 2);
+    } else {
+        const long long q = t - rowpart;
+        const int c = (int)(q / ny);
+        *gj = (int)(q % ny);
+        *gi = c < 2 ? c - 2 : nx + (c - 2);
+    }
+    return true;
+}
+
+// If the boundary prescribes ghost (gi, gj), write its state and Maxwellians at the
+// kinetic speed of the control block's next step into buf; true if it did.
+template <typename T>
+__device__ __forceinline__ bool write_dirichlet_ghost(const StepArgs<T> &A, T *buf, int gi, int gj) {
+    const GhostState<T> gs = dirichlet_ghost<T>(&A.bd, A.nx, A.ny, gi, gj);
+    if (!gs.hit) return false;
+    const StepConsts<T> k = consts_of<T>(A.ctl);
+    T f[4], g[4], M1[4], M2[4], M3[4], M4[4];
+    euler_fluxes(gs.u, k.gm1, f, g);
+    maxwell_pm(gs.u, f, k, M1, M2);
+    maxwell_pm(gs.u, g, k, M3, M4);
+    const long long dst = cidx(A, gi, gj);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        buf[q * A.plane + dst] = gs.u[q];
+        buf[(4 + q) * A.plane + dst] = M1[q];
+        buf[(8 + q) * A.plane + dst] = M2[q];
+        buf[(12 + q) * A.plane + dst] = M3[q];
+        buf[(16 + q) * A.plane + dst] = M4[q];
+    }
+    return true;
+}
+
+// The prescribed ghosts alone, in buffer (n & 1), before a step of the row-marching
+// kernel (which writes every other ghost as an image of the cells it updates).
+template <typename T>
+__global__ void k_dirichlet_ghosts(StepArgs<T> A) {
+    int gi, gj;
+    if (!ghost_of_thread(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, &gi, &gj)) return;
+    write_dirichlet_ghost(A, (A.ctl->n & 1) ? A.buf1 : A.buf0, gi, gj);
+}
+
 // Fill the two ghost layers of buffer (n & 1): periodic wrap, zero-gradient copy
 // of u and u_1..u_4, or the mirror image (normal momentum negated in u and all
 // populations, u_1 <-> u_2 across an x-wall, u_3 <-> u_4 across a y-wall); a
@@ -323,42 +375,10 @@ __device__ __noinline__ GhostState<T> dirichlet_ghost(const Bound *B, int nx, in
 template <typename T>
 __global__ void k_ghosts(StepArgs<T> A) {
     const int nx = A.nx, ny = A.ny;
-    const long long rowpart = 4ll * (nx + 4);
-    const long long total = rowpart + 4ll * ny;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
     int gi, gj;
-    if (t < rowpart) {
-        const int r = (int)(t / (nx + 4));
-        gi = (int)(t % (nx + 4)) - 2;
-        gj = r < 2 ? r - 2 : ny + (r - 2);
-    } else {
-        const long long q = t - rowpart;
-        const int c = (int)(q / ny);
-        gj = (int)(q % ny);
-        gi = c < 2 ? c - 2 : nx + (c - 2);
-    }
+    if (!ghost_of_thread(A, (long long)blockIdx.x * blockDim.x + threadIdx.x, &gi, &gj)) return;
     T *buf = (A.ctl->n & 1) ? A.buf1 : A.buf0;
-    if (A.bd.has_dir) {
-        const GhostState<T> gs = dirichlet_ghost<T>(&A.bd, nx, ny, gi, gj);
-        if (gs.hit) {
-            const StepConsts<T> k = consts_of<T>(A.ctl);
-            T f[4], g[4], M1[4], M2[4], M3[4], M4[4];
-            euler_fluxes(gs.u, k.gm1, f, g);
-            maxwell_pm(gs.u, f, k, M1, M2);
-            maxwell_pm(gs.u, g, k, M3, M4);
-            const long long dst = cidx(A, gi, gj);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                buf[q * A.plane + dst] = gs.u[q];
-                buf[(4 + q) * A.plane + dst] = M1[q];
-                buf[(8 + q) * A.plane + dst] = M2[q];
-                buf[(12 + q) * A.plane + dst] = M3[q];
-                buf[(16 + q) * A.plane + dst] = M4[q];
-            }
-            return;
-        }
-    }
+    if (A.bd.has_dir && write_dirichlet_ghost(A, buf, gi, gj)) return;
     // source cell: the y rule (type at column gi) applied to the x rule (type at the
     // source row); uniform sides skip the look-up
     bool mx = false, my = false;

@@ -20,6 +20,19 @@ cudaError_t launch_ghosts<VLBM_T>(const StepArgs<VLBM_T> &A, cudaStream_t s) {
 }
 
 template <>
+cudaError_t launch_dirichlet_ghosts<VLBM_T>(const StepArgs<VLBM_T> &A, cudaStream_t s) {
+    dim3 grd, blk;
+    ghosts_launch_shape(A.nx, A.ny, &grd, &blk);
+    k_dirichlet_ghosts<VLBM_T><<<grd, blk, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <>
+const void *dirichlet_ghosts_kernel_fn<VLBM_T>() {
+    return (const void *)k_dirichlet_ghosts<VLBM_T>;
+}
+
+template <>
 cudaError_t launch_init<VLBM_T>(const StepArgs<VLBM_T> &A, const VLBM_T *rho, const VLBM_T *mom,
                                 const VLBM_T *E, cudaStream_t s) {
     const dim3 blk(kBX, kBY), grd = cell_grid(A.nx, A.ny);

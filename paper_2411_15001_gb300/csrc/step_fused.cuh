@@ -186,20 +186,6 @@ struct FusedCtx {
         T u[4], f[4], g[4], M1[4], M2[4], M3[4], M4[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) u[q] = S.raw[slot][q][b];
-        // a prescribed ghost (Dirichlet part of the boundary): the field's state with
-        // its populations at equilibrium, i.e. d_k = 0
-        bool dg = false;
-        if ((unsigned)c >= (unsigned)D.nx || (unsigned)R >= (unsigned)D.ny) {
-            const Bound *bd = &desc()->bd;
-            if (bd->has_dir) {
-                const GhostState<T> gs = dirichlet_ghost<T>(bd, D.nx, D.ny, c, R);
-                if (gs.hit) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) u[q] = gs.u[q];
-                    dg = true;
-                }
-            }
-        }
         euler_fluxes(u, k.gm1, f, g);
         maxwell_pm(u, f, k, M1, M2);
         maxwell_pm(u, g, k, M3, M4);
@@ -216,13 +202,6 @@ struct FusedCtx {
             S.X[xs][4 + q][b] = f[q];
             S.X[xs][8 + q][b] = d1;
             S.X[xs][12 + q][b] = d2;
-        }
-        if (dg) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                S.X[xs][8 + q][b] = S.X[xs][12 + q][b] = T(0);
-                h0.d3[q] = h0.d4[q] = T(0);
-            }
         }
         const T rsy_new = face_star(h1.u[0], h1.g[0], u[0], g[0], k);  // y-face R - 1/2
         __syncthreads();                                                  // S1

@@ -224,6 +224,9 @@ cudaError_t launch_ctl_reset(DevCtl *ctl, double dx, double alpha, double a_fixe
 template <typename T> cudaError_t launch_init(const StepArgs<T> &a, const T *rho, const T *mom,
                                               const T *E, cudaStream_t s);
 template <typename T> cudaError_t launch_ghosts(const StepArgs<T> &a, cudaStream_t s);
+// The prescribed (Dirichlet) ghosts alone, before a row-marching step (shape as the ghost pass).
+template <typename T> cudaError_t launch_dirichlet_ghosts(const StepArgs<T> &a, cudaStream_t s);
+template <typename T> const void *dirichlet_ghosts_kernel_fn();
 template <typename T> cudaError_t launch_step_simple(const StepArgs<T> &a, cudaStream_t s);
 // Row-marching kernel over the work items of one or more grids, `grid` persistent CTAs.
 template <typename T> cudaError_t launch_step_fused(const FusedBatchArgs<T> &a, int limiter, int grid,
