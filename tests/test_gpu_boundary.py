@@ -159,17 +159,21 @@ R = 4
 
 
 def _sampled_step(s, p, lim, cells, tol=1e-4):
-    """One more GPU step checked on 9 x 9 interior patches against the oracle."""
+    """One more GPU step checked on 9 x 9 interior patches against the oracle, each
+    plane's error relative to its largest magnitude in the patch, or 1e-3 of its
+    largest in the grid where that is bigger (the momentum of gas at rest is
+    rounding noise, no scale)."""
     before = s.state_planes().cpu().numpy()
     a = s.monitors()["a"]
     s.step(1)
     after = s.state_planes().cpu().numpy()
     n = 2 * R + 1
     cfg = O.Config(n, n, (1, 1, 1, 1), lim, p.gamma, 0.5, 1e-16)
+    floor = 1e-3 * np.abs(before).reshape(20, -1).max(axis=1).astype(np.float64)
     for (j, i) in cells:
         patch = np.ascontiguousarray(before[:, j - R:j + R + 1, i - R:i + R + 1], dtype=np.float64)
         ref = O.step(cfg, patch, a)[:, R, R]
-        scale = np.abs(patch).reshape(20, -1).max(axis=1)
+        scale = np.maximum(np.abs(patch).reshape(20, -1).max(axis=1), floor)
         err = float((np.abs(after[:, j, i] - ref) / np.maximum(scale, 1e-300)).max())
         assert err <= tol, (j, i, err)
 
@@ -198,11 +202,13 @@ def test_double_mach_reflection_paper_grid(lim):
     s.close()
 
 
-@pytest.mark.parametrize("mach,prec", [(80, V.FP32), (2000, V.FP64)])
-def test_jets_paper_grid(mach, prec):
-    """800 x 400 to the paper's final time, RLMP, every step admissible (the Mach 2000
-    jet in FP64: its internal energy is 3e-7 of the kinetic energy, below what a
-    float state resolves)."""
+@pytest.mark.parametrize("mach", [80, 2000])
+def test_jets_paper_grid(mach):
+    """800 x 400 to the paper's final time, RLMP, FP64, every step admissible. A float
+    state cannot hold these jets: their internal energy is 3e-4 (Mach 80) and 3e-7
+    (Mach 2000) of the total, and in FP32 rounding drives E - |m|^2 / (2 rho) below 0
+    within a few hundred steps (measured at the Mach 80 jet: by step 155-438)."""
+    prec = V.FP64
     p = W.astro_jet(400, mach=mach)
     s = _solver(p, V.LIM_RLMP, prec)
     s.step_to(p.meta["t_end"], 10 ** 6)
