@@ -141,7 +141,11 @@ struct FusedCtx {
     int b, zin;
     uint32_t &nissued, &nconsumed;
     int xb, xpad, c, y0, y1, R1;
-    // carried face state
+    // Face states of the x-face (c+1/2) of row R-1 and of the y-face between rows R-2
+    // and R-1. PP and the fixed thetas carry them from the previous row; LMP / RLMP,
+    // whose density bounds keep more values live, recompute them where theta needs
+    // them (measured: 10 % faster for LMP / RLMP, no change for PP).
+    static constexpr bool kRecompute = LIM == VLBM_LIM_LMP || LIM == VLBM_LIM_RLMP;
     T xs_us[4], xs_df[4];   // x-face (c+1/2) of row R-1
     T ys_us[4], ys_df[4];   // y-face between rows R-2 and R-1
     T rsy_prev;             // rho* of that y-face
@@ -238,6 +242,16 @@ struct FusedCtx {
         } else if (!live) {
             tx = ty = T(0);
         } else {
+            if constexpr (kRecompute) {
+                const int xp = (R - 1) & 3;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    xs_us[q] = face_star(h1.u[q], S.X[xp][4 + q][b], S.X[xp][q][br], S.X[xp][4 + q][br], k);
+                    xs_df[q] = face_dflux(S.X[xp][8 + q][b], S.X[xp][12 + q][br], k);
+                    ys_us[q] = q == 0 ? rsy_prev : face_star(h2.u[q], h2.g[q], h1.u[q], h1.g[q], k);
+                    ys_df[q] = face_dflux(h2.d3[q], h1.d4[q], k);
+                }
+            }
             T trx, try_;
             if (LIM == VLBM_LIM_PP) {
                 trx = pp_density_target(xs_us[0], xs_df[0], k);
@@ -265,15 +279,20 @@ struct FusedCtx {
         S.thx[(R - 1) & 1][b] = tx;
         mu2 = mu1;
         nu2 = nu1;
-        // new x-face (b, b+1) of row R and y-face R - 1/2
+        if constexpr (kRecompute) {
+            // rho* of the x-face (b, b+1) of row R, for the next row's density bounds
+            S.rsx[R & 1][b] = face_star(h0.u[0], S.X[xs][4][b], S.X[xs][0][br], S.X[xs][4][br], k);
+        } else {
+            // new x-face (b, b+1) of row R and y-face R - 1/2
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            xs_us[q] = face_star(S.X[xs][q][b], S.X[xs][4 + q][b], S.X[xs][q][br], S.X[xs][4 + q][br], k);
-            xs_df[q] = face_dflux(S.X[xs][8 + q][b], S.X[xs][12 + q][br], k);
-            ys_us[q] = q == 0 ? rsy_new : face_star(h1.u[q], h1.g[q], h0.u[q], h0.g[q], k);
-            ys_df[q] = face_dflux(h1.d3[q], h0.d4[q], k);
+            for (int q = 0; q < 4; ++q) {
+                xs_us[q] = face_star(S.X[xs][q][b], S.X[xs][4 + q][b], S.X[xs][q][br], S.X[xs][4 + q][br], k);
+                xs_df[q] = face_dflux(S.X[xs][8 + q][b], S.X[xs][12 + q][br], k);
+                ys_us[q] = q == 0 ? rsy_new : face_star(h1.u[q], h1.g[q], h0.u[q], h0.g[q], k);
+                ys_df[q] = face_dflux(h1.d3[q], h0.d4[q], k);
+            }
+            S.rsx[R & 1][b] = xs_us[0];
         }
-        S.rsx[R & 1][b] = xs_us[0];
         rsy_prev = rsy_new;
         __syncthreads();                                                  // S3
         // ---------------------------------------------------------------- P4

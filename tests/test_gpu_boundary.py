@@ -198,7 +198,9 @@ def test_double_mach_reflection_paper_grid(lim):
     m = s.monitors()
     assert m["status"] == 0 and m["first_bad_step"] == -1
     before = s.state_planes().cpu().numpy()
-    _sampled_step(s, p, lim, _cells(before, 60, 3))
+    # LMP's theta_rho jumps where dF^rho changes sign: on the Mach stem a float and a
+    # double evaluation of the same face can land on either side (measured 4.2e-4)
+    _sampled_step(s, p, lim, _cells(before, 60, 3), tol=1e-3 if lim == V.LIM_LMP else 1e-4)
     s.close()
 
 
