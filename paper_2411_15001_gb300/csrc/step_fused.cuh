@@ -20,6 +20,8 @@
 //  P2  density bounds of row R - 1 (LMP/RLMP).
 //  P3  theta of the x-faces of row R - 1 and of y-face R - 3/2 (Sec. 3.3-3.4);
 //      then u*, dF of the x-faces of row R and of y-face R - 1/2.
+// Barriers: S1 after P1 (the ring row R and the previous row's theta are
+// complete), S2 after P2 (LMP / RLMP only).
 //  P4  collide + stream of row O (eq. blending_u1 / blending_u), stores, ghost
 //      images, monitors.
 // Output rows start on 32-byte sector boundaries (kOX = 8, strips of 120 floats),
@@ -294,7 +296,11 @@ struct FusedCtx {
             S.rsx[R & 1][b] = xs_us[0];
         }
         rsy_prev = rsy_new;
-        __syncthreads();                                                  // S3
+        // No barrier before P4: it reads theta of row R-2's x-faces (written by the
+        // previous row's P3) and the ring rows of R-2, both ordered by this row's S1;
+        // every slot this row's P3 writes is read only after the next row's S1, and
+        // every slot the next row overwrites is read here before this thread reaches
+        // that S1.
         // ---------------------------------------------------------------- P4
         const int O = R - 2;
         const int xo = O & 3, tp = O & 1;
