@@ -61,18 +61,21 @@ def _kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic():
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+def _ncu_summary():
+    """The committed ncu summary of the step kernel, if it was taken on the current
+    kernel sources; else {}."""
     path = os.path.join(ROOT, "profiles", "step_fused_blast.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except OSError:
-        return None
-    if d.get("kernel_hash") != _kernel_hash():
-        return None
-    return d.get("dram_bytes_per_launch_full_size")
+        return {}
+    return d if d.get("kernel_hash") == _kernel_hash() else {}
+
+
+def _ncu_traffic():
+    """DRAM bytes per launch of the step kernel (full size), or None."""
+    return _ncu_summary().get("dram_bytes_per_launch_full_size")
 
 
 class ClockSampler:
@@ -305,6 +308,10 @@ def run_ours(args):
             "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": _ncu_traffic(),
             "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})",
             "kernel": "k_step_fused<float, PP>", "kernel_ms_avg": kernel_ms / launches if launches else None}
+    nsum = _ncu_summary()
+    if nsum:   # ncu figures of the same kernel (profiles/): DRAM bytes per cell update, FP64 share
+        roof["dram_bytes_per_lu"] = nsum["dram_bytes_per_launch_full_size"] / (N_SIDE * N_SIDE)
+        roof["fp64_pipe_pct"] = nsum.get("fp64_pipe_pct")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,

@@ -112,3 +112,26 @@ def test_batch_grids_sampled():
                  if min(j, k) > 7 and j < probs[i].ny - 8 and k < probs[i].nx - 8]
         _check_samples(before[i], after, cells, a[i], O.LIM_PP, probs[i].gamma, 1e-13)
     b.close()
+
+
+def test_quadrant_1024_lmp_to_final_time():
+    """The 1024^2 quadrant problem with LMP run to t = 0.25 as specified (last step
+    shortened to land on it): FP32 with the row-marching kernel against the FP64
+    path, which is the oracle's run bit for bit on every smaller case: same number
+    of steps, every step admissible, density within L1 1e-3."""
+    p = W.quadrant_riemann(1024, seed=0)
+    out = {}
+    for prec, dt, kern in ((V.FP32, torch.float32, V.KERNEL_FUSED), (V.FP64, torch.float64, V.KERNEL_SIMPLE)):
+        s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, limiter=V.LIM_LMP, precision=prec, kernel=kern, device="cuda:0")
+        c = torch.tensor(p.conserved(), dtype=dt, device="cuda:0")
+        s.set_conserved(c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+        s.step_to(0.25, 10 ** 6)
+        m = s.monitors()
+        assert m["status"] == 0 and m["first_bad_step"] == -1 and m["done"] == 1
+        assert abs(m["t"] - 0.25) <= 1e-12
+        out[prec] = (s.state_planes().double().cpu().numpy(), m["n"])
+        s.close()
+    (u32, n32), (u64, n64) = out[V.FP32], out[V.FP64]
+    assert abs(n32 - n64) <= 2
+    err = float(np.abs(u32[0] - u64[0]).sum() / np.abs(u64[0]).sum())
+    assert err <= 1e-3, err
