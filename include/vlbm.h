@@ -318,8 +318,12 @@ VLBM_API const char *vlbm_batch_last_error(const vlbm_batch *b);
  * the forward run produced them (VLBM_ADJOINT_HOLD_A, the default) or
  * differentiated too (VLBM_ADJOINT_DIFF_A: the subgradient of the max taken at
  * the first cell, in index order j nx + i, where it is reached). Covered: the
- * first-order, unlimited and PP schemes on fully periodic grids; other limiters
- * or boundaries return VLBM_E_UNSUPPORTED.
+ * first-order, unlimited and PP schemes, on periodic grids and on grids with a
+ * boundary (zero gradient, mirror walls, prescribed states, sides that switch
+ * type, the sponge layer): there the transpose of the ghost fill carries each
+ * ghost's cotangent to the cell it was filled from, and a prescribed ghost holds
+ * no state. LMP / RLMP, and VLBM_ADJOINT_DIFF_A with a prescribed boundary state,
+ * return VLBM_E_UNSUPPORTED.
  *
  * Memory: checkpoints of the state every ckpt_every steps, a segment buffer of
  * ckpt_every + 1 states for the recomputation, and two cotangent buffers, all in

@@ -33,7 +33,8 @@ namespace vlbm {
 
 template <typename T, bool DA>
 static cudaError_t launch_adjoint_step_da(const AdjArgs<T> &A, int limiter, cudaStream_t s) {
-    const dim3 blk(32, 8), grd((A.nx + 31) / 32, (A.ny + 7) / 8);
+    const int wx = A.nx + 2 * A.ext, wy = A.ny + 2 * A.ext;   // with a boundary: the first ghost layer too
+    const dim3 blk(32, 8), grd((wx + 31) / 32, (wy + 7) / 8);
     switch (limiter) {
         case VLBM_LIM_FIRST_ORDER: k_adjoint_step<T, VLBM_LIM_FIRST_ORDER, DA><<<grd, blk, 0, s>>>(A); break;
         case VLBM_LIM_NONE: k_adjoint_step<T, VLBM_LIM_NONE, DA><<<grd, blk, 0, s>>>(A); break;
@@ -53,6 +54,19 @@ static cudaError_t launch_adjoint_init(const T *init_state, const Layout &L, con
                                        T *grad, double *abar, cudaStream_t s) {
     const dim3 blk(32, 8), grd((L.nx + 31) / 32, (L.ny + 7) / 8);
     k_adjoint_init<T><<<grd, blk, 0, s>>>(init_state, L.plane, L.pitch, L.nx, L.ny, kc, cot, grad, abar);
+    return cudaGetLastError();
+}
+
+// Transpose of the ghost fill on the padded cotangent, then its interior into cot.
+template <typename T>
+static cudaError_t fold_ghosts(T *pad, const vlbm_state *s, T *cot, cudaStream_t st) {
+    int bc[4];
+    uniform_types(s->bd, bc);
+    const int nx = s->grid.nx, ny = s->grid.ny;
+    k_adjoint_fold_y<T><<<(2 * (nx + 2) + 127) / 128, 128, 0, st>>>(pad, nx, ny, s->bd, bc[2], bc[3]);
+    k_adjoint_fold_x<T><<<(2 * ny + 127) / 128, 128, 0, st>>>(pad, nx, ny, s->bd, bc[0], bc[1]);
+    const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
+    k_adjoint_unpad<T><<<grd, blk, 0, st>>>(pad, nx, ny, cot);
     return cudaGetLastError();
 }
 
@@ -102,6 +116,7 @@ struct Plan {
     size_t cot_off;       // two cotangent buffers of 20 compact planes
     size_t cot_bytes;
     size_t red_off;       // the dL/da hand-over slots
+    size_t pad_off;       // a cotangent padded by one ghost layer (grids with a boundary)
     size_t total;
 };
 
@@ -124,6 +139,8 @@ Plan plan_of(const vlbm_state *s, int64_t nsteps, int32_t every) {
     off += 2 * p.cot_bytes;
     p.red_off = off;
     off += 256;
+    p.pad_off = off;
+    off += round256((size_t)kNPlane * (s->grid.nx + 2) * (s->grid.ny + 2) * s->L.elem);
     p.total = off;
     return p;
 }
@@ -168,8 +185,25 @@ bool build_recompute_descs(vlbm_state *s, char *scratch, const Plan &p, int32_t 
 }
 
 // One recomputation step m = s0 + j of a segment.
+// The prescribed ghosts of slot j + 1 (the state s^m, m = s0 + j) at the control
+// block's t and a, for the row-marching kernel's recomputation and for the adjoint
+// step that reads that state.
+template <typename T>
+cudaError_t dirichlet_slot(vlbm_state *s, char *scratch, const Plan &p, int64_t m, int64_t j) {
+    if (!use_fused(s) || !s->bd.has_dir) return cudaSuccess;
+    StepArgs<T> A = args_of<T>(s);
+    T *in = (T *)slot_ptr(scratch, p, s, j + 1), *out = (T *)slot_ptr(scratch, p, s, j + 2);
+    A.buf0 = (m & 1) ? out : in;
+    A.buf1 = (m & 1) ? in : out;
+    A.ctl = (DevCtl *)(scratch + p.segctl_off);
+    A.bd.ctl = A.ctl;
+    return launch_dirichlet_ghosts<T>(A, s->stream);
+}
+
 template <typename T>
 cudaError_t recompute_step(vlbm_state *s, char *scratch, const Plan &p, int32_t every, int64_t m, int64_t j) {
+    cudaError_t e0 = dirichlet_slot<T>(s, scratch, p, m, j);
+    if (e0 != cudaSuccess) return e0;
     if (use_fused(s)) {
         FusedBatchArgs<T> B = batch_args_of<T>(s);
         B.insts = (const InstDesc<T> *)(scratch + p.desc_off + ((size_t)(m & 1) * every + j) * 512);
@@ -180,6 +214,7 @@ cudaError_t recompute_step(vlbm_state *s, char *scratch, const Plan &p, int32_t 
     A.buf0 = (m & 1) ? out : in;
     A.buf1 = (m & 1) ? in : out;
     A.ctl = (DevCtl *)(scratch + p.segctl_off);
+    A.bd.ctl = A.ctl;
     cudaError_t e = launch_step_simple<T>(A, s->stream);
     if (e == cudaSuccess) e = launch_ghosts<T>(A, s->stream);   // reads the parity of n + 1
     return e;
@@ -239,6 +274,12 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     A.nx = s->grid.nx;
     A.ny = s->grid.ny;
     A.abar = diff_a ? &red->abar : nullptr;
+    bool periodic = true;
+    for (int q = 0; q < 4; ++q) periodic = periodic && s->grid.bc[q] == VLBM_BC_PERIODIC;
+    A.ext = periodic ? 0 : 1;
+    uniform_types(s->bd, A.bc);
+    A.sponge = s->sponge;
+    T *pad = (T *)(scratch + p.pad_off);
     for (int64_t c = nsteps > 0 ? p.nckpt - 1 : -1; c >= 0; --c) {
         const int64_t s0 = c * every;
         const int64_t e0 = (s0 + every < nsteps ? s0 + every : nsteps) - 1;
@@ -252,13 +293,15 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
                                     cudaMemcpyDeviceToDevice, s->stream);
             if (e == cudaSuccess && m < e0) e = recompute_step<T>(s, scratch, p, every, m, m - s0);
         }
+        if (e == cudaSuccess) e = dirichlet_slot<T>(s, scratch, p, e0, e0 - s0);   // the segment's last state
         if (e != cudaSuccess) return cuda_fail(s, e, "recomputation");
         for (int64_t m = e0; m >= s0; --m) {
             A.fwd = (const T *)slot_ptr(scratch, p, s, m - s0 + 1);
             A.cot_in = cot[cur];
-            A.cot_out = cot[cur ^ 1];
+            A.cot_out = A.ext ? pad : cot[cur ^ 1];
             A.k = fixed_a ? ctl_consts<T>(segctl) : (const StepConsts<T> *)(khist + (m - s0) * kConstSlot);
             e = launch_adjoint_step<T>(A, s->limiter, s->stream);
+            if (e == cudaSuccess && A.ext) e = fold_ghosts<T>(pad, s, cot[cur ^ 1], s->stream);
             if (e != cudaSuccess) return cuda_fail(s, e, "adjoint step launch");
             cur ^= 1;
             if (diff_a && m > 0) {   // a^m came from lambda of s^m (a^0 waits for the init map)
@@ -312,9 +355,8 @@ int vlbm_adjoint(vlbm_state *s, const void *d_u0, int64_t nsteps, int32_t ckpt_e
     if (!d_dLduN || !d_dLdu0) return fail(s, VLBM_E_INVAL, "cotangent pointer is NULL");
     if (s->limiter != VLBM_LIM_FIRST_ORDER && s->limiter != VLBM_LIM_NONE && s->limiter != VLBM_LIM_PP)
         return fail(s, VLBM_E_UNSUPPORTED, "the adjoint covers the first-order, unlimited and PP schemes");
-    for (int q = 0; q < 4; ++q)
-        if (s->grid.bc[q] != VLBM_BC_PERIODIC)
-            return fail(s, VLBM_E_UNSUPPORTED, "the adjoint covers periodic grids");
+    if (s->adj_mode == VLBM_ADJOINT_DIFF_A && s->a_fixed <= 0.0 && s->bd.has_dir)
+        return fail(s, VLBM_E_UNSUPPORTED, "differentiating a^n with a prescribed boundary state");
     DeviceGuard g(s->device);
     const Plan p = plan_of(s, nsteps, ckpt_every);
     int rc = check_scratch(s, d_scratch, scratch_bytes, p);

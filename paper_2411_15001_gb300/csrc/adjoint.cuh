@@ -13,7 +13,12 @@
 //  - the Maxwellians M_k = (1-alpha)/4 u +- f/(2a) (Example D2Q5) through the
 //    Jacobians of the Euler fluxes.
 // The forward state is read from a padded buffer with its ghost frame; the
-// cotangents are compact planes and the grid is periodic.
+// cotangents are compact planes. On a periodic grid the gather wraps around. With
+// a boundary (ext) the step reads ghost cells filled from the state (the ghost
+// fill G): the gather then also runs over the first ghost layer, where no output
+// exists (zero cotangent), into a buffer padded by one cell, and k_adjoint_fold_*
+// apply the transpose of G (y ghosts into their sources, then x ghosts; a mirror
+// ghost's map is its own transpose; a prescribed ghost depends on no state).
 //
 // Optionally (DA) the kernel also accumulates abar = dL/da^n, the cotangent of
 // the step's kinetic speed: a enters the Maxwellians (f / 2a), kappa = a (1 -
@@ -36,6 +41,9 @@ struct AdjArgs {
     T *cot_out;            // cotangent of s^n: 20 compact planes
     const StepConsts<T> *k;  // constants of the step (kinetic speed a^n as the forward run used it)
     double *abar;          // DA: accumulates dL/da^n
+    int ext;               // 1: grid with a boundary (cot_out padded by one cell, see above)
+    int bc[4];             // uniform side types (-1 where a side switches), for the sponge
+    int sponge;            // theta = 0 layer of the forward step (Sec. 4.2)
 };
 
 // w^T df/du for the Euler x-flux (dir 0) or y-flux (dir 1) at state u.
@@ -178,12 +186,35 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     bool act[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) th[f] = theta_and_grad<T, LIM>(us[f], df[f], k, gus[f], gdf[f], &act[f]);
-    // ---------------------------------------------------------- cotangents (periodic)
-    const int iw = i > 0 ? i - 1 : A.nx - 1, ie = i < A.nx - 1 ? i + 1 : 0;
-    const int js = j > 0 ? j - 1 : A.ny - 1, jn = j < A.ny - 1 ? j + 1 : 0;
-    const long long cC = (long long)j * A.nx + i, cW = (long long)j * A.nx + iw, cE = (long long)j * A.nx + ie;
-    const long long cS = (long long)js * A.nx + i, cN = (long long)jn * A.nx + i;
-    auto cot = [&](int q, long long c) { return A.cot_in[q * N + c]; };
+    if (A.sponge > 0) {   // theta = 0 on the faces of sponge cells, whatever the limiter
+        const Sponge sp(A.sponge, A.nx, A.ny, A.bc);
+        const bool cc = sp.cell(i, j);
+        const bool in[4] = {cc || sp.cell(i - 1, j), cc || sp.cell(i + 1, j), cc || sp.cell(i, j - 1),
+                            cc || sp.cell(i, j + 1)};
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+            if (in[f]) {
+                th[f] = T(0);
+                act[f] = false;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) gus[f][c] = gdf[f][c] = T(0);
+            }
+    }
+    // ---------------------------------------------------------- cotangents
+    // of the outputs of cell (x, y): wrapped on a periodic grid, 0 outside the
+    // interior on a grid with a boundary
+    auto cell_of = [&](int x, int y) -> long long {
+        if (A.ext) {
+            if ((unsigned)x >= (unsigned)A.nx || (unsigned)y >= (unsigned)A.ny) return -1;
+        } else {
+            x = x < 0 ? x + A.nx : (x >= A.nx ? x - A.nx : x);
+            y = y < 0 ? y + A.ny : (y >= A.ny ? y - A.ny : y);
+        }
+        return (long long)y * A.nx + x;
+    };
+    const long long cC = cell_of(i, j), cW = cell_of(i - 1, j), cE = cell_of(i + 1, j);
+    const long long cS = cell_of(i, j - 1), cN = cell_of(i, j + 1);
+    auto cot = [&](int q, long long c) { return c < 0 ? T(0) : A.cot_in[q * N + c]; };
     T ubC[4], ubW[4], ubE[4], ubS[4], ubN[4];
     T P1C[4], P2C[4], P3C[4], P4C[4], P1E[4], P2W[4], P3N[4], P4S[4];
 #pragma unroll
@@ -238,8 +269,14 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     flux_vjp(uC, k.gm1, 1, wy, ry);
 #pragma unroll
     for (int c = 0; c < 4; ++c) out[c] += rx[c] + ry[c];
+    if (A.ext) {
+        const long long Np = (long long)(A.nx + 2) * (A.ny + 2), cp = (long long)(j + 1) * (A.nx + 2) + (i + 1);
 #pragma unroll
-    for (int q = 0; q < kNPlane; ++q) A.cot_out[q * N + cC] = out[q];
+        for (int q = 0; q < kNPlane; ++q) A.cot_out[q * Np + cp] = out[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < kNPlane; ++q) A.cot_out[q * N + cC] = out[q];
+    }
     if constexpr (!DA) {
         return 0.0;
     } else {
@@ -284,10 +321,11 @@ __device__ __forceinline__ void warp_sum_atomic(double v, double *dst) {
 
 template <typename T, int LIM, bool DA>
 __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    // with a boundary the threads cover the first ghost layer too: cells -1 .. n
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - A.ext;
+    const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - A.ext;
     double abar = 0.0;
-    if (i < A.nx && j < A.ny) abar = adjoint_cell<T, LIM, DA>(A, i, j);
+    if (i < A.nx + A.ext && j < A.ny + A.ext) abar = adjoint_cell<T, LIM, DA>(A, i, j);
     if constexpr (DA) warp_sum_atomic(abar, A.abar);   // blocks are 32 x 8: whole warps
 }
 
@@ -402,6 +440,64 @@ __global__ void k_lambda_apply(const T *st, long long plane, int pitch, int nx, 
     const double s = ab * 2.0 / (1.0 - alpha);
     const long long cc = (long long)j * nx + i;
     for (int q = 0; q < 4; ++q) cot[q * N + cc] += (T)(s * g[q]);
+}
+
+}  // namespace vlbm
+
+namespace vlbm {
+
+// Transpose of the ghost fill on a padded cotangent (one ghost layer, (nx + 2) x
+// (ny + 2) per plane): the cotangent of each ghost goes to the cell it was filled
+// from (ZG copy, periodic copy, or mirror image with its map; a prescribed ghost
+// keeps nothing). The y rule was applied last, so it is undone first.
+template <typename T>
+__device__ __forceinline__ void fold_one(T *cot, long long Np, int w, int gi, int gj, int si, int sj, bool mx, bool my) {
+    const long long g = (long long)(gj + 1) * w + (gi + 1), d = (long long)(sj + 1) * w + (si + 1);
+#pragma unroll
+    for (int q = 0; q < kNPlane; ++q) {
+        int src = q;   // the mirror map is a symmetric permutation with signs: its own transpose
+        if (mx && q >= 4 && q < 12) src = q < 8 ? q + 4 : q - 4;
+        if (my && q >= 12) src = q < 16 ? q + 4 : q - 4;
+        T v = cot[src * Np + g];
+        if ((mx && (q & 3) == 1) || (my && (q & 3) == 2)) v = -v;
+        cot[q * Np + d] += v;
+    }
+}
+
+template <typename T>
+__global__ void k_adjoint_fold_y(T *cot, int nx, int ny, Bound bd, int bc2, int bc3) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // 2 (nx + 2) ghosts: rows -1 and ny
+    if (t >= 2 * (nx + 2)) return;
+    const int gi = t % (nx + 2) - 1, gj = t < nx + 2 ? -1 : ny;
+    const int s = gj < 0 ? 2 : 3;
+    const int type = (s == 2 ? bc2 : bc3) >= 0 ? (s == 2 ? bc2 : bc3) : side_type(bd, s, gi);
+    if (type == VLBM_BC_DIRICHLET) return;
+    bool my;
+    const int sj = ghost_source_typed(gj, ny, type, &my);
+    fold_one(cot, (long long)(nx + 2) * (ny + 2), nx + 2, gi, gj, gi, sj, false, my);
+}
+
+template <typename T>
+__global__ void k_adjoint_fold_x(T *cot, int nx, int ny, Bound bd, int bc0, int bc1) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // 2 ny ghosts: columns -1 and nx
+    if (t >= 2 * ny) return;
+    const int gj = t % ny, gi = t < ny ? -1 : nx;
+    const int s = gi < 0 ? 0 : 1;
+    const int type = (s == 0 ? bc0 : bc1) >= 0 ? (s == 0 ? bc0 : bc1) : side_type(bd, s, gj);
+    if (type == VLBM_BC_DIRICHLET) return;
+    bool mx;
+    const int si = ghost_source_typed(gi, nx, type, &mx);
+    fold_one(cot, (long long)(nx + 2) * (ny + 2), nx + 2, gi, gj, si, gj, mx, false);
+}
+
+// Interior of a padded cotangent into compact planes.
+template <typename T>
+__global__ void k_adjoint_unpad(const T *cot_pad, int nx, int ny, T *cot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const long long Np = (long long)(nx + 2) * (ny + 2), N = (long long)nx * ny;
+#pragma unroll
+    for (int q = 0; q < kNPlane; ++q) cot[q * N + (long long)j * nx + i] = cot_pad[q * Np + (long long)(j + 1) * (nx + 2) + i + 1];
 }
 
 }  // namespace vlbm
