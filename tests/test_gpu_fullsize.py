@@ -118,7 +118,10 @@ def test_quadrant_1024_lmp_to_final_time():
     """The 1024^2 quadrant problem with LMP run to t = 0.25 as specified (last step
     shortened to land on it): FP32 with the row-marching kernel against the FP64
     path, which is the oracle's run bit for bit on every smaller case: step counts
-    within 1 %, every step admissible, density within L1 1e-3."""
+    within 1 %, every step admissible, density within L1 1e-2. This run is
+    ill-conditioned at float precision: the FP64 oracle itself, with a relative 2^-24
+    jitter after every step, ends 5.5e-3 (L1) from its own clean run (2330 against
+    2329 steps; measured once, 33 CPU-minutes); the FP32 run lands 4.0e-3 away."""
     p = W.quadrant_riemann(1024, seed=0)
     out = {}
     for prec, dt, kern in ((V.FP32, torch.float32, V.KERNEL_FUSED), (V.FP64, torch.float64, V.KERNEL_SIMPLE)):
@@ -135,4 +138,4 @@ def test_quadrant_1024_lmp_to_final_time():
     err = float(np.abs(u32[0] - u64[0]).sum() / np.abs(u64[0]).sum())
     # the dynamic a^n follow each run's own max lambda: LMP's sensitivity moves the
     # step count a little (measured 2333 vs 2329)
-    assert abs(n32 - n64) <= 0.01 * n64 and err <= 1e-3, (n32, n64, err)
+    assert abs(n32 - n64) <= 0.01 * n64 and err <= 1e-2, (n32, n64, err)
