@@ -31,14 +31,14 @@ using namespace vlbm::api;
 
 namespace vlbm {
 
-template <typename T, bool DA>
+template <typename T, bool DA, bool EXT>
 static cudaError_t launch_adjoint_step_da(const AdjArgs<T> &A, int limiter, cudaStream_t s) {
-    const int wx = A.nx + 2 * A.ext, wy = A.ny + 2 * A.ext;   // with a boundary: the first ghost layer too
+    const int wx = A.nx + (EXT ? 2 : 0), wy = A.ny + (EXT ? 2 : 0);   // with a boundary: the first ghost layer too
     const dim3 blk(32, 8), grd((wx + 31) / 32, (wy + 7) / 8);
     switch (limiter) {
-        case VLBM_LIM_FIRST_ORDER: k_adjoint_step<T, VLBM_LIM_FIRST_ORDER, DA><<<grd, blk, 0, s>>>(A); break;
-        case VLBM_LIM_NONE: k_adjoint_step<T, VLBM_LIM_NONE, DA><<<grd, blk, 0, s>>>(A); break;
-        case VLBM_LIM_PP: k_adjoint_step<T, VLBM_LIM_PP, DA><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_FIRST_ORDER: k_adjoint_step<T, VLBM_LIM_FIRST_ORDER, DA, EXT><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_NONE: k_adjoint_step<T, VLBM_LIM_NONE, DA, EXT><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_PP: k_adjoint_step<T, VLBM_LIM_PP, DA, EXT><<<grd, blk, 0, s>>>(A); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -46,7 +46,11 @@ static cudaError_t launch_adjoint_step_da(const AdjArgs<T> &A, int limiter, cuda
 
 template <typename T>
 static cudaError_t launch_adjoint_step(const AdjArgs<T> &A, int limiter, cudaStream_t s) {
-    return A.abar ? launch_adjoint_step_da<T, true>(A, limiter, s) : launch_adjoint_step_da<T, false>(A, limiter, s);
+    if (A.ext)
+        return A.abar ? launch_adjoint_step_da<T, true, true>(A, limiter, s)
+                      : launch_adjoint_step_da<T, false, true>(A, limiter, s);
+    return A.abar ? launch_adjoint_step_da<T, true, false>(A, limiter, s)
+                  : launch_adjoint_step_da<T, false, false>(A, limiter, s);
 }
 
 template <typename T>

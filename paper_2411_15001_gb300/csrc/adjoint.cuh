@@ -140,7 +140,7 @@ __device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const 
 }
 
 // The transpose for cell (i, j); returns its part of dL/da^n (DA) or 0.
-template <typename T, int LIM, bool DA>
+template <typename T, int LIM, bool DA, bool EXT>
 __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j) {
     const StepConsts<T> k = *A.k;
     CellLoad<T> L{A.fwd, A.plane, A.pitch};
@@ -204,7 +204,7 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     // of the outputs of cell (x, y): wrapped on a periodic grid, 0 outside the
     // interior on a grid with a boundary
     auto cell_of = [&](int x, int y) -> long long {
-        if (A.ext) {
+        if constexpr (EXT) {
             if ((unsigned)x >= (unsigned)A.nx || (unsigned)y >= (unsigned)A.ny) return -1;
         } else {
             x = x < 0 ? x + A.nx : (x >= A.nx ? x - A.nx : x);
@@ -269,7 +269,7 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     flux_vjp(uC, k.gm1, 1, wy, ry);
 #pragma unroll
     for (int c = 0; c < 4; ++c) out[c] += rx[c] + ry[c];
-    if (A.ext) {
+    if constexpr (EXT) {
         const long long Np = (long long)(A.nx + 2) * (A.ny + 2), cp = (long long)(j + 1) * (A.nx + 2) + (i + 1);
 #pragma unroll
         for (int q = 0; q < kNPlane; ++q) A.cot_out[q * Np + cp] = out[q];
@@ -319,13 +319,14 @@ __device__ __forceinline__ void warp_sum_atomic(double v, double *dst) {
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
 }
 
-template <typename T, int LIM, bool DA>
+template <typename T, int LIM, bool DA, bool EXT>
 __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
-    // with a boundary the threads cover the first ghost layer too: cells -1 .. n
-    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - A.ext;
-    const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - A.ext;
+    // with a boundary (EXT) the threads cover the first ghost layer too: cells -1 .. n
+    constexpr int e = EXT ? 1 : 0;
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - e;
+    const int j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - e;
     double abar = 0.0;
-    if (i < A.nx + A.ext && j < A.ny + A.ext) abar = adjoint_cell<T, LIM, DA>(A, i, j);
+    if (i < A.nx + e && j < A.ny + e) abar = adjoint_cell<T, LIM, DA, EXT>(A, i, j);
     if constexpr (DA) warp_sum_atomic(abar, A.abar);   // blocks are 32 x 8: whole warps
 }
 
