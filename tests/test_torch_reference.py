@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 from tests import torch_reference as TR  # noqa: E402
 
 
-@pytest.mark.parametrize("lim", [O.LIM_FIRST, O.LIM_SECOND, O.LIM_PP])
+@pytest.mark.parametrize("lim", [O.LIM_FIRST, O.LIM_SECOND, O.LIM_PP, O.LIM_LMP, O.LIM_RLMP])
 def test_forward_matches_oracle(lim):
     p = W.vortex_with_bumps(24)
     cfg = O.Config(24, 24, (0, 0, 0, 0), lim, 1.4, 0.5, 1e-16)
@@ -92,3 +92,49 @@ def test_dynamic_speed_rollout_matches_oracle_and_its_differences():
         fd = (4.0 * (L(h) - L(-h)) / (2 * h) - (L(2 * h) - L(-2 * h)) / (4 * h)) / 3.0
         ad = float((g * d).sum())
         assert abs(fd - ad) <= 1e-7 * abs(ad), (k, fd, ad)
+
+
+def _waves(n=24):
+    """Smooth periodic waves with no flat region: the LMP bound is active on 240-310
+    faces per step, and theta moves smoothly with the data (a flat region puts dF^rho
+    at 0 where rho* sits on a bound, and LMP's theta jumps there between 1 and 0)."""
+    X, Y = np.meshgrid((np.arange(n) + 0.5) / n, (np.arange(n) + 0.5) / n)
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * X + 0.4) * np.cos(2 * np.pi * Y + 0.7) + 0.1 * np.sin(4 * np.pi * (X + 2 * Y))
+    v1 = 0.5 * np.cos(2 * np.pi * Y + 0.2)
+    v2 = 0.3 * np.sin(2 * np.pi * X + 1.1)
+    p = 1.0 + 0.2 * np.cos(2 * np.pi * (X - Y))
+    return np.stack(W.primitive_to_conserved(rho, v1, v2, p)), 1.0 / n
+
+
+@pytest.mark.parametrize("lim", [O.LIM_LMP, O.LIM_RLMP])
+def test_lmp_restatement_matches_oracle_theta_and_differences(lim):
+    """LMP / RLMP: the step equals the oracle's with the bound active on hundreds of
+    faces, and autograd equals central differences (Richardson) of the oracle's run
+    along random directions."""
+    cons, dx = _waves()
+    n = cons.shape[1]
+    cfg = O.Config(n, n, (0, 0, 0, 0), lim, 1.4, 0.5, 1e-16)
+    lam = 1.05 * O.max_speed(cfg, O.new_state(cons))
+    a = O.kinetic_speed(lam, 0.5)
+    st = O.run(cfg, cons, dx, nsteps=3, lam_fixed=lam)["state"]
+    _, dbg = O.step(cfg, st, a, debug=True)
+    assert (dbg["theta_x"] < 1.0).sum() + (dbg["theta_y"] < 1.0).sum() > 200
+    got = TR.step(torch.tensor(st), a, lim).numpy()
+    ref = O.step(cfg, st, a)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    nsteps = 6
+    rng = np.random.default_rng(5)
+    w = rng.uniform(0.5, 1.5, size=(4, n, n))
+    u0 = torch.tensor(cons, requires_grad=True)
+    (torch.tensor(w) * TR.rollout(u0, nsteps, a, lim)[:4]).sum().backward()
+    g = u0.grad.numpy()
+    for k in range(4):
+        d = rng.standard_normal((4, n, n)) * np.abs(cons) * 1e-2
+        h = 1e-5
+
+        def L(x):
+            return float((w * O.run(cfg, cons + x * d, dx, nsteps=nsteps, lam_fixed=lam)["state"][:4]).sum())
+
+        fd = (4.0 * (L(h) - L(-h)) / (2 * h) - (L(2 * h) - L(-2 * h)) / (4 * h)) / 3.0
+        ad = float((g * d).sum())
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (k, fd, ad)

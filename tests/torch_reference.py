@@ -34,6 +34,49 @@ def init_populations(u, a, alpha, gamma):
     return torch.cat([u, w * u + f / (2 * a), w * u - f / (2 * a), w * u + g / (2 * a), w * u - g / (2 * a)])
 
 
+def theta_p_only(us, df, kappa, eps):
+    """The internal-energy bound theta_p of Sec. 3.4 (1 where the radius is 0, 0 where
+    u* is outside G), with the scheme's tie rules."""
+    rs, m1, m2, Es = us[0], us[1], us[2], us[3]
+    dr, dm1, dm2, dE = df[0], df[1], df[2], df[3]
+    one = torch.ones_like(rs)
+    zero = torch.zeros_like(rs)
+    adr = torch.abs(dr)
+    g0 = m1 * m1 + m2 * m2 - 2.0 * rs * Es
+    g1 = 2.0 * (dr * Es + dE * rs - dm1 * m1 - dm2 * m2)
+    cq = dm1 * dm1 + dm2 * dm2 - 2.0 * dr * dE
+    disc = g1 * g1 - 4.0 * g0 * cq
+    pos = disc > 0
+    sq = torch.where(pos, torch.sqrt(torch.where(pos, disc, one)), zero)
+    inside = (rs > 0) & (g0 < 0)
+    r1 = adr / torch.where(inside, rs, one)
+    r2 = (torch.abs(g1) + sq) / (-2.0 * torch.where(inside, g0, -one))
+    r = torch.where(r1 > r2, r1, r2)
+    rpos = r > 0
+    t_p = kappa / torch.where(rpos, r, one) - eps
+    th_p = torch.where(rpos, torch.where(t_p > 0, t_p, zero), one)
+    return torch.where(inside, th_p, zero)
+
+
+def theta_lmp(us, df, mu_l, nu_l, mu_r, nu_r, kappa, eps):
+    """theta = min(1, theta_rho LMP, theta_p), clamped at 0: the three cases of
+    Sec. 3.3.1 with the bounds of the cells left (l) and right (r) of the face."""
+    rs, dr = us[0], df[0]
+    one = torch.ones_like(rs)
+    zero = torch.zeros_like(rs)
+    nz = dr != 0
+    a1, a2 = nu_r - rs, rs - mu_l
+    b1, b2 = rs - mu_r, nu_l - rs
+    dsafe = torch.where(nz, dr, one)
+    t_pos = kappa * torch.where(a1 < a2, a1, a2) / dsafe
+    t_neg = -kappa * torch.where(b1 < b2, b1, b2) / dsafe
+    th_rho = torch.where(nz, torch.where(dr > 0, t_pos, t_neg), one)
+    th_p = theta_p_only(us, df, kappa, eps)
+    th = torch.where(th_rho < one, th_rho, one)
+    th = torch.where(th_p < th, th_p, th)
+    return torch.where(th < 0, zero, th)
+
+
 def theta_pp(us, df, kappa, eps):
     """theta = min(1, theta_rho, theta_p), clamped at 0; us, df: (4, ...). Every
     selection is a torch.where with the comparison and tie rule of the scheme's
@@ -67,7 +110,11 @@ def theta_pp(us, df, kappa, eps):
 
 
 def step(s, a, limiter, alpha=0.5, gamma=1.4, eps=1e-16):
-    """One step; limiter 0 (theta = 0), 1 (theta = 1) or 2 (PP)."""
+    """One step; limiter 0 (theta = 0), 1 (theta = 1), 2 (PP), 3 (LMP) or 4 (RLMP).
+    The LMP bounds of a cell are the min / max of its density and of rho* on its four
+    faces (eq. LMP_minmax), in the order rho, west, east, south, north (the gradient
+    of a min goes to the first place it is reached); RLMP scales them by 0.999 and
+    1.001 (Sec. 3.3.2)."""
     u, P1, P2, P3, P4 = s[0:4], s[4:8], s[8:12], s[12:16], s[16:20]
     f, g = fluxes(u, gamma)
     w = (1.0 - alpha) / 4.0
@@ -90,9 +137,17 @@ def step(s, a, limiter, alpha=0.5, gamma=1.4, eps=1e-16):
     elif limiter == 1:
         tx = torch.ones_like(u[0])
         ty = torch.ones_like(u[0])
-    else:
+    elif limiter == 2:
         tx = theta_pp(us_x, df_x, kappa, eps)
         ty = theta_pp(us_y, df_y, kappa, eps)
+    else:
+        rho_all = torch.stack([u[0], Wr(us_x[0]), us_x[0], Sr(us_y[0]), us_y[0]])
+        mu = torch.min(rho_all, dim=0).values
+        nu = torch.max(rho_all, dim=0).values
+        if limiter == 4:
+            mu, nu = 0.999 * mu, 1.001 * nu
+        tx = theta_lmp(us_x, df_x, mu, nu, E(mu), E(nu), kappa, eps)
+        ty = theta_lmp(us_y, df_y, mu, nu, N(mu), N(nu), kappa, eps)
     tE, tW, tN, tS = tx, Wr(tx), ty, Sr(ty)
     P1n = Wr(M1 + tE * d1)          # pulled from the west cell across its east face
     P2n = E(M2 + tW * d2)           # pulled from the east cell across its west face
