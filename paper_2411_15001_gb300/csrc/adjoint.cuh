@@ -186,7 +186,9 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     bool act[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) th[f] = theta_and_grad<T, LIM>(us[f], df[f], k, gus[f], gdf[f], &act[f]);
-    if (A.sponge > 0) {   // theta = 0 on the faces of sponge cells, whatever the limiter
+    // theta = 0 on the faces of sponge cells, whatever the limiter (a sponge needs a
+    // zero-gradient side: never on a periodic grid, whose gather keeps its registers)
+    if (EXT && A.sponge > 0) {
         const Sponge sp(A.sponge, A.nx, A.ny, A.bc);
         const bool cc = sp.cell(i, j);
         const bool in[4] = {cc || sp.cell(i - 1, j), cc || sp.cell(i + 1, j), cc || sp.cell(i, j - 1),
@@ -203,18 +205,30 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     // ---------------------------------------------------------- cotangents
     // of the outputs of cell (x, y): wrapped on a periodic grid, 0 outside the
     // interior on a grid with a boundary
-    auto cell_of = [&](int x, int y) -> long long {
-        if constexpr (EXT) {
+    long long cC, cW, cE, cS, cN;
+    if constexpr (EXT) {
+        auto cell_of = [&](int x, int y) -> long long {
             if ((unsigned)x >= (unsigned)A.nx || (unsigned)y >= (unsigned)A.ny) return -1;
-        } else {
-            x = x < 0 ? x + A.nx : (x >= A.nx ? x - A.nx : x);
-            y = y < 0 ? y + A.ny : (y >= A.ny ? y - A.ny : y);
-        }
-        return (long long)y * A.nx + x;
+            return (long long)y * A.nx + x;
+        };
+        cC = cell_of(i, j);
+        cW = cell_of(i - 1, j);
+        cE = cell_of(i + 1, j);
+        cS = cell_of(i, j - 1);
+        cN = cell_of(i, j + 1);
+    } else {
+        const int iw = i > 0 ? i - 1 : A.nx - 1, ie = i < A.nx - 1 ? i + 1 : 0;
+        const int js = j > 0 ? j - 1 : A.ny - 1, jn = j < A.ny - 1 ? j + 1 : 0;
+        cC = (long long)j * A.nx + i;
+        cW = (long long)j * A.nx + iw;
+        cE = (long long)j * A.nx + ie;
+        cS = (long long)js * A.nx + i;
+        cN = (long long)jn * A.nx + i;
+    }
+    auto cot = [&](int q, long long c) -> T {
+        if constexpr (EXT) return c < 0 ? T(0) : A.cot_in[q * N + c];
+        else return A.cot_in[q * N + c];
     };
-    const long long cC = cell_of(i, j), cW = cell_of(i - 1, j), cE = cell_of(i + 1, j);
-    const long long cS = cell_of(i, j - 1), cN = cell_of(i, j + 1);
-    auto cot = [&](int q, long long c) { return c < 0 ? T(0) : A.cot_in[q * N + c]; };
     T ubC[4], ubW[4], ubE[4], ubS[4], ubN[4];
     T P1C[4], P2C[4], P3C[4], P4C[4], P1E[4], P2W[4], P3N[4], P4S[4];
 #pragma unroll
