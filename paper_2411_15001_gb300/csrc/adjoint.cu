@@ -39,6 +39,24 @@ static cudaError_t launch_adjoint_step_da(const AdjArgs<T> &A, int limiter, cuda
         case VLBM_LIM_FIRST_ORDER: k_adjoint_step<T, VLBM_LIM_FIRST_ORDER, DA, EXT><<<grd, blk, 0, s>>>(A); break;
         case VLBM_LIM_NONE: k_adjoint_step<T, VLBM_LIM_NONE, DA, EXT><<<grd, blk, 0, s>>>(A); break;
         case VLBM_LIM_PP: k_adjoint_step<T, VLBM_LIM_PP, DA, EXT><<<grd, blk, 0, s>>>(A); break;
+        case VLBM_LIM_LMP:
+        case VLBM_LIM_RLMP:
+            if constexpr (!DA && !EXT) {   // periodic grids, a^n held: passes 1, 2, then the gather
+                const size_t N = (size_t)A.nx * A.ny;
+                cudaError_t e = cudaMemsetAsync(A.lmp + kLmub * N, 0, 3 * N * sizeof(T), s);
+                if (e != cudaSuccess) return e;
+                if (limiter == VLBM_LIM_LMP) {
+                    k_adj_lmp_faces<T, VLBM_LIM_LMP><<<grd, blk, 0, s>>>(A);
+                    k_adj_lmp_bounds<T, VLBM_LIM_LMP><<<grd, blk, 0, s>>>(A);
+                    k_adjoint_step<T, VLBM_LIM_LMP, false, false><<<grd, blk, 0, s>>>(A);
+                } else {
+                    k_adj_lmp_faces<T, VLBM_LIM_RLMP><<<grd, blk, 0, s>>>(A);
+                    k_adj_lmp_bounds<T, VLBM_LIM_RLMP><<<grd, blk, 0, s>>>(A);
+                    k_adjoint_step<T, VLBM_LIM_RLMP, false, false><<<grd, blk, 0, s>>>(A);
+                }
+                break;
+            }
+            return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -121,6 +139,7 @@ struct Plan {
     size_t cot_bytes;
     size_t red_off;       // the dL/da hand-over slots
     size_t pad_off;       // a cotangent padded by one ghost layer (grids with a boundary)
+    size_t lmp_off;       // LMP / RLMP: the face and bound planes of the three-pass adjoint
     size_t total;
 };
 
@@ -145,6 +164,9 @@ Plan plan_of(const vlbm_state *s, int64_t nsteps, int32_t every) {
     off += 256;
     p.pad_off = off;
     off += round256((size_t)kNPlane * (s->grid.nx + 2) * (s->grid.ny + 2) * s->L.elem);
+    p.lmp_off = off;
+    if (s->limiter == VLBM_LIM_LMP || s->limiter == VLBM_LIM_RLMP)
+        off += round256((size_t)kLPlanes * s->grid.nx * s->grid.ny * s->L.elem);
     p.total = off;
     return p;
 }
@@ -283,6 +305,7 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     A.ext = periodic ? 0 : 1;
     uniform_types(s->bd, A.bc);
     A.sponge = s->sponge;
+    A.lmp = (T *)(scratch + p.lmp_off);
     T *pad = (T *)(scratch + p.pad_off);
     for (int64_t c = nsteps > 0 ? p.nckpt - 1 : -1; c >= 0; --c) {
         const int64_t s0 = c * every;
@@ -357,8 +380,13 @@ int vlbm_adjoint(vlbm_state *s, const void *d_u0, int64_t nsteps, int32_t ckpt_e
     if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
     if (nsteps < 0 || ckpt_every < 1) return fail(s, VLBM_E_INVAL, "need nsteps >= 0 and ckpt_every >= 1");
     if (!d_dLduN || !d_dLdu0) return fail(s, VLBM_E_INVAL, "cotangent pointer is NULL");
-    if (s->limiter != VLBM_LIM_FIRST_ORDER && s->limiter != VLBM_LIM_NONE && s->limiter != VLBM_LIM_PP)
-        return fail(s, VLBM_E_UNSUPPORTED, "the adjoint covers the first-order, unlimited and PP schemes");
+    if (s->limiter == VLBM_LIM_LMP || s->limiter == VLBM_LIM_RLMP) {
+        for (int q = 0; q < 4; ++q)
+            if (s->grid.bc[q] != VLBM_BC_PERIODIC)
+                return fail(s, VLBM_E_UNSUPPORTED, "the LMP / RLMP adjoint covers periodic grids");
+        if (s->adj_mode == VLBM_ADJOINT_DIFF_A && s->a_fixed <= 0.0)
+            return fail(s, VLBM_E_UNSUPPORTED, "the LMP / RLMP adjoint holds a^n (VLBM_ADJOINT_HOLD_A)");
+    }
     if (s->adj_mode == VLBM_ADJOINT_DIFF_A && s->a_fixed <= 0.0 && s->bd.has_dir)
         return fail(s, VLBM_E_UNSUPPORTED, "differentiating a^n with a prescribed boundary state");
     DeviceGuard g(s->device);

@@ -42,6 +42,10 @@ struct AdjArgs {
     const StepConsts<T> *k;  // constants of the step (kinetic speed a^n as the forward run used it)
     double *abar;          // DA: accumulates dL/da^n
     int ext;               // 1: grid with a boundary (cot_out padded by one cell, see above)
+    // LMP / RLMP (periodic grids): per-face theta and (u*, dF) cotangents, per-cell
+    // bound cotangents, filled by k_adj_lmp_faces / k_adj_lmp_bounds before the gather.
+    // Planes of nx ny: thE, thN, usbE[4], dfbE[4], usbN[4], dfbN[4], mub, nub, rb.
+    T *lmp;
     int bc[4];             // uniform side types (-1 where a side switches), for the sponge
     int sponge;            // theta = 0 layer of the forward step (Sec. 4.2)
 };
@@ -67,30 +71,10 @@ __device__ __forceinline__ void flux_vjp(const T u[4], T gm1, int dir, const T w
     }
 }
 
-// Forward theta of a face (as combine_theta computes it) and its gradient with
-// respect to (u*, dF) on the active branch. Density bounds of the PP kind only.
-// *active: theta is one of the two bounds (not 1, not clamped), both of the form
-// kappa X - eps, so that d theta / d kappa = (theta + eps) / kappa at fixed (u*, dF).
-template <typename T, int LIM>
-__device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const StepConsts<T> &k,
-                                            T gus[4], T gdf[4], bool *active) {
-    *active = false;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) gus[c] = gdf[c] = T(0);
-    if (LIM == VLBM_LIM_FIRST_ORDER) return T(0);
-    if (LIM == VLBM_LIM_NONE) return T(1);
-    const T tr = theta_rho_pp(us[0], df[0], k);
-    unsigned int dummy = 0;
-    const T th = combine_theta(tr, us, df, k, dummy);
-    if (!(th > T(0)) || !(th < T(1))) return th;    // clamped: no gradient
-    *active = true;
-    if (th == tr) {                                  // density bound active (Sec. 3.3.3)
-        const T ad = fabs(df[0]);
-        gus[0] = k.kappa / ad;
-        gdf[0] = -k.kappa * us[0] * (df[0] > T(0) ? T(1) : T(-1)) / (ad * ad);
-        return th;
-    }
-    // internal-energy bound active (Sec. 3.4): theta = kappa / varrho - eps
+// Gradient of theta = theta_p = kappa / varrho - eps (Sec. 3.4, the internal-energy
+// bound active) with respect to (u*, dF).
+template <typename T>
+__device__ __forceinline__ void thp_grad(const T us[4], const T df[4], const StepConsts<T> &k, T gus[4], T gdf[4]) {
     const T rs = us[0], m1 = us[1], m2 = us[2], Es = us[3];
     const T dr = df[0], dm1 = df[1], dm2 = df[2], dE = df[3];
     const T g0 = m1 * m1 + m2 * m2 - T(2) * rs * Es;
@@ -136,10 +120,206 @@ __device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const 
         gus[c] = f * gr_us[c];
         gdf[c] = f * gr_df[c];
     }
+}
+
+// Forward theta of a face (as combine_theta computes it) and its gradient with
+// respect to (u*, dF) on the active branch. Density bounds of the PP kind only.
+// *active: theta is one of the two bounds (not 1, not clamped), both of the form
+// kappa X - eps, so that d theta / d kappa = (theta + eps) / kappa at fixed (u*, dF).
+template <typename T, int LIM>
+__device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const StepConsts<T> &k,
+                                            T gus[4], T gdf[4], bool *active) {
+    *active = false;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) gus[c] = gdf[c] = T(0);
+    if (LIM == VLBM_LIM_FIRST_ORDER) return T(0);
+    if (LIM == VLBM_LIM_NONE) return T(1);
+    const T tr = theta_rho_pp(us[0], df[0], k);
+    unsigned int dummy = 0;
+    const T th = combine_theta(tr, us, df, k, dummy);
+    if (!(th > T(0)) || !(th < T(1))) return th;    // clamped: no gradient
+    *active = true;
+    if (th == tr) {                                  // density bound active (Sec. 3.3.3)
+        const T ad = fabs(df[0]);
+        gus[0] = k.kappa / ad;
+        gdf[0] = -k.kappa * us[0] * (df[0] > T(0) ? T(1) : T(-1)) / (ad * ad);
+        return th;
+    }
+    thp_grad(us, df, k, gus, gdf);
     return th;
 }
 
 // The transpose for cell (i, j); returns its part of dL/da^n (DA) or 0.
+enum { kLthE = 0, kLthN = 1, kLusbE = 2, kLdfbE = 6, kLusbN = 10, kLdfbN = 14, kLmub = 18, kLnub = 19, kLrb = 20,
+       kLPlanes = 21 };
+
+// rho* of the x-face (i, i+1) or the y-face (j, j+1) of row / column of cell (i, j)
+// (the density component of u*, eq. D2Q5_convexproof_3: the flux of rho is the
+// normal momentum), from the padded forward state.
+template <typename T>
+__device__ __forceinline__ T rho_star_x(const CellLoad<T> &L, int i, int j, const StepConsts<T> &k) {
+    return face_star(L.v(0, i, j), L.v(1, i, j), L.v(0, i + 1, j), L.v(1, i + 1, j), k);
+}
+template <typename T>
+__device__ __forceinline__ T rho_star_y(const CellLoad<T> &L, int i, int j, const StepConsts<T> &k) {
+    return face_star(L.v(0, i, j), L.v(2, i, j), L.v(0, i, j + 1), L.v(2, i, j + 1), k);
+}
+
+// LMP bounds of cell (i, j) (eq. LMP_minmax; RLMP x 0.999 / 1.001): the min / max of
+// rho and of rho* on the four faces, in the order rho, west, east, south, north;
+// *imin / *imax: the first of them where the min / max is reached.
+template <typename T, int LIM>
+__device__ __forceinline__ void lmp_bounds(const CellLoad<T> &L, int i, int j, const StepConsts<T> &k, T *mu, T *nu,
+                                           int *imin, int *imax) {
+    const T v[5] = {L.v(0, i, j), rho_star_x(L, i - 1, j, k), rho_star_x(L, i, j, k), rho_star_y(L, i, j - 1, k),
+                    rho_star_y(L, i, j, k)};
+    T lo = v[0], hi = v[0];
+    int a = 0, b = 0;
+#pragma unroll
+    for (int q = 1; q < 5; ++q) {
+        if (v[q] < lo) { lo = v[q]; a = q; }
+        if (v[q] > hi) { hi = v[q]; b = q; }
+    }
+    *mu = LIM == VLBM_LIM_RLMP ? RN<T>::mul(lo, T(0.999)) : lo;
+    *nu = LIM == VLBM_LIM_RLMP ? RN<T>::mul(hi, T(1.001)) : hi;
+    *imin = a;
+    *imax = b;
+}
+
+// One face of the LMP adjoint: theta as the step computes it, from the face states
+// (us, df) and the bounds of the cells left (L) and right (R) of it; with tb, the
+// cotangent of theta, the cotangents of u*, dF go to usb, dfb (4 each) and those of
+// the bounds to the cells' mub / nub slots.
+template <typename T, int LIM>
+__device__ __forceinline__ T lmp_face(const T us[4], const T df[4], T muL, T nuL, T muR, T nuR, T tb,
+                                      const StepConsts<T> &k, T usb[4], T dfb[4], T *mubL, T *nubL, T *mubR,
+                                      T *nubR) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) usb[c] = dfb[c] = T(0);
+    const T tr = theta_rho_lmp(us[0], df[0], muL, nuL, muR, nuR, k);
+    unsigned int dummy = 0;
+    const T th = combine_theta(tr, us, df, k, dummy);
+    if (tb == T(0) || !(th > T(0)) || !(th < T(1))) return th;   // no cotangent, or clamped
+    if (th == tr) {          // density bound active (Sec. 3.3.1): theta = s kappa X / dF^rho
+        const T dr = df[0], rs = us[0];
+        const T g = k.kappa / dr;                                   // d theta / dX, with s folded in
+        T gX = T(0), *slot = nullptr;   // dX / drho* and the bound X takes its other term from
+        T gB = T(0);
+        if (dr > T(0)) {
+            const T a1 = nuR - rs, a2 = rs - muL;
+            if (a1 < a2) { gX = T(-1); gB = T(1); slot = nubR; }      // X = nuR - rho*
+            else { gX = T(1); gB = T(-1); slot = mubL; }               // X = rho* - muL
+            usb[0] = tb * g * gX;
+            atomicAdd(slot, tb * g * gB);
+        } else {
+            const T b1 = rs - muR, b2 = nuL - rs;
+            if (b1 < b2) { gX = T(1); gB = T(-1); slot = mubR; }       // X = rho* - muR
+            else { gX = T(-1); gB = T(1); slot = nubL; }               // X = nuL - rho*
+            usb[0] = -tb * g * gX;
+            atomicAdd(slot, -tb * g * gB);
+        }
+        dfb[0] = -tb * th / dr;
+        return th;
+    }
+    T gus[4], gdf[4];   // internal-energy bound active
+    thp_grad(us, df, k, gus, gdf);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        usb[c] = tb * gus[c];
+        dfb[c] = tb * gdf[c];
+    }
+    return th;
+}
+
+// Pass 1 of the LMP / RLMP adjoint (periodic grid, forward state padded with its
+// periodic ghost frame): each cell takes its east and north faces.
+template <typename T, int LIM>
+__global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= A.nx || j >= A.ny) return;
+    const StepConsts<T> k = *A.k;
+    const CellLoad<T> L{A.fwd, A.plane, A.pitch};
+    const long long N = (long long)A.nx * A.ny;
+    const int ie = i < A.nx - 1 ? i + 1 : 0, jn = j < A.ny - 1 ? j + 1 : 0;
+    const long long cC = (long long)j * A.nx + i, cE = (long long)j * A.nx + ie, cN = (long long)jn * A.nx + i;
+    T *P = A.lmp;
+    auto cot = [&](int q, long long c) { return A.cot_in[q * N + c]; };
+    T uC[4], uE[4], uN[4], fC[4], gC[4], fE[4], gE[4], fN[4], gN[4];
+    L.u4(0, i, j, uC);
+    L.u4(0, i + 1, j, uE);
+    L.u4(0, i, j + 1, uN);
+    euler_fluxes(uC, k.gm1, fC, gC);
+    euler_fluxes(uE, k.gm1, fE, gE);
+    euler_fluxes(uN, k.gm1, fN, gN);
+    T usE[4], dfE[4], usN[4], dfN[4], tbE = T(0), tbN = T(0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const T d1C = RN<T>::sub(maxwell_plus(uC[c], fC[c], k), L.v(4 + c, i, j));
+        const T d2E = RN<T>::sub(maxwell_minus(uE[c], fE[c], k), L.v(8 + c, i + 1, j));
+        const T d3C = RN<T>::sub(maxwell_plus(uC[c], gC[c], k), L.v(12 + c, i, j));
+        const T d4N = RN<T>::sub(maxwell_minus(uN[c], gN[c], k), L.v(16 + c, i, j + 1));
+        usE[c] = face_star(uC[c], fC[c], uE[c], fE[c], k);
+        dfE[c] = face_dflux(d1C, d2E, k);
+        usN[c] = face_star(uC[c], gC[c], uN[c], gN[c], k);
+        dfN[c] = face_dflux(d3C, d4N, k);
+        // cotangent of theta: the pulled populations theta d and the local -theta d of u'
+        const T ubC = cot(c, cC), ubE = cot(c, cE), ubN = cot(c, cN);
+        tbE += d1C * (cot(4 + c, cE) + ubE - ubC) + d2E * (cot(8 + c, cC) + ubC - ubE);
+        tbN += d3C * (cot(12 + c, cN) + ubN - ubC) + d4N * (cot(16 + c, cC) + ubC - ubN);
+    }
+    T muC, nuC, muE, nuE, muN, nuN;
+    int a, b;
+    lmp_bounds<T, LIM>(L, i, j, k, &muC, &nuC, &a, &b);
+    lmp_bounds<T, LIM>(L, i + 1, j, k, &muE, &nuE, &a, &b);
+    lmp_bounds<T, LIM>(L, i, j + 1, k, &muN, &nuN, &a, &b);
+    T usb[4], dfb[4];
+    P[kLthE * N + cC] = lmp_face<T, LIM>(usE, dfE, muC, nuC, muE, nuE, tbE, k, usb, dfb, &P[kLmub * N + cC],
+                                         &P[kLnub * N + cC], &P[kLmub * N + cE], &P[kLnub * N + cE]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        P[(kLusbE + c) * N + cC] = usb[c];
+        P[(kLdfbE + c) * N + cC] = dfb[c];
+    }
+    P[kLthN * N + cC] = lmp_face<T, LIM>(usN, dfN, muC, nuC, muN, nuN, tbN, k, usb, dfb, &P[kLmub * N + cC],
+                                         &P[kLnub * N + cC], &P[kLmub * N + cN], &P[kLnub * N + cN]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        P[(kLusbN + c) * N + cC] = usb[c];
+        P[(kLdfbN + c) * N + cC] = dfb[c];
+    }
+}
+
+// Pass 2: the bound cotangents of each cell go to the value its min / max took:
+// its own density (rb) or rho* of one of its faces (the density component of that
+// face's u* cotangent). RLMP scales by 0.999 / 1.001.
+template <typename T, int LIM>
+__global__ void __launch_bounds__(256) k_adj_lmp_bounds(AdjArgs<T> A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= A.nx || j >= A.ny) return;
+    const long long N = (long long)A.nx * A.ny, cC = (long long)j * A.nx + i;
+    T *P = A.lmp;
+    const T mb = P[kLmub * N + cC], nb = P[kLnub * N + cC];
+    if (mb == T(0) && nb == T(0)) return;
+    const StepConsts<T> k = *A.k;
+    const CellLoad<T> L{A.fwd, A.plane, A.pitch};
+    T mu, nu;
+    int a, b;
+    lmp_bounds<T, LIM>(L, i, j, k, &mu, &nu, &a, &b);
+    const int iw = i > 0 ? i - 1 : A.nx - 1, js = j > 0 ? j - 1 : A.ny - 1;
+    const long long cW = (long long)j * A.nx + iw, cS = (long long)js * A.nx + i;
+    auto give = [&](int which, T v) {
+        if (v == T(0)) return;
+        T *dst = which == 0 ? &P[kLrb * N + cC]
+               : which == 1 ? &P[kLusbE * N + cW]
+               : which == 2 ? &P[kLusbE * N + cC]
+               : which == 3 ? &P[kLusbN * N + cS]
+                            : &P[kLusbN * N + cC];
+        atomicAdd(dst, v);
+    };
+    give(a, LIM == VLBM_LIM_RLMP ? mb * T(0.999) : mb);
+    give(b, LIM == VLBM_LIM_RLMP ? nb * T(1.001) : nb);
+}
+
 template <typename T, int LIM, bool DA, bool EXT>
 __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j) {
     const StepConsts<T> k = *A.k;
@@ -182,10 +362,13 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
         us[3][c] = face_star(uC[c], gC[c], uN[c], gN[c], k);
         df[3][c] = face_dflux(d3C[c], d4N[c], k);
     }
+    constexpr bool kLmp = LIM == VLBM_LIM_LMP || LIM == VLBM_LIM_RLMP;
     T th[4], gus[4][4], gdf[4][4];
     bool act[4];
+    if constexpr (!kLmp) {
 #pragma unroll
-    for (int f = 0; f < 4; ++f) th[f] = theta_and_grad<T, LIM>(us[f], df[f], k, gus[f], gdf[f], &act[f]);
+        for (int f = 0; f < 4; ++f) th[f] = theta_and_grad<T, LIM>(us[f], df[f], k, gus[f], gdf[f], &act[f]);
+    }
     // theta = 0 on the faces of sponge cells, whatever the limiter (a sponge needs a
     // zero-gradient side: never on a periodic grid, whose gather keeps its registers)
     if (EXT && A.sponge > 0) {
@@ -229,6 +412,12 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
         if constexpr (EXT) return c < 0 ? T(0) : A.cot_in[q * N + c];
         else return A.cot_in[q * N + c];
     };
+    if constexpr (kLmp) {   // theta of the four faces as pass 1 found it
+        th[0] = A.lmp[kLthE * N + cW];
+        th[1] = A.lmp[kLthE * N + cC];
+        th[2] = A.lmp[kLthN * N + cS];
+        th[3] = A.lmp[kLthN * N + cC];
+    }
     T ubC[4], ubW[4], ubE[4], ubS[4], ubN[4];
     T P1C[4], P2C[4], P3C[4], P4C[4], P1E[4], P2W[4], P3N[4], P4S[4];
 #pragma unroll
@@ -261,10 +450,27 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     T wx[4], wy[4], out[kNPlane];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const T usb_W = tb[0] * gus[0][c], usb_E = tb[1] * gus[1][c];
-        const T usb_S = tb[2] * gus[2][c], usb_N = tb[3] * gus[3][c];
-        const T dfb_W = tb[0] * gdf[0][c], dfb_E = tb[1] * gdf[1][c];
-        const T dfb_S = tb[2] * gdf[2][c], dfb_N = tb[3] * gdf[3][c];
+        T usb_W, usb_E, usb_S, usb_N, dfb_W, dfb_E, dfb_S, dfb_N;
+        if constexpr (kLmp) {   // passes 1 and 2 left the face cotangents
+            const T *P = A.lmp;
+            usb_W = P[(kLusbE + c) * N + cW];
+            usb_E = P[(kLusbE + c) * N + cC];
+            usb_S = P[(kLusbN + c) * N + cS];
+            usb_N = P[(kLusbN + c) * N + cC];
+            dfb_W = P[(kLdfbE + c) * N + cW];
+            dfb_E = P[(kLdfbE + c) * N + cC];
+            dfb_S = P[(kLdfbN + c) * N + cS];
+            dfb_N = P[(kLdfbN + c) * N + cC];
+        } else {
+            usb_W = tb[0] * gus[0][c];
+            usb_E = tb[1] * gus[1][c];
+            usb_S = tb[2] * gus[2][c];
+            usb_N = tb[3] * gus[3][c];
+            dfb_W = tb[0] * gdf[0][c];
+            dfb_E = tb[1] * gdf[1][c];
+            dfb_S = tb[2] * gdf[2][c];
+            dfb_N = tb[3] * gdf[3][c];
+        }
         const T db1 = th[1] * (P1E[c] - ubC[c]) + k.a * dfb_E;
         const T db2 = th[0] * (P2W[c] - ubC[c]) - k.a * dfb_W;
         const T db3 = th[3] * (P3N[c] - ubC[c]) + k.a * dfb_N;
@@ -283,6 +489,7 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     flux_vjp(uC, k.gm1, 1, wy, ry);
 #pragma unroll
     for (int c = 0; c < 4; ++c) out[c] += rx[c] + ry[c];
+    if constexpr (kLmp) out[0] += A.lmp[kLrb * N + cC];   // the density where a cell's bound was taken
     if constexpr (EXT) {
         const long long Np = (long long)(A.nx + 2) * (A.ny + 2), cp = (long long)(j + 1) * (A.nx + 2) + (i + 1);
 #pragma unroll

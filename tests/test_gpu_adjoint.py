@@ -319,8 +319,14 @@ def test_adjoint_full_size_vortex_with_bumps():
 def test_adjoint_rejects_unsupported():
     p = W.vortex_with_bumps(32)
     u0 = torch.tensor(p.conserved(), dtype=torch.float64, device=DEV)
-    s = V.VLBM(p.nx, p.ny, p.dx, lam=1.0, limiter=V.LIM_LMP, precision=V.FP64, device=DEV)
-    with pytest.raises(V.VLBMError) as e:
+    s = V.VLBM(p.nx, p.ny, p.dx, bc=(1, 1, 0, 0), lam=1.0, limiter=V.LIM_LMP, precision=V.FP64, device=DEV)
+    with pytest.raises(V.VLBMError) as e:      # LMP with a boundary
+        s.adjoint(u0, 4, 2, s.adjoint_scratch(4, 2), u0=u0)
+    assert e.value.code == V.E_UNSUPPORTED
+    s.close()
+    s = V.VLBM(p.nx, p.ny, p.dx, limiter=V.LIM_RLMP, precision=V.FP64, device=DEV)
+    s.set_adjoint_mode(V.ADJOINT_DIFF_A)
+    with pytest.raises(V.VLBMError) as e:      # LMP with a differentiated dynamic a
         s.adjoint(u0, 4, 2, s.adjoint_scratch(4, 2), u0=u0)
     assert e.value.code == V.E_UNSUPPORTED
     s.close()
@@ -446,3 +452,33 @@ def test_adjoint_rejects_diff_a_with_prescribed_states():
     with pytest.raises(V.VLBMError):
         s.adjoint(u0.clone(), 4, 2, sc, u0=u0)
     s.close()
+
+
+@pytest.mark.parametrize("kernel", [V.KERNEL_SIMPLE, V.KERNEL_FUSED])
+@pytest.mark.parametrize("limiter", [V.LIM_LMP, V.LIM_RLMP])
+def test_adjoint_lmp_matches_autograd(limiter, kernel):
+    """LMP / RLMP (periodic, a held): the three-pass adjoint (faces, bounds, gather)
+    against autograd of the PyTorch restatement, FP64, on smooth waves where the
+    density bound is active on 240-310 faces per step."""
+    from tests.test_torch_reference import _waves
+    cons, dx = _waves(32)
+    n = cons.shape[1]
+    cfg = O.Config(n, n, (0, 0, 0, 0), limiter, 1.4, 0.5, 1e-16)
+    lam = 1.05 * O.max_speed(cfg, O.new_state(cons))
+    a = O.kinetic_speed(lam, 0.5)
+    st = O.run(cfg, cons, dx, nsteps=4, lam_fixed=lam)["state"]
+    _, dbg = O.step(cfg, st, a, debug=True)
+    assert (dbg["theta_x"] < 1.0).sum() + (dbg["theta_y"] < 1.0).sum() > 200
+    p = W.Problem("waves", n, n, dx, 0.0, 0.0, cons[0], cons[1], cons[2], cons[3])
+    w, tgt = _setup(p, 0.0)
+    nsteps, every = 16, 5
+    s = _solver(p, limiter, V.FP64, lam, kernel)
+    u0 = torch.tensor(cons, dtype=torch.float64, device=DEV)
+    uN, g = _adjoint(s, u0, nsteps, every, w, tgt)
+    assert s.monitors()["status"] == 0
+    s.close()
+    ref = O.run(cfg, cons, dx, nsteps=nsteps, lam_fixed=lam)["state"]
+    assert np.array_equal(uN.cpu().numpy(), ref[:4])
+    sN, g_ref = _autograd_gradient(cons, nsteps, a, limiter, w, tgt, 1e-16)
+    err = np.abs(g.cpu().numpy() - g_ref)
+    assert err.max() <= 1e-9 * np.abs(g_ref).max(), (err.max(), np.unravel_index(err.argmax(), err.shape))
