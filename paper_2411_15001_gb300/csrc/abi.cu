@@ -46,10 +46,9 @@ Layout make_layout(int nx, int ny, int elem) {
     L.buf_bytes = (size_t)L.plane * kNPlane * elem;
     L.ctl_offset = 2 * L.buf_bytes;
     L.desc_offset = L.ctl_offset + ((sizeof(DevCtl) + 255) / 256) * 256;
-    // descriptor block: InstDesc (512 B), BatchCtl (256 B), item table at the smallest chunk
-    const size_t strips = (nx + kFusedOut - 1) / kFusedOut;
-    const size_t items = strips * ((ny + kFusedMinChunk - 1) / kFusedMinChunk);
-    L.total = L.desc_offset + 512 + 256 + ((items * sizeof(int) + 255) / 256) * 256;
+    // descriptor block: InstDesc (512 B), BatchCtl (256 B), item table (bands of at
+    // least the smallest height)
+    L.total = L.desc_offset + 512 + 256 + ((max_items(nx, ny) * sizeof(WorkItem) + 255) / 256) * 256;
     return L;
 }
 }  // namespace vlbm
@@ -106,15 +105,11 @@ static void build_desc(vlbm_state *s) {
     d.ny = s->grid.ny;
     uniform_types(s->bd, d.bc);
     d.bd = s->bd;
-    d.strips = s->strips;
-    d.chunk = s->chunk;
-    d.item0 = 0;
     d.nitems = s->nitems;
     d.ctl = s->ctl;
     d.sponge = s->sponge;
     static_assert(sizeof(InstDesc<T>) <= 512, "descriptor block");
     s->desc_host.assign((unsigned char *)&d, (unsigned char *)&d + sizeof d);
-    s->items_host.assign(s->nitems, 0);
 }
 
 // Upload the descriptor, the item table and a zero work counter (stream-ordered;
@@ -126,7 +121,7 @@ static cudaError_t upload_desc(vlbm_state *s) {
                                     s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + 512, 0, sizeof(BatchCtl), s->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + 768, s->items_host.data(), s->items_host.size() * sizeof(int),
+        e = cudaMemcpyAsync(base + 768, s->items_host.data(), s->items_host.size() * sizeof(WorkItem),
                             cudaMemcpyHostToDevice, s->stream);
     return e;
 }
@@ -349,7 +344,6 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
     s->device = pa.device;
     {
         DeviceGuard g(s->device);
-        s->strips = (grid->nx + kFusedOut - 1) / kFusedOut;
         s->have_tmap = make_tmap(s);
         if (s->have_tmap) {
             int sms = 0;
@@ -357,12 +351,11 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
             const int per_sm = precision == VLBM_FP64 ? fused_occupancy<double>(limiter)
                                                       : fused_occupancy<float>(limiter);
             const long long ctas = (long long)per_sm * (sms > 0 ? sms : 1);
-            const long long rows = (long long)s->strips * grid->ny;
-            long long chunk = rows / (2 * ctas);
-            if (chunk < kFusedMinChunk) chunk = kFusedMinChunk;
-            if (chunk > kFusedMaxChunk) chunk = kFusedMaxChunk;
-            s->chunk = (int)chunk;
-            s->nitems = s->strips * ((grid->ny + s->chunk - 1) / s->chunk);
+            // guided bands of at most kFusedMaxChunk rows
+            long long work = (long long)((grid->nx + kFusedOut - 1) / kFusedOut) * grid->ny;
+            s->items_host.resize(max_items(grid->nx, grid->ny));
+            s->nitems = append_items(s->items_host.data(), 0, grid->nx, grid->ny, kFusedMaxChunk, true, work, ctas);
+            s->items_host.resize(s->nitems);
             s->fused_grid = (int)(ctas < s->nitems ? ctas : s->nitems);
             if (precision == VLBM_FP64) build_desc<double>(s);
             else build_desc<float>(s);

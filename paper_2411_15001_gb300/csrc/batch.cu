@@ -47,7 +47,7 @@ struct vlbm_batch {
     int chunk = 32, ctas_per_sm = 3, order = VLBM_ORDER_LPT;
     int nitems = 0;
     std::vector<unsigned char> desc_host;
-    std::vector<int> items_host;
+    std::vector<WorkItem> items_host;
     bool desc_dirty = true;
     // graph of kGraphSteps launches
     cudaGraph_t graph = nullptr;
@@ -87,8 +87,7 @@ static size_t plan_layout(vlbm_batch *b, int n, const vlbm_grid *grids, int elem
         b->L[i] = make_layout(grids[i].nx, grids[i].ny, elem);
         b->buf_off[i] = off;
         off += up256(2 * b->L[i].buf_bytes);
-        const size_t strips = (grids[i].nx + kFusedOut - 1) / kFusedOut;
-        items += strips * ((grids[i].ny + kFusedMinChunk - 1) / kFusedMinChunk);
+        items += max_items(grids[i].nx, grids[i].ny);
     }
     b->ctl_off = off;
     off += (size_t)n * kCtlStride;
@@ -98,7 +97,7 @@ static size_t plan_layout(vlbm_batch *b, int n, const vlbm_grid *grids, int elem
     off += 256;
     b->items_off = off;
     b->items_cap = items;
-    off += up256(items * sizeof(int));
+    off += up256(items * sizeof(WorkItem));
     return off;
 }
 
@@ -124,17 +123,25 @@ static StepArgs<T> inst_args(const vlbm_batch *b, int i) {
 }
 
 // Descriptors and the item table for the current chunk / order: grids in
-// longest-first order (LPT) or in index order; a grid's items strip-fastest.
+// longest-first order (LPT, GUIDED) or in index order; a grid's items
+// strip-fastest, in bands of `chunk` rows, or under GUIDED in bands of decreasing
+// height (at most `chunk`) sized from the work left in all grids.
 template <typename T>
 static void build_items(vlbm_batch *b) {
     std::vector<int> ord(b->n);
     std::iota(ord.begin(), ord.end(), 0);
-    if (b->order == VLBM_ORDER_LPT)
+    if (b->order == VLBM_ORDER_LPT || b->order == VLBM_ORDER_GUIDED)
         std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
             return (long long)b->grids[x].nx * b->grids[x].ny > (long long)b->grids[y].nx * b->grids[y].ny;
         });
     b->desc_host.assign((size_t)b->n * kDescStride, 0);
-    b->items_host.clear();
+    b->items_host.resize(b->items_cap);
+    const bool guided = b->order == VLBM_ORDER_GUIDED;
+    long long work = 0;
+    for (int i = 0; i < b->n; ++i)
+        work += (long long)((b->grids[i].nx + kFusedOut - 1) / kFusedOut) * b->grids[i].ny;
+    const long long ctas = (long long)b->ctas_per_sm * b->sms;
+    size_t used = 0;
     for (int i : ord) {
         InstDesc<T> d;
         memset(&d, 0, sizeof d);
@@ -148,16 +155,14 @@ static void build_items(vlbm_batch *b) {
         d.ny = A.ny;
         for (int k = 0; k < 4; ++k) d.bc[k] = A.bc[k];
         d.bd = A.bd;
-        d.strips = (A.nx + kFusedOut - 1) / kFusedOut;
-        d.chunk = b->chunk;
-        d.item0 = (int)b->items_host.size();
-        d.nitems = d.strips * ((A.ny + b->chunk - 1) / b->chunk);
+        d.nitems = append_items(b->items_host.data() + used, i, A.nx, A.ny, b->chunk, guided, work, ctas);
+        used += d.nitems;
         d.ctl = A.ctl;
         d.sponge = A.sponge;
-        for (int q = 0; q < d.nitems; ++q) b->items_host.push_back(i);
         memcpy(&b->desc_host[(size_t)i * kDescStride], &d, sizeof d);
     }
-    b->nitems = (int)b->items_host.size();
+    b->items_host.resize(used);
+    b->nitems = (int)used;
     b->desc_dirty = true;
 }
 
@@ -167,7 +172,7 @@ static cudaError_t upload(vlbm_batch *b) {
     cudaError_t e = cudaMemcpyAsync(base + b->desc_off, b->desc_host.data(), b->desc_host.size(),
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + b->items_off, b->items_host.data(), b->items_host.size() * sizeof(int),
+        e = cudaMemcpyAsync(base + b->items_off, b->items_host.data(), b->items_host.size() * sizeof(WorkItem),
                             cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + b->bctl_off, 0, sizeof(BatchCtl), b->stream);
     // the host copies must outlive the copies: wait for them
@@ -181,7 +186,7 @@ static FusedBatchArgs<T> batch_args(const vlbm_batch *b) {
     FusedBatchArgs<T> B;
     char *base = (char *)b->ws;
     B.insts = (const InstDesc<T> *)(base + b->desc_off);
-    B.item_inst = (const int *)(base + b->items_off);
+    B.items = (const WorkItem *)(base + b->items_off);
     B.nitems = b->nitems;
     B.bctl = (BatchCtl *)(base + b->bctl_off);
     B.gamma = b->gamma;
@@ -456,7 +461,7 @@ int vlbm_batch_get_tuning(const vlbm_batch *b, vlbm_batch_tuning *t) {
 int vlbm_batch_set_tuning(vlbm_batch *b, const vlbm_batch_tuning *t) {
     if (!b || !t) return bfail(b, VLBM_E_INVAL, "bad argument");
     if (t->chunk < kFusedMinChunk || t->chunk > 256 || t->ctas_per_sm < 1 || t->ctas_per_sm > 4 ||
-        (t->order != VLBM_ORDER_LPT && t->order != VLBM_ORDER_INDEX))
+        (t->order != VLBM_ORDER_LPT && t->order != VLBM_ORDER_INDEX && t->order != VLBM_ORDER_GUIDED))
         return bfail(b, VLBM_E_INVAL, "tuning out of range");
     const int maxc = b->precision == VLBM_FP64 ? fused_occupancy<double>(b->limiter)
                                                : fused_occupancy<float>(b->limiter);
@@ -475,7 +480,7 @@ int vlbm_batch_autotune(vlbm_batch *b, int32_t trial_steps, vlbm_batch_tuning *b
     const int maxc = b->precision == VLBM_FP64 ? fused_occupancy<double>(b->limiter)
                                                : fused_occupancy<float>(b->limiter);
     const int chunks[] = {16, 32, 64, 128};
-    const int orders[] = {VLBM_ORDER_LPT, VLBM_ORDER_INDEX};
+    const int orders[] = {VLBM_ORDER_LPT, VLBM_ORDER_INDEX, VLBM_ORDER_GUIDED};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bfail(b, VLBM_E_CUDA, "event creation failed");

@@ -22,9 +22,9 @@ struct vlbm_state {
     int device;
     CUtensorMap tmap;   // 3D view [40 planes][rows][pitch] of both state buffers
     bool have_tmap;
-    int strips, chunk, nitems, fused_grid;
+    int nitems, fused_grid;
     std::vector<unsigned char> desc_host;   // InstDesc<T> of this grid
-    std::vector<int> items_host;            // item -> grid (all 0)
+    std::vector<vlbm::WorkItem> items_host;  // work items in launch order (guided bands)
     bool profiling;
     std::vector<cudaEvent_t> ev;   // event pairs of timed launches
     size_t ev_used;
@@ -102,7 +102,7 @@ inline FusedBatchArgs<T> batch_args_of(const vlbm_state *s) {
     char *base = (char *)s->ws + s->L.desc_offset;
     B.insts = (const InstDesc<T> *)base;
     B.bctl = (BatchCtl *)(base + 512);
-    B.item_inst = (const int *)(base + 768);
+    B.items = (const WorkItem *)(base + 768);
     B.nitems = s->nitems;
     B.gamma = s->gamma;
     B.alpha = s->alpha;

@@ -2,8 +2,9 @@
 // row-marching pass: every cell's 20 values are read from HBM once and written
 // once, together with the ghost images of the boundary cells.
 //
-// Work. A grid is cut into strips of kFOut = 120 output columns and chunks of
-// `chunk` rows; a work item is one (instance, strip, chunk). Persistent CTAs of
+// Work. A grid is cut into strips of kFOut = 120 output columns and bands of
+// rows; a work item is one (instance, strip, band), listed by the host in the
+// order CTAs take them (tall bands first under guided scheduling). Persistent CTAs of
 // kFB = 128 threads (one column each: four halo columns on either side of the
 // strip) take items from a global counter, so items that cost more (faces whose
 // theta_p needs the FP64 solve cluster on shocks) do not hold up the step. One
@@ -181,10 +182,8 @@ struct FusedCtx {
         rsy_prev = mu2 = nu2 = thy_prev = T(0);
     }
 
-    // One row iteration; returns false if a wait timed out (the CTA then stops).
-    __device__ __forceinline__ bool row(int R) {
-        Hist<T> h0;
-        // ---------------------------------------------------------------- P1
+    // P1 of row R (see the file comment); returns rho* of the y-face R - 1/2.
+    __device__ __forceinline__ T p1(int R, Hist<T> &h0) {
         const int slot = nconsumed % kRawSlots;
         const uint32_t par = (nconsumed / kRawSlots) & 1u;
         ++nconsumed;
@@ -209,7 +208,66 @@ struct FusedCtx {
             S.X[xs][8 + q][b] = d1;
             S.X[xs][12 + q][b] = d2;
         }
-        const T rsy_new = face_star(h1.u[0], h1.g[0], u[0], g[0], k);  // y-face R - 1/2
+        return face_star(h1.u[0], h1.g[0], u[0], g[0], k);  // y-face R - 1/2
+    }
+
+    // Face states of the x-face (b, b+1) of row R and of the y-face R - 1/2 (PP and
+    // the fixed thetas), for theta in the next row.
+    __device__ __forceinline__ void next_faces(int R, const Hist<T> &h0, T rsy_new, int br) {
+        const int xs = R & 3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            xs_us[q] = face_star(S.X[xs][q][b], S.X[xs][4 + q][b], S.X[xs][q][br], S.X[xs][4 + q][br], k);
+            xs_df[q] = face_dflux(S.X[xs][8 + q][b], S.X[xs][12 + q][br], k);
+            ys_us[q] = q == 0 ? rsy_new : face_star(h1.u[q], h1.g[q], h0.u[q], h0.g[q], k);
+            ys_df[q] = face_dflux(h1.d3[q], h0.d4[q], k);
+        }
+    }
+
+    // LMP density bounds (eq. LMP_minmax) of row R - 1, own column: rho of the cell
+    // and rho* of its four faces.
+    __device__ __forceinline__ void bounds(int R, T rsy_new, int bl, T &mu, T &nu) const {
+        const int rp = (R - 1) & 1;
+        const T v0 = h1.u[0], v1 = S.rsx[rp][bl], v2 = S.rsx[rp][b];
+        mu = fmin(fmin(fmin(v0, v1), fmin(v2, rsy_prev)), rsy_new);
+        nu = fmax(fmax(fmax(v0, v1), fmax(v2, rsy_prev)), rsy_new);
+        if (LIM == VLBM_LIM_RLMP) {  // Sec. 3.3.2
+            mu = RN<T>::mul(mu, T(0.999));
+            nu = RN<T>::mul(nu, T(1.001));
+        }
+    }
+
+    // The rows of an item before row y0 + 1: no output row of the item uses their
+    // thetas (x-faces below row y0, y-faces below y0 - 1/2) or their collide (rows
+    // below y0 - 1), so they only load the row and form what the next rows read --
+    // the face states (PP and the fixed thetas) or rho* of the x-faces and, in row
+    // y0, the bounds of row y0 - 1 (LMP / RLMP).
+    __device__ __forceinline__ bool row_warm(int R) {
+        Hist<T> h0;
+        const T rsy_new = p1(R, h0);
+        __syncthreads();                                                  // S1
+        if (S.abort) return false;
+        if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
+        const int bl = b > 0 ? b - 1 : 0, br = b < kFB - 1 ? b + 1 : b;
+        if constexpr (kRecompute) {
+            bounds(R, rsy_new, bl, mu2, nu2);
+            const int xs = R & 3;
+            S.rsx[R & 1][b] = face_star(h0.u[0], S.X[xs][4][b], S.X[xs][0][br], S.X[xs][4][br], k);
+        } else {
+            next_faces(R, h0, rsy_new, br);
+        }
+        rsy_prev = rsy_new;
+        h2 = h1;
+        h1 = h0;
+        return true;
+    }
+
+    // One row iteration; returns false if a wait timed out (the CTA then stops).
+    __device__ __forceinline__ bool row(int R) {
+        Hist<T> h0;
+        // ---------------------------------------------------------------- P1
+        const T rsy_new = p1(R, h0);
+        const int xs = R & 3;
         __syncthreads();                                                  // S1
         if (S.abort) return false;
         if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
@@ -219,13 +277,7 @@ struct FusedCtx {
         T mu1 = T(0), nu1 = T(0);
         if (LIM == VLBM_LIM_LMP || LIM == VLBM_LIM_RLMP) {
             const int rp = (R - 1) & 1;
-            const T v0 = h1.u[0], v1 = S.rsx[rp][bl], v2 = S.rsx[rp][b];
-            mu1 = fmin(fmin(fmin(v0, v1), fmin(v2, rsy_prev)), rsy_new);
-            nu1 = fmax(fmax(fmax(v0, v1), fmax(v2, rsy_prev)), rsy_new);
-            if (LIM == VLBM_LIM_RLMP) {  // Sec. 3.3.2
-                mu1 = RN<T>::mul(mu1, T(0.999));
-                nu1 = RN<T>::mul(nu1, T(1.001));
-            }
+            bounds(R, rsy_new, bl, mu1, nu1);
             S.mu[rp][b] = mu1;
             S.nu[rp][b] = nu1;
             __syncthreads();                                              // S2
@@ -285,15 +337,7 @@ struct FusedCtx {
             // rho* of the x-face (b, b+1) of row R, for the next row's density bounds
             S.rsx[R & 1][b] = face_star(h0.u[0], S.X[xs][4][b], S.X[xs][0][br], S.X[xs][4][br], k);
         } else {
-            // new x-face (b, b+1) of row R and y-face R - 1/2
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                xs_us[q] = face_star(S.X[xs][q][b], S.X[xs][4 + q][b], S.X[xs][q][br], S.X[xs][4 + q][br], k);
-                xs_df[q] = face_dflux(S.X[xs][8 + q][b], S.X[xs][12 + q][br], k);
-                ys_us[q] = q == 0 ? rsy_new : face_star(h1.u[q], h1.g[q], h0.u[q], h0.g[q], k);
-                ys_df[q] = face_dflux(h1.d3[q], h0.d4[q], k);
-            }
-            S.rsx[R & 1][b] = xs_us[0];
+            next_faces(R, h0, rsy_new, br);
         }
         rsy_prev = rsy_new;
         // No barrier before P4: it reads theta of row R-2's x-faces (written by the
@@ -374,7 +418,8 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         const int item = S.item;
         __syncthreads();
         if (item >= B.nitems) break;
-        const InstDesc<T> &D = B.insts[B.item_inst[item]];
+        const WorkItem it = B.items[item];
+        const InstDesc<T> &D = B.insts[it.inst];
         DevCtl *C = D.ctl;
         if (C->done) continue;
         Geo geo;
@@ -386,23 +431,25 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         geo.sponge = D.sponge;
         const long long n = C->n;
         const StepConsts<T> k = consts_of<T>(C);
-        const int local = item - D.item0;
-        const int s = local % D.strips, ch = local / D.strips;
         Monitor<T> mon;
         mon.init();
         FusedCtx<T, LIM> X{S, &D.tmap, geo, k, (n & 1) ? D.buf0 : D.buf1, mon, b, (n & 1) ? kNPlane : 0,
                            nissued, nconsumed};
-        X.y0 = ch * D.chunk;
-        X.y1 = X.y0 + D.chunk < D.ny ? X.y0 + D.chunk : D.ny;
-        X.xb = kFOut * s - kFHalo;
+        X.y0 = it.y0;
+        X.y1 = it.y1;
+        X.xb = kFOut * it.strip - kFHalo;
         X.xpad = X.xb + kOX;
         X.c = X.xb + b;
-        const int R0 = X.y0 - 2;
+        // LMP / RLMP start at row y0 - 2 (the bounds of row y0 - 1 need rho* of the
+        // y-face y0 - 3/2), the others at y0 - 1
+        const int R0 = X.y0 - (FusedCtx<T, LIM>::kRecompute ? 2 : 1);
         X.R1 = X.y1 + 1;
         if (b == 0)
             for (int r = R0; r < R0 + kRawSlots && r <= X.R1; ++r) X.issue(r);
         X.reset_state();
-        for (int R = R0; R <= X.R1 && ok; ++R) ok = X.row(R);
+        int R = R0;
+        for (; R < X.y0 + 1 && ok; ++R) ok = X.row_warm(R);
+        for (; R <= X.R1 && ok; ++R) ok = X.row(R);
         if (!ok) break;
         // the item's monitors go to its grid; the CTA finishing the grid's last item
         // ends that grid's step

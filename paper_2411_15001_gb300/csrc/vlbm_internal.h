@@ -156,8 +156,7 @@ struct alignas(256) InstDesc {
     long long plane;
     int pitch, nx, ny;
     int bc[4];
-    int strips, chunk;    // strips of 120 columns, chunks of `chunk` rows
-    int item0, nitems;    // this grid's work items in the launch
+    int nitems;           // this grid's work items in the launch
     DevCtl *ctl;
     int sponge;           // width of the theta = 0 layer at zero-gradient sides (Sec. 4.2)
     Bound bd;             // split sides and the prescribed field
@@ -193,10 +192,16 @@ struct BatchCtl {
     unsigned int work, ctas_done;
 };
 
+// One work item of the row-marching kernel: rows [y0, y1) of strip `strip`
+// (output columns 120 strip .. 120 strip + 119) of grid `inst`.
+struct alignas(16) WorkItem {
+    int inst, strip, y0, y1;
+};
+
 template <typename T>
 struct FusedBatchArgs {
     const InstDesc<T> *insts;
-    const int *item_inst;  // grid of every work item
+    const WorkItem *items;  // in the order the CTAs take them
     int nitems;
     BatchCtl *bctl;
     double gamma, alpha, eps;
@@ -244,7 +249,43 @@ bool encode_state_tmap(CUtensorMap *out, void *base, const Layout &L);
 constexpr int kFusedOut = 120;                             // output columns per strip
 constexpr int kFusedBox = 128;                             // TMA box width (columns)
 constexpr int kFusedMinChunk = 16;                         // rows per work item, bounds
-constexpr int kFusedMaxChunk = 64;
+constexpr int kFusedMaxChunk = 128;
+
+// Work items of one grid appended to `out`, strip-fastest within each band of
+// rows. Uniform order: bands of `hmax` rows. Guided order (guided self-scheduling,
+// Polychronopoulos & Kuck 1987): each band is as high as the work left -- strip-rows
+// of this grid and of the grids after it, `work_left`, which the call decreases --
+// divided by the CTA count, within [kFusedMinChunk, hmax]: the first items are
+// tall (few repeated halo rows), the last ones short (a CTA taking one near the end
+// of the step finishes soon after the others). Measured on the 4096^2 blast (3 CTAs
+// x 152 SMs): 6.6 % faster than the best uniform height; work left / (2 x CTAs) and
+// minimum heights of 8-32 rows were within 2.5 % of it.
+inline int append_items(WorkItem *out, int inst, int nx, int ny, int hmax, bool guided,
+                        long long &work_left, long long ctas) {
+    const int strips = (nx + kFusedOut - 1) / kFusedOut;
+    int n = 0;
+    for (int y = 0; y < ny;) {
+        long long h = hmax;
+        if (guided) {
+            h = work_left / (ctas > 0 ? ctas : 1);
+            if (h < kFusedMinChunk) h = kFusedMinChunk;
+            if (h > hmax) h = hmax;
+        }
+        if (h > ny - y) h = ny - y;
+        for (int s = 0; s < strips; ++s) {
+            if (out) out[n] = WorkItem{inst, s, y, y + (int)h};
+            ++n;
+        }
+        work_left -= (long long)strips * h;
+        y += (int)h;
+    }
+    return n;
+}
+// Upper bound of append_items' count for any order with hmax >= kFusedMinChunk.
+inline size_t max_items(int nx, int ny) {
+    const size_t strips = (nx + kFusedOut - 1) / kFusedOut;
+    return strips * ((ny + kFusedMinChunk - 1) / kFusedMinChunk + 1);
+}
 template <typename T> cudaError_t launch_moments(const StepArgs<T> &a, T *rho, T *mom, T *E,
                                                  cudaStream_t s);
 template <typename T> cudaError_t launch_save(const StepArgs<T> &a, void *dst, cudaStream_t s);

@@ -92,7 +92,7 @@ class vlbm_batch_tuning(ctypes.Structure):
                 ("items", ctypes.c_int32), ("ctas", ctypes.c_int32)]
 
 
-ORDER_LPT, ORDER_INDEX = 0, 1
+ORDER_LPT, ORDER_INDEX, ORDER_GUIDED = 0, 1, 2
 
 
 class VLBMError(RuntimeError):
