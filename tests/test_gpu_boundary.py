@@ -158,11 +158,16 @@ def test_noalloc_rejects_a_boundary():
 R = 4
 
 
-def _sampled_step(s, p, lim, cells, tol=1e-4):
+def _sampled_step(s, p, lim, cells, tol=1e-4, jitter=0):
     """One more GPU step checked on 9 x 9 interior patches against the oracle, each
     plane's error relative to its largest magnitude in the patch, or 1e-3 of its
     largest in the grid where that is bigger (the momentum of gas at rest is
-    rounding noise, no scale)."""
+    rounding noise, no scale). With jitter = k > 0 a cell's bound is also at least
+    4x the largest change of the oracle's result under k seeded relative
+    perturbations of the patch by up to 2^-22 (the few units in the last place by
+    which a float evaluation of the face quantities can differ from the double
+    one): where the step's outcome depends on a branch that float-level changes
+    flip, this is how far a float evaluation may land from the double one."""
     before = s.state_planes().cpu().numpy()
     a = s.monitors()["a"]
     s.step(1)
@@ -170,12 +175,17 @@ def _sampled_step(s, p, lim, cells, tol=1e-4):
     n = 2 * R + 1
     cfg = O.Config(n, n, (1, 1, 1, 1), lim, p.gamma, 0.5, 1e-16)
     floor = 1e-3 * np.abs(before).reshape(20, -1).max(axis=1).astype(np.float64)
+    rng = np.random.default_rng(17)
     for (j, i) in cells:
         patch = np.ascontiguousarray(before[:, j - R:j + R + 1, i - R:i + R + 1], dtype=np.float64)
         ref = O.step(cfg, patch, a)[:, R, R]
-        scale = np.maximum(np.abs(patch).reshape(20, -1).max(axis=1), floor)
-        err = float((np.abs(after[:, j, i] - ref) / np.maximum(scale, 1e-300)).max())
-        assert err <= tol, (j, i, err)
+        scale = np.maximum(np.maximum(np.abs(patch).reshape(20, -1).max(axis=1), floor), 1e-300)
+        bound = tol
+        for _ in range(jitter):
+            pj = patch * (1.0 + 2.0 ** -22 * rng.uniform(-1.0, 1.0, patch.shape))
+            bound = max(bound, 4.0 * float((np.abs(O.step(cfg, pj, a)[:, R, R] - ref) / scale).max()))
+        err = float((np.abs(after[:, j, i] - ref) / scale).max())
+        assert err <= bound, (j, i, err, bound)
 
 
 def _cells(before, nsample, seed):
@@ -198,9 +208,11 @@ def test_double_mach_reflection_paper_grid(lim):
     m = s.monitors()
     assert m["status"] == 0 and m["first_bad_step"] == -1
     before = s.state_planes().cpu().numpy()
-    # LMP's theta_rho jumps where dF^rho changes sign: on the Mach stem a float and a
-    # double evaluation of the same face can land on either side (measured 4.2e-4)
-    _sampled_step(s, p, lim, _cells(before, 60, 3), tol=1e-3 if lim == V.LIM_LMP else 1e-4)
+    # LMP's theta_rho jumps where dF^rho changes sign (the cases of Sec. 3.3.1): on
+    # the Mach stem a float and a double evaluation of the same face can land on
+    # either side (measured 4.2e-4 and 1.3e-3 of the patch scale at two states), so
+    # each cell is held to the oracle's own spread under float-level input changes
+    _sampled_step(s, p, lim, _cells(before, 60, 3), tol=1e-4, jitter=8)
     s.close()
 
 
