@@ -138,3 +138,80 @@ def test_lmp_restatement_matches_oracle_theta_and_differences(lim):
         fd = (4.0 * (L(h) - L(-h)) / (2 * h) - (L(2 * h) - L(-2 * h)) / (4 * h)) / 3.0
         ad = float((g * d).sum())
         assert abs(fd - ad) <= 1e-6 * abs(ad), (k, fd, ad)
+
+
+def boxed_waves(case, nx=24, ny=20):
+    """Smooth waves (nowhere flat) in a box with the sides of `case`: zero-gradient
+    and mirror walls ("zg-mirror"); zero-gradient sides with a 3-cell sponge layer,
+    periodic in y ("sponge"); prescribed states on two sides and a south side that
+    switches from mirror to zero gradient at column 15 ("dirichlet-split").
+    Returns (oracle Config without limiter, conserved fields, dx, boundary kwargs)."""
+    dx = 1.0 / nx
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * dx, (np.arange(ny) + 0.5) * dx)
+    rho = 1.0 + 0.3 * np.sin(2 * np.pi * X + 0.4) * np.cos(2 * np.pi * Y + 0.7) + 0.1 * np.sin(4 * np.pi * (X + 2 * Y))
+    v1 = 0.4 * np.cos(2 * np.pi * Y + 0.2)
+    v2 = 0.3 * np.sin(2 * np.pi * X + 1.1)
+    p = 1.0 + 0.2 * np.cos(2 * np.pi * (X - Y))
+    cons = np.stack(W.primitive_to_conserved(rho, v1, v2, p))
+    kw = {"bc": (1, 1, 2, 2), "sponge": 0}
+    if case == "sponge":
+        kw = {"bc": (1, 1, 0, 0), "sponge": 3}
+    elif case == "dirichlet-split":
+        st = W._conserved_state(1.0, 0.3, 0.15, 1.0, 1.4)
+        kw = {"bc": (3, 1, 2, 3), "sponge": 0, "bc_hi": (3, 1, 1, 3), "split": (0, 0, 15, 0),
+              "field": O.Field(st, st, ())}
+    return cons, dx, kw
+
+
+def _box_cfg(nx, ny, lim, kw, dx):
+    return O.Config(nx, ny, kw["bc"], lim, 1.4, 0.5, 1e-16, kw["sponge"], bc_hi=kw.get("bc_hi"),
+                    split=kw.get("split", (0, 0, 0, 0)), dx=dx, field=kw.get("field"))
+
+
+@pytest.mark.parametrize("case", ["zg-mirror", "sponge", "dirichlet-split"])
+def test_frame_restatement_matches_oracle_step(case):
+    """The step inside the oracle's ghost frame (gathered from the oracle's own fill)
+    equals the oracle's step for every limiter."""
+    cons, dx, kw = boxed_waves(case)
+    ny, nx = cons.shape[1:]
+    for lim in range(5):
+        cfg = _box_cfg(nx, ny, lim, kw, dx)
+        lam = 1.05 * O.max_speed(cfg, O.new_state(cons))
+        a = O.kinetic_speed(lam, 0.5)
+        st = O.run(cfg, cons, dx, nsteps=3, lam_fixed=lam)["state"]
+        fr = TR.ghost_frame(cfg, a, sponge=kw["sponge"])
+        got = TR.step_frame(torch.tensor(st), a, lim, fr).numpy()
+        ref = O.step(cfg, st, a)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (case, lim)
+
+
+@pytest.mark.parametrize("case", ["zg-mirror", "dirichlet-split"])
+def test_frame_restatement_gradient_matches_differences(case):
+    """LMP in a box: autograd through the frame restatement equals Richardson central
+    differences of the oracle's run along random directions, with the density bound
+    active on boundary faces."""
+    cons, dx, kw = boxed_waves(case)
+    ny, nx = cons.shape[1:]
+    lim = O.LIM_LMP
+    cfg = _box_cfg(nx, ny, lim, kw, dx)
+    lam = 1.05 * O.max_speed(cfg, O.new_state(cons))
+    a = O.kinetic_speed(lam, 0.5)
+    _, dbg = O.step(cfg, O.run(cfg, cons, dx, nsteps=3, lam_fixed=lam)["state"], a, debug=True)
+    assert (dbg["theta_x"] < 1.0).sum() + (dbg["theta_y"] < 1.0).sum() > 60
+    fr = TR.ghost_frame(cfg, a)
+    nsteps = 6
+    rng = np.random.default_rng(8)
+    w = rng.uniform(0.5, 1.5, size=(4, ny, nx))
+    u0 = torch.tensor(cons, requires_grad=True)
+    (torch.tensor(w) * TR.rollout_frame(u0, nsteps, a, lim, fr)[:4]).sum().backward()
+    g = u0.grad.numpy()
+    for k in range(3):
+        d = rng.standard_normal((4, ny, nx)) * np.abs(cons) * 1e-2
+        h = 1e-5
+
+        def L(x):
+            return float((w * O.run(cfg, cons + x * d, dx, nsteps=nsteps, lam_fixed=lam)["state"][:4]).sum())
+
+        fd = (4.0 * (L(h) - L(-h)) / (2 * h) - (L(2 * h) - L(-2 * h)) / (4 * h)) / 3.0
+        ad = float((g * d).sum())
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (k, fd, ad)

@@ -1,5 +1,6 @@
-"""Plain PyTorch FP64 restatement of one blended step on a fully periodic grid,
-for differentiating the scheme with autograd (test infrastructure only).
+"""Plain PyTorch FP64 restatement of one blended step, on a fully periodic grid or
+(step_frame) inside a two-layer ghost frame, for differentiating the scheme with
+autograd (test infrastructure only).
 
 It follows the same equations as the oracle -- Maxwellians of the D2Q5 example
 (Sec. 2), face states u* (eq. D2Q5_convexproof_3) and dF (eq. 2nd-order_flux),
@@ -115,6 +116,14 @@ def step(s, a, limiter, alpha=0.5, gamma=1.4, eps=1e-16):
     faces (eq. LMP_minmax), in the order rho, west, east, south, north (the gradient
     of a min goes to the first place it is reached); RLMP scales them by 0.999 and
     1.001 (Sec. 3.3.2)."""
+    return _core(s, a, limiter, alpha, gamma, eps)
+
+
+def _core(s, a, limiter, alpha, gamma, eps, sponge_x=None, sponge_y=None):
+    """The step on an array whose neighbours are taken with torch.roll: the whole
+    grid when it is periodic, or a grid padded with its ghost frame, where the
+    values rolled in at the outer edge reach no cell more than two cells inside it
+    (the stencil's radius). sponge_x / sponge_y: faces forced to theta = 0."""
     u, P1, P2, P3, P4 = s[0:4], s[4:8], s[8:12], s[12:16], s[16:20]
     f, g = fluxes(u, gamma)
     w = (1.0 - alpha) / 4.0
@@ -148,6 +157,9 @@ def step(s, a, limiter, alpha=0.5, gamma=1.4, eps=1e-16):
             mu, nu = 0.999 * mu, 1.001 * nu
         tx = theta_lmp(us_x, df_x, mu, nu, E(mu), E(nu), kappa, eps)
         ty = theta_lmp(us_y, df_y, mu, nu, N(mu), N(nu), kappa, eps)
+    if sponge_x is not None:
+        tx = torch.where(sponge_x, torch.zeros_like(tx), tx)
+        ty = torch.where(sponge_y, torch.zeros_like(ty), ty)
     tE, tW, tN, tS = tx, Wr(tx), ty, Sr(ty)
     P1n = Wr(M1 + tE * d1)          # pulled from the west cell across its east face
     P2n = E(M2 + tW * d2)           # pulled from the east cell across its west face
@@ -181,4 +193,52 @@ def rollout_dynamic(u0, nsteps, limiter, alpha=0.5, gamma=1.4, eps=1e-16):
     for _ in range(nsteps):
         s = step(s, a, limiter, alpha, gamma, eps)
         a = 2.0 * speed_max(s[0:4], gamma) / (1.0 - alpha)
+    return s
+
+
+def ghost_frame(cfg, a, t=0.0, sponge=0):
+    """The oracle's ghost fill (two layers, x rule then y rule) as a gather: every
+    entry of the padded (20, ny + 4, nx + 4) array is sign x one state entry, or a
+    constant (a prescribed state's value, which does not depend on the state). The
+    map is read off the oracle by filling a state whose entries are distinct codes
+    (and twice those codes: a constant does not change). With sponge = w > 0, the
+    faces with theta = 0 of the sponge layer (Sec. 4.2: every face of a cell within
+    w cells of a zero-gradient side, ghost cells included; sides of one type)."""
+    import numpy as np
+
+    from oracle import oracle as O
+
+    nx, ny = cfg.nx, cfg.ny
+    code = (np.arange(20 * ny * nx, dtype=np.float64) + 1.0).reshape(20, ny, nx)
+    e1 = O.fill_ghosts(cfg, code, a, t)
+    e2 = O.fill_ghosts(cfg, 2.0 * code, a, t)
+    const = e2 == e1
+    lin = ~const
+    if not np.array_equal(e2[lin], 2.0 * e1[lin]):
+        raise ValueError("ghost fill is not a signed copy")
+    frame = {"src": torch.tensor(np.where(lin, np.abs(e1) - 1.0, 0.0).astype(np.int64)),
+             "sign": torch.tensor(np.where(lin, np.sign(e1), 0.0)),
+             "cval": torch.tensor(np.where(const, e1, 0.0))}
+    if sponge > 0:
+        I, J = np.meshgrid(np.arange(-2, nx + 2), np.arange(-2, ny + 2))
+        zg = [b == 1 for b in cfg.bc]
+        m = (zg[0] & (I < sponge)) | (zg[1] & (I >= nx - sponge)) | (zg[2] & (J < sponge)) | \
+            (zg[3] & (J >= ny - sponge))
+        frame["sponge_x"] = torch.tensor(m | np.roll(m, -1, axis=1))
+        frame["sponge_y"] = torch.tensor(m | np.roll(m, -1, axis=0))
+    return frame
+
+
+def step_frame(s, a, limiter, frame, alpha=0.5, gamma=1.4, eps=1e-16):
+    """One step of a grid with a boundary: the ghost frame gathered from s, the step
+    on the padded array, its interior returned."""
+    P = frame["sign"] * s.reshape(-1)[frame["src"]] + frame["cval"]
+    out = _core(P, a, limiter, alpha, gamma, eps, frame.get("sponge_x"), frame.get("sponge_y"))
+    return out[:, 2:-2, 2:-2]
+
+
+def rollout_frame(u0, nsteps, a, limiter, frame, alpha=0.5, gamma=1.4, eps=1e-16):
+    s = init_populations(u0, a, alpha, gamma)
+    for _ in range(nsteps):
+        s = step_frame(s, a, limiter, frame, alpha, gamma, eps)
     return s
