@@ -41,18 +41,31 @@ static cudaError_t launch_adjoint_step_da(const AdjArgs<T> &A, int limiter, cuda
         case VLBM_LIM_PP: k_adjoint_step<T, VLBM_LIM_PP, DA, EXT><<<grd, blk, 0, s>>>(A); break;
         case VLBM_LIM_LMP:
         case VLBM_LIM_RLMP:
-            if constexpr (!DA && !EXT) {   // periodic grids, a^n held: passes 1, 2, then the gather
-                const size_t N = (size_t)A.nx * A.ny;
-                cudaError_t e = cudaMemsetAsync(A.lmp + kLmub * N, 0, 3 * N * sizeof(T), s);
+            if constexpr (!DA) {   // a^n held: passes 1, 2, then the gather (and the outer ring)
+                // faces of cells 0 .. n - 1 (periodic) or -1 .. n - 1 (boundary); bounds and
+                // the gather over the cells of the step (with the first ghost layer)
+                const dim3 gf((A.nx + (EXT ? 1 : 0) + 31) / 32, (A.ny + (EXT ? 1 : 0) + 7) / 8);
+                cudaError_t e;
+                if (EXT) {   // every plane: the bounds pass adds into faces pass 1 does not write
+                    const size_t NL = (size_t)(A.nx + 4) * (A.ny + 4);
+                    e = cudaMemsetAsync(A.lmp, 0, kLPlanes * NL * sizeof(T), s);
+                } else {
+                    const size_t N = (size_t)A.nx * A.ny;
+                    e = cudaMemsetAsync(A.lmp + kLmub * N, 0, 3 * N * sizeof(T), s);
+                }
                 if (e != cudaSuccess) return e;
                 if (limiter == VLBM_LIM_LMP) {
-                    k_adj_lmp_faces<T, VLBM_LIM_LMP><<<grd, blk, 0, s>>>(A);
-                    k_adj_lmp_bounds<T, VLBM_LIM_LMP><<<grd, blk, 0, s>>>(A);
-                    k_adjoint_step<T, VLBM_LIM_LMP, false, false><<<grd, blk, 0, s>>>(A);
+                    k_adj_lmp_faces<T, VLBM_LIM_LMP, EXT><<<gf, blk, 0, s>>>(A);
+                    k_adj_lmp_bounds<T, VLBM_LIM_LMP, EXT><<<grd, blk, 0, s>>>(A);
+                    k_adjoint_step<T, VLBM_LIM_LMP, false, EXT><<<grd, blk, 0, s>>>(A);
                 } else {
-                    k_adj_lmp_faces<T, VLBM_LIM_RLMP><<<grd, blk, 0, s>>>(A);
-                    k_adj_lmp_bounds<T, VLBM_LIM_RLMP><<<grd, blk, 0, s>>>(A);
-                    k_adjoint_step<T, VLBM_LIM_RLMP, false, false><<<grd, blk, 0, s>>>(A);
+                    k_adj_lmp_faces<T, VLBM_LIM_RLMP, EXT><<<gf, blk, 0, s>>>(A);
+                    k_adj_lmp_bounds<T, VLBM_LIM_RLMP, EXT><<<grd, blk, 0, s>>>(A);
+                    k_adjoint_step<T, VLBM_LIM_RLMP, false, EXT><<<grd, blk, 0, s>>>(A);
+                }
+                if (EXT) {
+                    const int ring = 2 * (A.nx + 4) + 2 * (A.ny + 2);
+                    k_adj_lmp_ring<T><<<(ring + 255) / 256, 256, 0, s>>>(A);
                 }
                 break;
             }
@@ -79,16 +92,17 @@ static cudaError_t launch_adjoint_init(const T *init_state, const Layout &L, con
     return cudaGetLastError();
 }
 
-// Transpose of the ghost fill on the padded cotangent, then its interior into cot.
+// Transpose of the ghost fill on the padded cotangent (np ghost layers), then its
+// interior into cot.
 template <typename T>
-static cudaError_t fold_ghosts(T *pad, const vlbm_state *s, T *cot, cudaStream_t st) {
+static cudaError_t fold_ghosts(T *pad, int np, const vlbm_state *s, T *cot, cudaStream_t st) {
     int bc[4];
     uniform_types(s->bd, bc);
     const int nx = s->grid.nx, ny = s->grid.ny;
-    k_adjoint_fold_y<T><<<(2 * (nx + 2) + 127) / 128, 128, 0, st>>>(pad, nx, ny, s->bd, bc[2], bc[3]);
-    k_adjoint_fold_x<T><<<(2 * ny + 127) / 128, 128, 0, st>>>(pad, nx, ny, s->bd, bc[0], bc[1]);
+    k_adjoint_fold_y<T><<<(nx + 2 * np + 127) / 128, 128, 0, st>>>(pad, nx, ny, np, s->bd, bc[2], bc[3]);
+    k_adjoint_fold_x<T><<<(ny + 127) / 128, 128, 0, st>>>(pad, nx, ny, np, s->bd, bc[0], bc[1]);
     const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
-    k_adjoint_unpad<T><<<grd, blk, 0, st>>>(pad, nx, ny, cot);
+    k_adjoint_unpad<T><<<grd, blk, 0, st>>>(pad, nx, ny, np, cot);
     return cudaGetLastError();
 }
 
@@ -138,7 +152,7 @@ struct Plan {
     size_t cot_off;       // two cotangent buffers of 20 compact planes
     size_t cot_bytes;
     size_t red_off;       // the dL/da hand-over slots
-    size_t pad_off;       // a cotangent padded by one ghost layer (grids with a boundary)
+    size_t pad_off;       // a cotangent padded by the ghost layers the adjoint covers (grids with a boundary)
     size_t lmp_off;       // LMP / RLMP: the face and bound planes of the three-pass adjoint
     size_t total;
 };
@@ -162,11 +176,12 @@ Plan plan_of(const vlbm_state *s, int64_t nsteps, int32_t every) {
     off += 2 * p.cot_bytes;
     p.red_off = off;
     off += 256;
+    const bool lmp = s->limiter == VLBM_LIM_LMP || s->limiter == VLBM_LIM_RLMP;
+    const int np = lmp ? 2 : 1;   // the LMP bounds reach the second ghost layer
     p.pad_off = off;
-    off += round256((size_t)kNPlane * (s->grid.nx + 2) * (s->grid.ny + 2) * s->L.elem);
+    off += round256((size_t)kNPlane * (s->grid.nx + 2 * np) * (s->grid.ny + 2 * np) * s->L.elem);
     p.lmp_off = off;
-    if (s->limiter == VLBM_LIM_LMP || s->limiter == VLBM_LIM_RLMP)
-        off += round256((size_t)kLPlanes * s->grid.nx * s->grid.ny * s->L.elem);
+    if (lmp) off += round256((size_t)kLPlanes * (s->grid.nx + 4) * (s->grid.ny + 4) * s->L.elem);
     p.total = off;
     return p;
 }
@@ -303,6 +318,7 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     bool periodic = true;
     for (int q = 0; q < 4; ++q) periodic = periodic && s->grid.bc[q] == VLBM_BC_PERIODIC;
     A.ext = periodic ? 0 : 1;
+    A.pad = (s->limiter == VLBM_LIM_LMP || s->limiter == VLBM_LIM_RLMP) ? 2 : 1;
     uniform_types(s->bd, A.bc);
     A.sponge = s->sponge;
     A.lmp = (T *)(scratch + p.lmp_off);
@@ -328,7 +344,7 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
             A.cot_out = A.ext ? pad : cot[cur ^ 1];
             A.k = fixed_a ? ctl_consts<T>(segctl) : (const StepConsts<T> *)(khist + (m - s0) * kConstSlot);
             e = launch_adjoint_step<T>(A, s->limiter, s->stream);
-            if (e == cudaSuccess && A.ext) e = fold_ghosts<T>(pad, s, cot[cur ^ 1], s->stream);
+            if (e == cudaSuccess && A.ext) e = fold_ghosts<T>(pad, A.pad, s, cot[cur ^ 1], s->stream);
             if (e != cudaSuccess) return cuda_fail(s, e, "adjoint step launch");
             cur ^= 1;
             if (diff_a && m > 0) {   // a^m came from lambda of s^m (a^0 waits for the init map)
@@ -380,13 +396,9 @@ int vlbm_adjoint(vlbm_state *s, const void *d_u0, int64_t nsteps, int32_t ckpt_e
     if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
     if (nsteps < 0 || ckpt_every < 1) return fail(s, VLBM_E_INVAL, "need nsteps >= 0 and ckpt_every >= 1");
     if (!d_dLduN || !d_dLdu0) return fail(s, VLBM_E_INVAL, "cotangent pointer is NULL");
-    if (s->limiter == VLBM_LIM_LMP || s->limiter == VLBM_LIM_RLMP) {
-        for (int q = 0; q < 4; ++q)
-            if (s->grid.bc[q] != VLBM_BC_PERIODIC)
-                return fail(s, VLBM_E_UNSUPPORTED, "the LMP / RLMP adjoint covers periodic grids");
-        if (s->adj_mode == VLBM_ADJOINT_DIFF_A && s->a_fixed <= 0.0)
-            return fail(s, VLBM_E_UNSUPPORTED, "the LMP / RLMP adjoint holds a^n (VLBM_ADJOINT_HOLD_A)");
-    }
+    if ((s->limiter == VLBM_LIM_LMP || s->limiter == VLBM_LIM_RLMP) && s->adj_mode == VLBM_ADJOINT_DIFF_A &&
+        s->a_fixed <= 0.0)
+        return fail(s, VLBM_E_UNSUPPORTED, "the LMP / RLMP adjoint holds a^n (VLBM_ADJOINT_HOLD_A)");
     if (s->adj_mode == VLBM_ADJOINT_DIFF_A && s->a_fixed <= 0.0 && s->bd.has_dir)
         return fail(s, VLBM_E_UNSUPPORTED, "differentiating a^n with a prescribed boundary state");
     DeviceGuard g(s->device);

@@ -41,10 +41,12 @@ struct AdjArgs {
     T *cot_out;            // cotangent of s^n: 20 compact planes
     const StepConsts<T> *k;  // constants of the step (kinetic speed a^n as the forward run used it)
     double *abar;          // DA: accumulates dL/da^n
-    int ext;               // 1: grid with a boundary (cot_out padded by one cell, see above)
-    // LMP / RLMP (periodic grids): per-face theta and (u*, dF) cotangents, per-cell
-    // bound cotangents, filled by k_adj_lmp_faces / k_adj_lmp_bounds before the gather.
-    // Planes of nx ny: thE, thN, usbE[4], dfbE[4], usbN[4], dfbN[4], mub, nub, rb.
+    int ext;               // 1: grid with a boundary (cot_out padded by `pad` cells, see above)
+    int pad;               // 1, or 2 for LMP / RLMP (their bounds reach the second ghost layer)
+    // LMP / RLMP: per-face theta and (u*, dF) cotangents, per-cell bound cotangents,
+    // filled by k_adj_lmp_faces / k_adj_lmp_bounds before the gather. Planes of
+    // nx ny cells (periodic) or (nx + 4) (ny + 4) (with a boundary: cells -2 .. n + 1):
+    // thE, thN, usbE[4], dfbE[4], usbN[4], dfbN[4], mub, nub, rb.
     T *lmp;
     int bc[4];             // uniform side types (-1 where a side switches), for the sponge
     int sponge;            // theta = 0 layer of the forward step (Sec. 4.2)
@@ -149,9 +151,25 @@ __device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const 
     return th;
 }
 
-// The transpose for cell (i, j); returns its part of dL/da^n (DA) or 0.
 enum { kLthE = 0, kLthN = 1, kLusbE = 2, kLdfbE = 6, kLusbN = 10, kLdfbN = 14, kLmub = 18, kLnub = 19, kLrb = 20,
        kLPlanes = 21 };
+
+// Cells of one LMP plane, and the index of cell (i, j) in it: compact with the
+// periodic wrap, or padded by two cells on a grid with a boundary (-1 outside).
+template <typename T>
+__device__ __forceinline__ long long lmp_cells(const AdjArgs<T> &A) {
+    return A.ext ? (long long)(A.nx + 4) * (A.ny + 4) : (long long)A.nx * A.ny;
+}
+template <typename T>
+__device__ __forceinline__ long long lmp_ix(const AdjArgs<T> &A, int i, int j) {
+    if (A.ext) {
+        if (i < -2 || i > A.nx + 1 || j < -2 || j > A.ny + 1) return -1;
+        return (long long)(j + 2) * (A.nx + 4) + (i + 2);
+    }
+    i = i < 0 ? i + A.nx : (i >= A.nx ? i - A.nx : i);
+    j = j < 0 ? j + A.ny : (j >= A.ny ? j - A.ny : j);
+    return (long long)j * A.nx + i;
+}
 
 // rho* of the x-face (i, i+1) or the y-face (j, j+1) of row / column of cell (i, j)
 // (the density component of u*, eq. D2Q5_convexproof_3: the flux of rho is the
@@ -231,19 +249,26 @@ __device__ __forceinline__ T lmp_face(const T us[4], const T df[4], T muL, T nuL
     return th;
 }
 
-// Pass 1 of the LMP / RLMP adjoint (periodic grid, forward state padded with its
-// periodic ghost frame): each cell takes its east and north faces.
-template <typename T, int LIM>
+// Pass 1 of the LMP / RLMP adjoint: each cell takes its east and north faces. On a
+// periodic grid every cell; with a boundary (EXT) cells -1 .. n - 1 in both
+// directions (every face next to an interior cell), outputs outside the interior
+// having no cotangent; faces of sponge cells have theta = 0 and no cotangent.
+template <typename T, int LIM, bool EXT>
 __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    constexpr int e = EXT ? 1 : 0;
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - e, j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - e;
     if (i >= A.nx || j >= A.ny) return;
     const StepConsts<T> k = *A.k;
     const CellLoad<T> L{A.fwd, A.plane, A.pitch};
-    const long long N = (long long)A.nx * A.ny;
-    const int ie = i < A.nx - 1 ? i + 1 : 0, jn = j < A.ny - 1 ? j + 1 : 0;
-    const long long cC = (long long)j * A.nx + i, cE = (long long)j * A.nx + ie, cN = (long long)jn * A.nx + i;
+    const long long N = (long long)A.nx * A.ny, NL = lmp_cells(A);
+    auto out_cell = [&](int x, int y) -> long long {   // cotangent index of cell (x, y)'s outputs
+        if (EXT) return ((unsigned)x >= (unsigned)A.nx || (unsigned)y >= (unsigned)A.ny) ? -1 : (long long)y * A.nx + x;
+        return lmp_ix(A, x, y);
+    };
+    const long long cC = out_cell(i, j), cE = out_cell(i + 1, j), cN = out_cell(i, j + 1);
+    const long long lC = lmp_ix(A, i, j), lE = lmp_ix(A, i + 1, j), lN = lmp_ix(A, i, j + 1);
     T *P = A.lmp;
-    auto cot = [&](int q, long long c) { return A.cot_in[q * N + c]; };
+    auto cot = [&](int q, long long c) -> T { return c < 0 ? T(0) : A.cot_in[q * N + c]; };
     T uC[4], uE[4], uN[4], fC[4], gC[4], fE[4], gE[4], fN[4], gN[4];
     L.u4(0, i, j, uC);
     L.u4(0, i + 1, j, uE);
@@ -272,48 +297,58 @@ __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
     lmp_bounds<T, LIM>(L, i, j, k, &muC, &nuC, &a, &b);
     lmp_bounds<T, LIM>(L, i + 1, j, k, &muE, &nuE, &a, &b);
     lmp_bounds<T, LIM>(L, i, j + 1, k, &muN, &nuN, &a, &b);
-    T usb[4], dfb[4];
-    P[kLthE * N + cC] = lmp_face<T, LIM>(usE, dfE, muC, nuC, muE, nuE, tbE, k, usb, dfb, &P[kLmub * N + cC],
-                                         &P[kLnub * N + cC], &P[kLmub * N + cE], &P[kLnub * N + cE]);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        P[(kLusbE + c) * N + cC] = usb[c];
-        P[(kLdfbE + c) * N + cC] = dfb[c];
+    bool spE = false, spN = false;   // sponge faces (Sec. 4.2): theta = 0 whatever the limiter
+    if (EXT && A.sponge > 0) {
+        const Sponge sp(A.sponge, A.nx, A.ny, A.bc);
+        const bool sc = sp.cell(i, j);
+        spE = sc || sp.cell(i + 1, j);
+        spN = sc || sp.cell(i, j + 1);
     }
-    P[kLthN * N + cC] = lmp_face<T, LIM>(usN, dfN, muC, nuC, muN, nuN, tbN, k, usb, dfb, &P[kLmub * N + cC],
-                                         &P[kLnub * N + cC], &P[kLmub * N + cN], &P[kLnub * N + cN]);
+    T usb[4], dfb[4];
+    T th = lmp_face<T, LIM>(usE, dfE, muC, nuC, muE, nuE, spE ? T(0) : tbE, k, usb, dfb, &P[kLmub * NL + lC],
+                            &P[kLnub * NL + lC], &P[kLmub * NL + lE], &P[kLnub * NL + lE]);
+    P[kLthE * NL + lC] = spE ? T(0) : th;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        P[(kLusbN + c) * N + cC] = usb[c];
-        P[(kLdfbN + c) * N + cC] = dfb[c];
+        P[(kLusbE + c) * NL + lC] = usb[c];
+        P[(kLdfbE + c) * NL + lC] = dfb[c];
+    }
+    th = lmp_face<T, LIM>(usN, dfN, muC, nuC, muN, nuN, spN ? T(0) : tbN, k, usb, dfb, &P[kLmub * NL + lC],
+                          &P[kLnub * NL + lC], &P[kLmub * NL + lN], &P[kLnub * NL + lN]);
+    P[kLthN * NL + lC] = spN ? T(0) : th;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        P[(kLusbN + c) * NL + lC] = usb[c];
+        P[(kLdfbN + c) * NL + lC] = dfb[c];
     }
 }
 
 // Pass 2: the bound cotangents of each cell go to the value its min / max took:
 // its own density (rb) or rho* of one of its faces (the density component of that
-// face's u* cotangent). RLMP scales by 0.999 / 1.001.
-template <typename T, int LIM>
+// face's u* cotangent). RLMP scales by 0.999 / 1.001. With a boundary (EXT) the
+// cells of the first ghost layer too (their bounds enter the boundary faces).
+template <typename T, int LIM, bool EXT>
 __global__ void __launch_bounds__(256) k_adj_lmp_bounds(AdjArgs<T> A) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= A.nx || j >= A.ny) return;
-    const long long N = (long long)A.nx * A.ny, cC = (long long)j * A.nx + i;
+    constexpr int e = EXT ? 1 : 0;
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - e, j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - e;
+    if (i >= A.nx + e || j >= A.ny + e) return;
+    const long long NL = lmp_cells(A), cC = lmp_ix(A, i, j);
     T *P = A.lmp;
-    const T mb = P[kLmub * N + cC], nb = P[kLnub * N + cC];
+    const T mb = P[kLmub * NL + cC], nb = P[kLnub * NL + cC];
     if (mb == T(0) && nb == T(0)) return;
     const StepConsts<T> k = *A.k;
     const CellLoad<T> L{A.fwd, A.plane, A.pitch};
     T mu, nu;
     int a, b;
     lmp_bounds<T, LIM>(L, i, j, k, &mu, &nu, &a, &b);
-    const int iw = i > 0 ? i - 1 : A.nx - 1, js = j > 0 ? j - 1 : A.ny - 1;
-    const long long cW = (long long)j * A.nx + iw, cS = (long long)js * A.nx + i;
+    const long long cW = lmp_ix(A, i - 1, j), cS = lmp_ix(A, i, j - 1);
     auto give = [&](int which, T v) {
         if (v == T(0)) return;
-        T *dst = which == 0 ? &P[kLrb * N + cC]
-               : which == 1 ? &P[kLusbE * N + cW]
-               : which == 2 ? &P[kLusbE * N + cC]
-               : which == 3 ? &P[kLusbN * N + cS]
-                            : &P[kLusbN * N + cC];
+        T *dst = which == 0 ? &P[kLrb * NL + cC]
+               : which == 1 ? &P[kLusbE * NL + cW]
+               : which == 2 ? &P[kLusbE * NL + cC]
+               : which == 3 ? &P[kLusbN * NL + cS]
+                            : &P[kLusbN * NL + cC];
         atomicAdd(dst, v);
     };
     give(a, LIM == VLBM_LIM_RLMP ? mb * T(0.999) : mb);
@@ -412,11 +447,16 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
         if constexpr (EXT) return c < 0 ? T(0) : A.cot_in[q * N + c];
         else return A.cot_in[q * N + c];
     };
+    long long lC = 0, lW = 0, lS = 0, NL = 0;   // the cell and its west / south neighbours in the LMP planes
     if constexpr (kLmp) {   // theta of the four faces as pass 1 found it
-        th[0] = A.lmp[kLthE * N + cW];
-        th[1] = A.lmp[kLthE * N + cC];
-        th[2] = A.lmp[kLthN * N + cS];
-        th[3] = A.lmp[kLthN * N + cC];
+        NL = lmp_cells(A);
+        lC = lmp_ix(A, i, j);
+        lW = lmp_ix(A, i - 1, j);
+        lS = lmp_ix(A, i, j - 1);
+        th[0] = A.lmp[kLthE * NL + lW];
+        th[1] = A.lmp[kLthE * NL + lC];
+        th[2] = A.lmp[kLthN * NL + lS];
+        th[3] = A.lmp[kLthN * NL + lC];
     }
     T ubC[4], ubW[4], ubE[4], ubS[4], ubN[4];
     T P1C[4], P2C[4], P3C[4], P4C[4], P1E[4], P2W[4], P3N[4], P4S[4];
@@ -453,14 +493,14 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
         T usb_W, usb_E, usb_S, usb_N, dfb_W, dfb_E, dfb_S, dfb_N;
         if constexpr (kLmp) {   // passes 1 and 2 left the face cotangents
             const T *P = A.lmp;
-            usb_W = P[(kLusbE + c) * N + cW];
-            usb_E = P[(kLusbE + c) * N + cC];
-            usb_S = P[(kLusbN + c) * N + cS];
-            usb_N = P[(kLusbN + c) * N + cC];
-            dfb_W = P[(kLdfbE + c) * N + cW];
-            dfb_E = P[(kLdfbE + c) * N + cC];
-            dfb_S = P[(kLdfbN + c) * N + cS];
-            dfb_N = P[(kLdfbN + c) * N + cC];
+            usb_W = P[(kLusbE + c) * NL + lW];
+            usb_E = P[(kLusbE + c) * NL + lC];
+            usb_S = P[(kLusbN + c) * NL + lS];
+            usb_N = P[(kLusbN + c) * NL + lC];
+            dfb_W = P[(kLdfbE + c) * NL + lW];
+            dfb_E = P[(kLdfbE + c) * NL + lC];
+            dfb_S = P[(kLdfbN + c) * NL + lS];
+            dfb_N = P[(kLdfbN + c) * NL + lC];
         } else {
             usb_W = tb[0] * gus[0][c];
             usb_E = tb[1] * gus[1][c];
@@ -489,9 +529,10 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     flux_vjp(uC, k.gm1, 1, wy, ry);
 #pragma unroll
     for (int c = 0; c < 4; ++c) out[c] += rx[c] + ry[c];
-    if constexpr (kLmp) out[0] += A.lmp[kLrb * N + cC];   // the density where a cell's bound was taken
+    if constexpr (kLmp) out[0] += A.lmp[kLrb * NL + lC];   // the density where a cell's bound was taken
     if constexpr (EXT) {
-        const long long Np = (long long)(A.nx + 2) * (A.ny + 2), cp = (long long)(j + 1) * (A.nx + 2) + (i + 1);
+        const int w = A.nx + 2 * A.pad;
+        const long long Np = (long long)w * (A.ny + 2 * A.pad), cp = (long long)(j + A.pad) * w + (i + A.pad);
 #pragma unroll
         for (int q = 0; q < kNPlane; ++q) A.cot_out[q * Np + cp] = out[q];
     } else {
@@ -532,6 +573,58 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     }
 }
 
+
+// LMP / RLMP with a boundary: the cells of the second ghost layer (the outer ring of
+// the padded cotangent, 2 (nx + 4) + 2 (ny + 2) cells). Their outputs and the
+// faces between them and the first layer carry no theta cotangent, but the bounds
+// of a first-layer cell can be taken at rho* of such a face: that u* cotangent
+// reaches the ring cell through u* = (uL + uR)/2 -/+ (F(uR) - F(uL)) / (2 kappa).
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_lmp_ring(AdjArgs<T> A) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = A.nx + 4, h = A.ny + 2;
+    if (t >= 2 * w + 2 * h) return;
+    int i, j;
+    if (t < 2 * w) { i = t % w - 2; j = t < w ? -2 : A.ny + 1; }
+    else { const int r = t - 2 * w; j = r % h - 1; i = r < h ? -2 : A.nx + 1; }
+    const long long NL = lmp_cells(A);
+    auto usb = [&](int plane, int x, int y) -> T {
+        const long long c = lmp_ix(A, x, y);
+        return c < 0 ? T(0) : A.lmp[plane * NL + c];
+    };
+    T out[kNPlane];
+#pragma unroll
+    for (int q = 0; q < kNPlane; ++q) out[q] = T(0);
+    T uW[4], uE[4], uS[4], uN[4];
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uW[c] = usb(kLusbE + c, i - 1, j);
+        uE[c] = usb(kLusbE + c, i, j);
+        uS[c] = usb(kLusbN + c, i, j - 1);
+        uN[c] = usb(kLusbN + c, i, j);
+        any = any || uW[c] != T(0) || uE[c] != T(0) || uS[c] != T(0) || uN[c] != T(0);
+    }
+    if (any) {   // only then is the cell's state read (a ring cell on a corner may hold none)
+        const StepConsts<T> k = *A.k;
+        const CellLoad<T> L{A.fwd, A.plane, A.pitch};
+        T u[4], wx[4], wy[4], rx[4], ry[4];
+        L.u4(0, i, j, u);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            out[c] = T(0.5) * (uW[c] + uE[c] + uS[c] + uN[c]);
+            wx[c] = (uE[c] - uW[c]) * k.inv2k;
+            wy[c] = (uN[c] - uS[c]) * k.inv2k;
+        }
+        flux_vjp(u, k.gm1, 0, wx, rx);
+        flux_vjp(u, k.gm1, 1, wy, ry);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) out[c] += rx[c] + ry[c];
+    }
+    const long long Np = (long long)w * (A.ny + 4), cp = (long long)(j + 2) * w + (i + 2);
+#pragma unroll
+    for (int q = 0; q < kNPlane; ++q) A.cot_out[q * Np + cp] = out[q];
+}
 
 // Sum of v over the CTA's warps into *dst (every thread of the CTA calls it).
 __device__ __forceinline__ void warp_sum_atomic(double v, double *dst) {
@@ -668,13 +761,16 @@ __global__ void k_lambda_apply(const T *st, long long plane, int pitch, int nx, 
 
 namespace vlbm {
 
-// Transpose of the ghost fill on a padded cotangent (one ghost layer, (nx + 2) x
-// (ny + 2) per plane): the cotangent of each ghost goes to the cell it was filled
+// Transpose of the ghost fill on a padded cotangent (`pad` ghost layers, (nx + 2 pad) x
+// (ny + 2 pad) per plane): the cotangent of each ghost goes to the cell it was filled
 // from (ZG copy, periodic copy, or mirror image with its map; a prescribed ghost
-// keeps nothing). The y rule was applied last, so it is undone first.
+// keeps nothing). The y rule was applied last, so it is undone first. One thread
+// takes every ghost of a column (y) or row (x) in turn: ghosts that share a source
+// (the layers of a zero-gradient side) never add to it at the same time.
 template <typename T>
-__device__ __forceinline__ void fold_one(T *cot, long long Np, int w, int gi, int gj, int si, int sj, bool mx, bool my) {
-    const long long g = (long long)(gj + 1) * w + (gi + 1), d = (long long)(sj + 1) * w + (si + 1);
+__device__ __forceinline__ void fold_one(T *cot, long long Np, int w, int pad, int gi, int gj, int si, int sj, bool mx,
+                                         bool my) {
+    const long long g = (long long)(gj + pad) * w + (gi + pad), d = (long long)(sj + pad) * w + (si + pad);
 #pragma unroll
     for (int q = 0; q < kNPlane; ++q) {
         int src = q;   // the mirror map is a symmetric permutation with signs: its own transpose
@@ -687,39 +783,50 @@ __device__ __forceinline__ void fold_one(T *cot, long long Np, int w, int gi, in
 }
 
 template <typename T>
-__global__ void k_adjoint_fold_y(T *cot, int nx, int ny, Bound bd, int bc2, int bc3) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // 2 (nx + 2) ghosts: rows -1 and ny
-    if (t >= 2 * (nx + 2)) return;
-    const int gi = t % (nx + 2) - 1, gj = t < nx + 2 ? -1 : ny;
-    const int s = gj < 0 ? 2 : 3;
-    const int type = (s == 2 ? bc2 : bc3) >= 0 ? (s == 2 ? bc2 : bc3) : side_type(bd, s, gi);
-    if (type == VLBM_BC_DIRICHLET) return;
-    bool my;
-    const int sj = ghost_source_typed(gj, ny, type, &my);
-    fold_one(cot, (long long)(nx + 2) * (ny + 2), nx + 2, gi, gj, gi, sj, false, my);
+__global__ void k_adjoint_fold_y(T *cot, int nx, int ny, int pad, Bound bd, int bc2, int bc3) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // one thread per column -pad .. nx + pad - 1
+    const int w = nx + 2 * pad;
+    if (t >= w) return;
+    const int gi = t - pad;
+    const long long Np = (long long)w * (ny + 2 * pad);
+    for (int l = 0; l < 2 * pad; ++l) {
+        const int gj = l < pad ? -1 - l : ny + (l - pad);
+        const int s = gj < 0 ? 2 : 3;
+        const int type = (s == 2 ? bc2 : bc3) >= 0 ? (s == 2 ? bc2 : bc3) : side_type(bd, s, gi);
+        if (type == VLBM_BC_DIRICHLET) continue;
+        bool my;
+        const int sj = ghost_source_typed(gj, ny, type, &my);
+        fold_one(cot, Np, w, pad, gi, gj, gi, sj, false, my);
+    }
 }
 
 template <typename T>
-__global__ void k_adjoint_fold_x(T *cot, int nx, int ny, Bound bd, int bc0, int bc1) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // 2 ny ghosts: columns -1 and nx
-    if (t >= 2 * ny) return;
-    const int gj = t % ny, gi = t < ny ? -1 : nx;
-    const int s = gi < 0 ? 0 : 1;
-    const int type = (s == 0 ? bc0 : bc1) >= 0 ? (s == 0 ? bc0 : bc1) : side_type(bd, s, gj);
-    if (type == VLBM_BC_DIRICHLET) return;
-    bool mx;
-    const int si = ghost_source_typed(gi, nx, type, &mx);
-    fold_one(cot, (long long)(nx + 2) * (ny + 2), nx + 2, gi, gj, si, gj, mx, false);
+__global__ void k_adjoint_fold_x(T *cot, int nx, int ny, int pad, Bound bd, int bc0, int bc1) {
+    const int gj = blockIdx.x * blockDim.x + threadIdx.x;   // one thread per interior row
+    if (gj >= ny) return;
+    const int w = nx + 2 * pad;
+    const long long Np = (long long)w * (ny + 2 * pad);
+    for (int l = 0; l < 2 * pad; ++l) {
+        const int gi = l < pad ? -1 - l : nx + (l - pad);
+        const int s = gi < 0 ? 0 : 1;
+        const int type = (s == 0 ? bc0 : bc1) >= 0 ? (s == 0 ? bc0 : bc1) : side_type(bd, s, gj);
+        if (type == VLBM_BC_DIRICHLET) continue;
+        bool mx;
+        const int si = ghost_source_typed(gi, nx, type, &mx);
+        fold_one(cot, Np, w, pad, gi, gj, si, gj, mx, false);
+    }
 }
 
 // Interior of a padded cotangent into compact planes.
 template <typename T>
-__global__ void k_adjoint_unpad(const T *cot_pad, int nx, int ny, T *cot) {
+__global__ void k_adjoint_unpad(const T *cot_pad, int nx, int ny, int pad, T *cot) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= nx || j >= ny) return;
-    const long long Np = (long long)(nx + 2) * (ny + 2), N = (long long)nx * ny;
+    const int w = nx + 2 * pad;
+    const long long Np = (long long)w * (ny + 2 * pad), N = (long long)nx * ny;
 #pragma unroll
-    for (int q = 0; q < kNPlane; ++q) cot[q * N + (long long)j * nx + i] = cot_pad[q * Np + (long long)(j + 1) * (nx + 2) + i + 1];
+    for (int q = 0; q < kNPlane; ++q)
+        cot[q * N + (long long)j * nx + i] = cot_pad[q * Np + (long long)(j + pad) * w + i + pad];
 }
 
 }  // namespace vlbm

@@ -319,11 +319,6 @@ def test_adjoint_full_size_vortex_with_bumps():
 def test_adjoint_rejects_unsupported():
     p = W.vortex_with_bumps(32)
     u0 = torch.tensor(p.conserved(), dtype=torch.float64, device=DEV)
-    s = V.VLBM(p.nx, p.ny, p.dx, bc=(1, 1, 0, 0), lam=1.0, limiter=V.LIM_LMP, precision=V.FP64, device=DEV)
-    with pytest.raises(V.VLBMError) as e:      # LMP with a boundary
-        s.adjoint(u0, 4, 2, s.adjoint_scratch(4, 2), u0=u0)
-    assert e.value.code == V.E_UNSUPPORTED
-    s.close()
     s = V.VLBM(p.nx, p.ny, p.dx, limiter=V.LIM_RLMP, precision=V.FP64, device=DEV)
     s.set_adjoint_mode(V.ADJOINT_DIFF_A)
     with pytest.raises(V.VLBMError) as e:      # LMP with a differentiated dynamic a
@@ -480,5 +475,42 @@ def test_adjoint_lmp_matches_autograd(limiter, kernel):
     ref = O.run(cfg, cons, dx, nsteps=nsteps, lam_fixed=lam)["state"]
     assert np.array_equal(uN.cpu().numpy(), ref[:4])
     sN, g_ref = _autograd_gradient(cons, nsteps, a, limiter, w, tgt, 1e-16)
+    err = np.abs(g.cpu().numpy() - g_ref)
+    assert err.max() <= 1e-9 * np.abs(g_ref).max(), (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+@pytest.mark.parametrize("kernel", [V.KERNEL_SIMPLE, V.KERNEL_FUSED])
+@pytest.mark.parametrize("limiter", [V.LIM_LMP, V.LIM_RLMP])
+@pytest.mark.parametrize("case", ["zg-mirror", "sponge", "dirichlet-split"])
+def test_adjoint_lmp_with_boundaries(case, limiter, kernel):
+    """LMP / RLMP on grids with a boundary (a held): the bounds of the first ghost
+    layer enter the boundary faces and reach rho* of faces in the second, so the
+    three passes run over a two-layer frame and the fold undoes two ghost layers.
+    FP64 gradient against autograd through the restatement inside the oracle's
+    ghost frame, on smooth waves in a box."""
+    from tests.test_torch_reference import _box_cfg, boxed_waves
+    cons, dx, kw = boxed_waves(case)
+    ny, nx = cons.shape[1:]
+    cfg = _box_cfg(nx, ny, limiter, kw, dx)
+    lam = 1.05 * O.max_speed(cfg, O.new_state(cons))
+    a = O.kinetic_speed(lam, 0.5)
+    boundary = V.make_boundary(kw["bc"], kw["bc_hi"], kw["split"], 0.0, 0.0, kw["field"]) if "field" in kw else None
+    s = V.VLBM(nx, ny, dx, bc=kw["bc"], lam=lam, limiter=limiter, precision=V.FP64, kernel=kernel, device=DEV,
+               sponge=kw["sponge"], boundary=boundary)
+    nsteps, every = 16, 5
+    rng = np.random.default_rng(5)
+    w = torch.tensor(rng.uniform(0.5, 1.5, size=(4, ny, nx)), dtype=torch.float64, device=DEV)
+    tgt = torch.tensor(cons * 0.97, dtype=torch.float64, device=DEV)
+    u0 = torch.tensor(cons, dtype=torch.float64, device=DEV)
+    uN, g = _adjoint(s, u0, nsteps, every, w, tgt)
+    assert s.monitors()["status"] == 0
+    s.close()
+    ref = O.run(cfg, cons, dx, nsteps=nsteps, lam_fixed=lam)["state"]
+    assert np.array_equal(uN.cpu().numpy(), ref[:4])
+    fr = TR.ghost_frame(cfg, a, sponge=kw["sponge"])
+    x = torch.tensor(cons, dtype=torch.float64, requires_grad=True)
+    sN = TR.rollout_frame(x, nsteps, a, limiter, fr)
+    (0.5 * (w.cpu() * (sN[:4] - tgt.cpu()) ** 2).sum()).backward()
+    g_ref = x.grad.numpy()
     err = np.abs(g.cpu().numpy() - g_ref)
     assert err.max() <= 1e-9 * np.abs(g_ref).max(), (err.max(), np.unravel_index(err.argmax(), err.shape))
