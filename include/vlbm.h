@@ -328,10 +328,11 @@ VLBM_API const char *vlbm_batch_last_error(const vlbm_batch *b);
  * ghost's cotangent to the cell it was filled from, and a prescribed ghost holds
  * no state. LMP / RLMP (Sec. 3.3.1-3.3.2: theta^rho through the local bounds, each
  * the min / max of five candidates, the cotangent going to the first that attains
- * it) are covered with a fixed or held a^n, on every grid (with a boundary the
- * bounds of the first ghost layer reach the second, and both layers are folded
- * back). LMP / RLMP with VLBM_ADJOINT_DIFF_A, and VLBM_ADJOINT_DIFF_A with a
- * prescribed boundary state, return VLBM_E_UNSUPPORTED.
+ * it) are covered on every grid (with a boundary the bounds of the first ghost
+ * layer reach the second, and both layers are folded back), a^n held or
+ * differentiated (d theta / da then includes the bound's dependence on a through
+ * rho* of the face where it was taken). VLBM_ADJOINT_DIFF_A with a prescribed
+ * boundary state returns VLBM_E_UNSUPPORTED.
  *
  * Memory: checkpoints of the state every ckpt_every steps, a segment buffer of
  * ckpt_every + 1 states for the recomputation, and two cotangent buffers, all in

@@ -41,7 +41,7 @@ static cudaError_t launch_adjoint_step_da(const AdjArgs<T> &A, int limiter, cuda
         case VLBM_LIM_PP: k_adjoint_step<T, VLBM_LIM_PP, DA, EXT><<<grd, blk, 0, s>>>(A); break;
         case VLBM_LIM_LMP:
         case VLBM_LIM_RLMP:
-            if constexpr (!DA) {   // a^n held: passes 1, 2, then the gather (and the outer ring)
+            {   // passes 1, 2, then the gather (and the outer ring)
                 // faces of cells 0 .. n - 1 (periodic) or -1 .. n - 1 (boundary); bounds and
                 // the gather over the cells of the step (with the first ghost layer)
                 const dim3 gf((A.nx + (EXT ? 1 : 0) + 31) / 32, (A.ny + (EXT ? 1 : 0) + 7) / 8);
@@ -55,13 +55,13 @@ static cudaError_t launch_adjoint_step_da(const AdjArgs<T> &A, int limiter, cuda
                 }
                 if (e != cudaSuccess) return e;
                 if (limiter == VLBM_LIM_LMP) {
-                    k_adj_lmp_faces<T, VLBM_LIM_LMP, EXT><<<gf, blk, 0, s>>>(A);
+                    k_adj_lmp_faces<T, VLBM_LIM_LMP, EXT, DA><<<gf, blk, 0, s>>>(A);
                     k_adj_lmp_bounds<T, VLBM_LIM_LMP, EXT><<<grd, blk, 0, s>>>(A);
-                    k_adjoint_step<T, VLBM_LIM_LMP, false, EXT><<<grd, blk, 0, s>>>(A);
+                    k_adjoint_step<T, VLBM_LIM_LMP, DA, EXT><<<grd, blk, 0, s>>>(A);
                 } else {
-                    k_adj_lmp_faces<T, VLBM_LIM_RLMP, EXT><<<gf, blk, 0, s>>>(A);
+                    k_adj_lmp_faces<T, VLBM_LIM_RLMP, EXT, DA><<<gf, blk, 0, s>>>(A);
                     k_adj_lmp_bounds<T, VLBM_LIM_RLMP, EXT><<<grd, blk, 0, s>>>(A);
-                    k_adjoint_step<T, VLBM_LIM_RLMP, false, EXT><<<grd, blk, 0, s>>>(A);
+                    k_adjoint_step<T, VLBM_LIM_RLMP, DA, EXT><<<grd, blk, 0, s>>>(A);
                 }
                 if (EXT) {
                     const int ring = 2 * (A.nx + 4) + 2 * (A.ny + 2);
@@ -69,7 +69,6 @@ static cudaError_t launch_adjoint_step_da(const AdjArgs<T> &A, int limiter, cuda
                 }
                 break;
             }
-            return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -396,9 +395,6 @@ int vlbm_adjoint(vlbm_state *s, const void *d_u0, int64_t nsteps, int32_t ckpt_e
     if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
     if (nsteps < 0 || ckpt_every < 1) return fail(s, VLBM_E_INVAL, "need nsteps >= 0 and ckpt_every >= 1");
     if (!d_dLduN || !d_dLdu0) return fail(s, VLBM_E_INVAL, "cotangent pointer is NULL");
-    if ((s->limiter == VLBM_LIM_LMP || s->limiter == VLBM_LIM_RLMP) && s->adj_mode == VLBM_ADJOINT_DIFF_A &&
-        s->a_fixed <= 0.0)
-        return fail(s, VLBM_E_UNSUPPORTED, "the LMP / RLMP adjoint holds a^n (VLBM_ADJOINT_HOLD_A)");
     if (s->adj_mode == VLBM_ADJOINT_DIFF_A && s->a_fixed <= 0.0 && s->bd.has_dir)
         return fail(s, VLBM_E_UNSUPPORTED, "differentiating a^n with a prescribed boundary state");
     DeviceGuard g(s->device);

@@ -46,7 +46,7 @@ struct AdjArgs {
     // LMP / RLMP: per-face theta and (u*, dF) cotangents, per-cell bound cotangents,
     // filled by k_adj_lmp_faces / k_adj_lmp_bounds before the gather. Planes of
     // nx ny cells (periodic) or (nx + 4) (ny + 4) (with a boundary: cells -2 .. n + 1):
-    // thE, thN, usbE[4], dfbE[4], usbN[4], dfbN[4], mub, nub, rb.
+    // thE, thN, usbE[4], dfbE[4], usbN[4], dfbN[4], mub, nub, rb, and (DA) taE, taN.
     T *lmp;
     int bc[4];             // uniform side types (-1 where a side switches), for the sponge
     int sponge;            // theta = 0 layer of the forward step (Sec. 4.2)
@@ -152,7 +152,7 @@ __device__ __forceinline__ T theta_and_grad(const T us[4], const T df[4], const 
 }
 
 enum { kLthE = 0, kLthN = 1, kLusbE = 2, kLdfbE = 6, kLusbN = 10, kLdfbN = 14, kLmub = 18, kLnub = 19, kLrb = 20,
-       kLPlanes = 21 };
+       kLtaE = 21, kLtaN = 22, kLPlanes = 23 };   // taE / taN: d theta / d a^n (DA)
 
 // Cells of one LMP plane, and the index of cell (i, j) in it: compact with the
 // periodic wrap, or padded by two cells on a grid with a boundary (-1 outside).
@@ -204,6 +204,57 @@ __device__ __forceinline__ void lmp_bounds(const CellLoad<T> &L, int i, int j, c
     *imax = b;
 }
 
+// d/da^n of the LMP bounds of cell (i, j) at a fixed state: the bound is rho (no
+// a-dependence) or rho* of one face, rho* = (rhoL + rhoR)/2 - (mR - mL)/(2 kappa)
+// with m the momentum normal to the face and kappa proportional to a, so
+// d rho* / da = (mR - mL) / (2 kappa a). imin / imax: the candidates lmp_bounds chose.
+template <typename T, int LIM>
+__device__ __forceinline__ void lmp_bounds_da(const CellLoad<T> &L, int i, int j, const StepConsts<T> &k, int imin,
+                                              int imax, T *dmu, T *dnu) {
+    auto drs = [&](int which) -> T {
+        const T s = k.inv2k / k.a;
+        switch (which) {
+            case 1: return (L.v(1, i, j) - L.v(1, i - 1, j)) * s;
+            case 2: return (L.v(1, i + 1, j) - L.v(1, i, j)) * s;
+            case 3: return (L.v(2, i, j) - L.v(2, i, j - 1)) * s;
+            case 4: return (L.v(2, i, j + 1) - L.v(2, i, j)) * s;
+            default: return T(0);
+        }
+    };
+    *dmu = LIM == VLBM_LIM_RLMP ? T(0.999) * drs(imin) : drs(imin);
+    *dnu = LIM == VLBM_LIM_RLMP ? T(1.001) * drs(imax) : drs(imax);
+}
+
+// d theta / da^n of one LMP face at a fixed state, on the branch the step took:
+// dus / ddf are d u* / da and d dF / da of the face, d* the bounds' derivatives.
+template <typename T, int LIM>
+__device__ __forceinline__ T lmp_face_da(const T us[4], const T df[4], T muL, T nuL, T muR, T nuR, T dmuL, T dnuL,
+                                         T dmuR, T dnuR, const T dus[4], const T ddf[4], const StepConsts<T> &k) {
+    const T tr = theta_rho_lmp(us[0], df[0], muL, nuL, muR, nuR, k);
+    unsigned int dummy = 0;
+    const T th = combine_theta(tr, us, df, k, dummy);
+    if (!(th > T(0)) || !(th < T(1))) return T(0);
+    const T ia = T(1) / k.a;
+    if (th == tr) {          // theta = s kappa X / dF^rho, kappa proportional to a
+        const T dr = df[0], rs = us[0];
+        T dX;
+        if (dr > T(0)) {
+            const T a1 = nuR - rs, a2 = rs - muL;
+            dX = a1 < a2 ? dnuR - dus[0] : dus[0] - dmuL;
+            return th * ia + k.kappa / dr * dX - th * ddf[0] / dr;
+        }
+        const T b1 = rs - muR, b2 = nuL - rs;
+        dX = b1 < b2 ? dus[0] - dmuR : dnuL - dus[0];
+        return th * ia - k.kappa / dr * dX - th * ddf[0] / dr;
+    }
+    T gus[4], gdf[4];       // theta_p = kappa / varrho - eps
+    thp_grad(us, df, k, gus, gdf);
+    T d = (th + k.eps) * ia;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d += gus[c] * dus[c] + gdf[c] * ddf[c];
+    return d;
+}
+
 // One face of the LMP adjoint: theta as the step computes it, from the face states
 // (us, df) and the bounds of the cells left (L) and right (R) of it; with tb, the
 // cotangent of theta, the cotangents of u*, dF go to usb, dfb (4 each) and those of
@@ -253,7 +304,7 @@ __device__ __forceinline__ T lmp_face(const T us[4], const T df[4], T muL, T nuL
 // periodic grid every cell; with a boundary (EXT) cells -1 .. n - 1 in both
 // directions (every face next to an interior cell), outputs outside the interior
 // having no cotangent; faces of sponge cells have theta = 0 and no cotangent.
-template <typename T, int LIM, bool EXT>
+template <typename T, int LIM, bool EXT, bool DA>
 __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
     constexpr int e = EXT ? 1 : 0;
     const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - e, j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - e;
@@ -277,12 +328,19 @@ __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
     euler_fluxes(uE, k.gm1, fE, gE);
     euler_fluxes(uN, k.gm1, fN, gN);
     T usE[4], dfE[4], usN[4], dfN[4], tbE = T(0), tbN = T(0);
+    T dusE[4], ddfE[4], dusN[4], ddfN[4];   // DA: d u* / da, d dF / da of the two faces
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const T d1C = RN<T>::sub(maxwell_plus(uC[c], fC[c], k), L.v(4 + c, i, j));
         const T d2E = RN<T>::sub(maxwell_minus(uE[c], fE[c], k), L.v(8 + c, i + 1, j));
         const T d3C = RN<T>::sub(maxwell_plus(uC[c], gC[c], k), L.v(12 + c, i, j));
         const T d4N = RN<T>::sub(maxwell_minus(uN[c], gN[c], k), L.v(16 + c, i, j + 1));
+        if (DA) {
+            dusE[c] = (fE[c] - fC[c]) * k.inv2k / k.a;
+            ddfE[c] = (d1C - d2E) - (fC[c] + fE[c]) * k.inv2a;
+            dusN[c] = (gN[c] - gC[c]) * k.inv2k / k.a;
+            ddfN[c] = (d3C - d4N) - (gC[c] + gN[c]) * k.inv2a;
+        }
         usE[c] = face_star(uC[c], fC[c], uE[c], fE[c], k);
         dfE[c] = face_dflux(d1C, d2E, k);
         usN[c] = face_star(uC[c], gC[c], uN[c], gN[c], k);
@@ -293,10 +351,10 @@ __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
         tbN += d3C * (cot(12 + c, cN) + ubN - ubC) + d4N * (cot(16 + c, cC) + ubC - ubN);
     }
     T muC, nuC, muE, nuE, muN, nuN;
-    int a, b;
-    lmp_bounds<T, LIM>(L, i, j, k, &muC, &nuC, &a, &b);
-    lmp_bounds<T, LIM>(L, i + 1, j, k, &muE, &nuE, &a, &b);
-    lmp_bounds<T, LIM>(L, i, j + 1, k, &muN, &nuN, &a, &b);
+    int aC, bC, aE, bE, aN, bN;
+    lmp_bounds<T, LIM>(L, i, j, k, &muC, &nuC, &aC, &bC);
+    lmp_bounds<T, LIM>(L, i + 1, j, k, &muE, &nuE, &aE, &bE);
+    lmp_bounds<T, LIM>(L, i, j + 1, k, &muN, &nuN, &aN, &bN);
     bool spE = false, spN = false;   // sponge faces (Sec. 4.2): theta = 0 whatever the limiter
     if (EXT && A.sponge > 0) {
         const Sponge sp(A.sponge, A.nx, A.ny, A.bc);
@@ -320,6 +378,16 @@ __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
     for (int c = 0; c < 4; ++c) {
         P[(kLusbN + c) * NL + lC] = usb[c];
         P[(kLdfbN + c) * NL + lC] = dfb[c];
+    }
+    if (DA) {
+        T dmC, dnC, dmE, dnE, dmN, dnN;
+        lmp_bounds_da<T, LIM>(L, i, j, k, aC, bC, &dmC, &dnC);
+        lmp_bounds_da<T, LIM>(L, i + 1, j, k, aE, bE, &dmE, &dnE);
+        lmp_bounds_da<T, LIM>(L, i, j + 1, k, aN, bN, &dmN, &dnN);
+        P[kLtaE * NL + lC] =
+            spE ? T(0) : lmp_face_da<T, LIM>(usE, dfE, muC, nuC, muE, nuE, dmC, dnC, dmE, dnE, dusE, ddfE, k);
+        P[kLtaN * NL + lC] =
+            spN ? T(0) : lmp_face_da<T, LIM>(usN, dfN, muC, nuC, muN, nuN, dmC, dnC, dmN, dnN, dusN, ddfN, k);
     }
 }
 
@@ -546,14 +614,21 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
         // dF = a (dL - dR) with dM_{1,3}/da = -F/(2a^2), dM_{2,4}/da = +F/(2a^2)
         const T ia = T(1) / k.a, h = k.inv2a * ia;
         T dth[4];
+        if constexpr (kLmp) {   // pass 1 left d theta / da of every face
+            dth[0] = A.lmp[kLtaE * NL + lW];
+            dth[1] = A.lmp[kLtaE * NL + lC];
+            dth[2] = A.lmp[kLtaN * NL + lS];
+            dth[3] = A.lmp[kLtaN * NL + lC];
+        } else {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) dth[f] = act[f] ? (th[f] + k.eps) * ia : T(0);
+            for (int f = 0; f < 4; ++f) dth[f] = act[f] ? (th[f] + k.eps) * ia : T(0);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            dth[0] += gus[0][c] * (fC[c] - fW[c]) * k.inv2k * ia + gdf[0][c] * ((d1W[c] - d2C[c]) - (fW[c] + fC[c]) * k.inv2a);
-            dth[1] += gus[1][c] * (fE[c] - fC[c]) * k.inv2k * ia + gdf[1][c] * ((d1C[c] - d2E[c]) - (fC[c] + fE[c]) * k.inv2a);
-            dth[2] += gus[2][c] * (gC[c] - gS[c]) * k.inv2k * ia + gdf[2][c] * ((d3S[c] - d4C[c]) - (gS[c] + gC[c]) * k.inv2a);
-            dth[3] += gus[3][c] * (gN[c] - gC[c]) * k.inv2k * ia + gdf[3][c] * ((d3C[c] - d4N[c]) - (gC[c] + gN[c]) * k.inv2a);
+            for (int c = 0; c < 4; ++c) {
+                dth[0] += gus[0][c] * (fC[c] - fW[c]) * k.inv2k * ia + gdf[0][c] * ((d1W[c] - d2C[c]) - (fW[c] + fC[c]) * k.inv2a);
+                dth[1] += gus[1][c] * (fE[c] - fC[c]) * k.inv2k * ia + gdf[1][c] * ((d1C[c] - d2E[c]) - (fC[c] + fE[c]) * k.inv2a);
+                dth[2] += gus[2][c] * (gC[c] - gS[c]) * k.inv2k * ia + gdf[2][c] * ((d3S[c] - d4C[c]) - (gS[c] + gC[c]) * k.inv2a);
+                dth[3] += gus[3][c] * (gN[c] - gC[c]) * k.inv2k * ia + gdf[3][c] * ((d3C[c] - d4N[c]) - (gC[c] + gN[c]) * k.inv2a);
+            }
         }
         double ab = 0.0;
 #pragma unroll

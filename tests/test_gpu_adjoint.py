@@ -319,12 +319,6 @@ def test_adjoint_full_size_vortex_with_bumps():
 def test_adjoint_rejects_unsupported():
     p = W.vortex_with_bumps(32)
     u0 = torch.tensor(p.conserved(), dtype=torch.float64, device=DEV)
-    s = V.VLBM(p.nx, p.ny, p.dx, limiter=V.LIM_RLMP, precision=V.FP64, device=DEV)
-    s.set_adjoint_mode(V.ADJOINT_DIFF_A)
-    with pytest.raises(V.VLBMError) as e:      # LMP with a differentiated dynamic a
-        s.adjoint(u0, 4, 2, s.adjoint_scratch(4, 2), u0=u0)
-    assert e.value.code == V.E_UNSUPPORTED
-    s.close()
     s = V.VLBM(p.nx, p.ny, p.dx, lam=1.0, limiter=V.LIM_PP, precision=V.FP64, device=DEV)
     s.set_conserved(u0[0].contiguous(), u0[1:3].contiguous(), u0[3].contiguous())
     with pytest.raises(V.VLBMError) as e:        # no rollout precedes it
@@ -510,6 +504,45 @@ def test_adjoint_lmp_with_boundaries(case, limiter, kernel):
     fr = TR.ghost_frame(cfg, a, sponge=kw["sponge"])
     x = torch.tensor(cons, dtype=torch.float64, requires_grad=True)
     sN = TR.rollout_frame(x, nsteps, a, limiter, fr)
+    (0.5 * (w.cpu() * (sN[:4] - tgt.cpu()) ** 2).sum()).backward()
+    g_ref = x.grad.numpy()
+    err = np.abs(g.cpu().numpy() - g_ref)
+    assert err.max() <= 1e-9 * np.abs(g_ref).max(), (err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+@pytest.mark.parametrize("kernel", [V.KERNEL_SIMPLE, V.KERNEL_FUSED])
+@pytest.mark.parametrize("case", ["periodic-lmp", "periodic-rlmp", "zg-mirror-lmp", "sponge-rlmp"])
+def test_adjoint_lmp_dynamic_speed(case, kernel):
+    """ADJOINT_DIFF_A with LMP / RLMP: d theta / da of every face (kappa, u*, dF and the
+    bound that won, through rho* of its face) from pass 1, handed to the argmax cell
+    of lambda^n; against autograd of the restatement with a^n = 4 lambda(s^n)."""
+    from tests.test_torch_reference import _box_cfg, _waves, boxed_waves
+    name, lim = case.rsplit("-", 1)
+    limiter = V.LIM_LMP if lim == "lmp" else V.LIM_RLMP
+    if name == "periodic":
+        cons, dx = _waves(32)
+        kw = {"bc": (0, 0, 0, 0), "sponge": 0}
+    else:
+        cons, dx, kw = boxed_waves(name)
+    ny, nx = cons.shape[1:]
+    s = V.VLBM(nx, ny, dx, bc=kw["bc"], limiter=limiter, precision=V.FP64, kernel=kernel, device=DEV,
+               sponge=kw["sponge"])
+    s.set_adjoint_mode(V.ADJOINT_DIFF_A)
+    nsteps, every = 16, 5
+    rng = np.random.default_rng(6)
+    w = torch.tensor(rng.uniform(0.5, 1.5, size=(4, ny, nx)), dtype=torch.float64, device=DEV)
+    tgt = torch.tensor(cons * 0.97, dtype=torch.float64, device=DEV)
+    u0 = torch.tensor(cons, dtype=torch.float64, device=DEV)
+    uN, g = _adjoint(s, u0, nsteps, every, w, tgt)
+    assert s.monitors()["status"] == 0
+    s.close()
+    x = torch.tensor(cons, dtype=torch.float64, requires_grad=True)
+    if name == "periodic":
+        sN = TR.rollout_dynamic(x, nsteps, limiter)
+    else:
+        fr = TR.ghost_frame(_box_cfg(nx, ny, limiter, kw, dx), 1.0, sponge=kw["sponge"])
+        sN = TR.rollout_dynamic_frame(x, nsteps, limiter, fr)
+    assert np.abs(sN[:4].detach().numpy() - uN.cpu().numpy()).max() <= 1e-12 * np.abs(cons).max()
     (0.5 * (w.cpu() * (sN[:4] - tgt.cpu()) ** 2).sum()).backward()
     g_ref = x.grad.numpy()
     err = np.abs(g.cpu().numpy() - g_ref)

@@ -215,3 +215,16 @@ def test_frame_restatement_gradient_matches_differences(case):
         fd = (4.0 * (L(h) - L(-h)) / (2 * h) - (L(2 * h) - L(-2 * h)) / (4 * h)) / 3.0
         ad = float((g * d).sum())
         assert abs(fd - ad) <= 1e-6 * abs(ad), (k, fd, ad)
+
+
+@pytest.mark.parametrize("case", ["zg-mirror", "sponge"])
+def test_frame_dynamic_rollout_matches_oracle(case):
+    """The dynamic-speed rollout inside the frame follows the oracle's run with a^n =
+    4 lambda(s^n) (Sec. 4 preamble)."""
+    cons, dx, kw = boxed_waves(case)
+    ny, nx = cons.shape[1:]
+    cfg = _box_cfg(nx, ny, O.LIM_RLMP, kw, dx)
+    fr = TR.ghost_frame(cfg, 1.0, sponge=kw["sponge"])
+    got = TR.rollout_dynamic_frame(torch.tensor(cons), 8, O.LIM_RLMP, fr).numpy()
+    ref = O.run(cfg, cons, dx, nsteps=8)["state"]
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()

@@ -242,3 +242,14 @@ def rollout_frame(u0, nsteps, a, limiter, frame, alpha=0.5, gamma=1.4, eps=1e-16
     for _ in range(nsteps):
         s = step_frame(s, a, limiter, frame, alpha, gamma, eps)
     return s
+
+
+def rollout_dynamic_frame(u0, nsteps, limiter, frame, alpha=0.5, gamma=1.4, eps=1e-16):
+    """rollout_dynamic inside a ghost frame without prescribed states (whose constant
+    ghost populations would depend on a^n)."""
+    a = 2.0 * speed_max(u0, gamma) / (1.0 - alpha)
+    s = init_populations(u0, a, alpha, gamma)
+    for _ in range(nsteps):
+        s = step_frame(s, a, limiter, frame, alpha, gamma, eps)
+        a = 2.0 * speed_max(s[0:4], gamma) / (1.0 - alpha)
+    return s
