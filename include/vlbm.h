@@ -212,6 +212,17 @@ VLBM_API int vlbm_moments(const vlbm_state *s, void *d_rho, void *d_mom, void *d
  * Returns the sticky device status (VLBM_OK, VLBM_E_POSITIVITY, ...). */
 VLBM_API int vlbm_monitors(vlbm_state *s, vlbm_monitor_t *out);
 
+/* Monitors without waiting for the stream (for a loop that checks every step's
+ * monitors while the next step runs): vlbm_monitors_async enqueues on the state's
+ * stream a copy of the raw step-state record, as the work enqueued so far leaves
+ * it, into h_dst (caller-owned host memory of vlbm_monitors_raw_bytes() bytes;
+ * pinned, or the copy is not asynchronous). Once that copy has completed (the
+ * caller records an event after it, or synchronises), vlbm_monitors_decode turns
+ * the record into *out and returns its sticky status, as vlbm_monitors does. */
+VLBM_API size_t vlbm_monitors_raw_bytes(void);
+VLBM_API int vlbm_monitors_async(vlbm_state *s, void *h_dst);
+VLBM_API int vlbm_monitors_decode(const void *h_src, vlbm_monitor_t *out);
+
 /* Wait for the stream and return the sticky device status. */
 VLBM_API int vlbm_sync(vlbm_state *s);
 

@@ -462,13 +462,7 @@ int vlbm_moments(const vlbm_state *s, void *d_rho, void *d_mom, void *d_E) {
     return VLBM_OK;
 }
 
-int vlbm_monitors(vlbm_state *s, vlbm_monitor_t *out) {
-    if (!s || !out) return fail(s, VLBM_E_INVAL, "state or out is NULL");
-    if (!s->loaded) return fail(s, VLBM_E_INVAL, "no state loaded");
-    DeviceGuard g(s->device);
-    DevCtl h;
-    int rc = read_ctl(s, &h);
-    if (rc) return rc;
+static int decode_ctl(const DevCtl &h, vlbm_monitor_t *out) {
     out->n = h.n;
     out->t = h.t;
     out->a = h.a;
@@ -484,6 +478,34 @@ int vlbm_monitors(vlbm_state *s, vlbm_monitor_t *out) {
     out->done = h.done;
     out->status = h.status;
     return h.status;
+}
+
+int vlbm_monitors(vlbm_state *s, vlbm_monitor_t *out) {
+    if (!s || !out) return fail(s, VLBM_E_INVAL, "state or out is NULL");
+    if (!s->loaded) return fail(s, VLBM_E_INVAL, "no state loaded");
+    DeviceGuard g(s->device);
+    DevCtl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    return decode_ctl(h, out);
+}
+
+size_t vlbm_monitors_raw_bytes(void) { return sizeof(DevCtl); }
+
+int vlbm_monitors_async(vlbm_state *s, void *h_dst) {
+    if (!s || !h_dst) return fail(s, VLBM_E_INVAL, "state or destination is NULL");
+    if (!s->loaded) return fail(s, VLBM_E_INVAL, "no state loaded");
+    DeviceGuard g(s->device);
+    const cudaError_t e = cudaMemcpyAsync(h_dst, s->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copying the device control block");
+    return VLBM_OK;
+}
+
+int vlbm_monitors_decode(const void *h_src, vlbm_monitor_t *out) {
+    if (!h_src || !out) return fail(nullptr, VLBM_E_INVAL, "source or out is NULL");
+    DevCtl h;
+    memcpy(&h, h_src, sizeof h);
+    return decode_ctl(h, out);
 }
 
 int vlbm_sync(vlbm_state *s) {

@@ -117,6 +117,9 @@ _SIGS = {
     "vlbm_step_to": (ctypes.c_int, [_P, _D, _I64]),
     "vlbm_moments": (ctypes.c_int, [_P, _P, _P, _P]),
     "vlbm_monitors": (ctypes.c_int, [_P, ctypes.POINTER(vlbm_monitor_t)]),
+    "vlbm_monitors_raw_bytes": (_SZ, []),
+    "vlbm_monitors_async": (ctypes.c_int, [_P, _P]),
+    "vlbm_monitors_decode": (ctypes.c_int, [_P, ctypes.POINTER(vlbm_monitor_t)]),
     "vlbm_sync": (ctypes.c_int, [_P]),
     "vlbm_time": (ctypes.c_int, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "vlbm_checkpoint_bytes": (_SZ, [_P]),
@@ -190,6 +193,20 @@ def vlbm_moments(s, d_rho, d_mom, d_E) -> int:
 def vlbm_monitors(s):
     m = vlbm_monitor_t()
     rc = _lib.vlbm_monitors(s, ctypes.byref(m))
+    return rc, m
+
+
+def vlbm_monitors_raw_bytes() -> int:
+    return int(_lib.vlbm_monitors_raw_bytes())
+
+
+def vlbm_monitors_async(s, h_dst) -> int:
+    return _lib.vlbm_monitors_async(s, h_dst)
+
+
+def vlbm_monitors_decode(h_src):
+    m = vlbm_monitor_t()
+    rc = _lib.vlbm_monitors_decode(h_src, ctypes.byref(m))
     return rc, m
 
 
@@ -392,15 +409,33 @@ class VLBM:
         _check(vlbm_moments(self._s, rho.data_ptr(), mom.data_ptr(), E.data_ptr()), self._s)
         return rho, mom, E
 
-    def monitors(self) -> dict:
-        rc, m = vlbm_monitors(self._s)
-        if rc == E_CUDA:
-            _check(rc, self._s)
+    @staticmethod
+    def _monitor_dict(m) -> dict:
         return {"status": m.status, "n": m.n, "t": m.t, "a": m.a, "dt": m.dt, "lambda": m.lambda_,
                 "bad_cells": m.bad_cells, "nonfinite_cells": m.nonfinite_cells,
                 "first_bad_step": m.first_bad_step, "min_rho": m.min_rho, "sum": list(m.sum),
                 "theta_p_fp64_faces": m.theta_p_fp64_faces,
                 "min_internal_energy": m.min_internal_energy, "done": m.done}
+
+    def monitors(self) -> dict:
+        rc, m = vlbm_monitors(self._s)
+        if rc == E_CUDA:
+            _check(rc, self._s)
+        return self._monitor_dict(m)
+
+    def monitor_buffer(self):
+        """A pinned host buffer for monitors_async (vlbm_monitors_raw_bytes bytes)."""
+        return self.torch.empty(vlbm_monitors_raw_bytes(), dtype=self.torch.uint8).pin_memory()
+
+    def monitors_async(self, buf):
+        """Enqueue on the solver's stream a copy of the monitors, as the work enqueued so far
+        leaves them, into the pinned buffer `buf` (vlbm_monitors_async); read them with
+        decode_monitors(buf) once the copy has completed."""
+        _check(vlbm_monitors_async(self._s, buf.data_ptr()), self._s)
+
+    def decode_monitors(self, buf) -> dict:
+        rc, m = vlbm_monitors_decode(buf.data_ptr())
+        return self._monitor_dict(m)
 
     def sync(self) -> int:
         return vlbm_sync(self._s)

@@ -268,3 +268,27 @@ def test_monitor_min_density_and_internal_energy(kernel, prec, rtol):
     rhoe = ref[3] - 0.5 * (ref[1] ** 2 + ref[2] ** 2) / ref[0]
     assert abs(mon["min_rho"] - ref[0].min()) <= rtol * ref[0].min()
     assert abs(mon["min_internal_energy"] - rhoe.min()) <= 10 * rtol * rhoe.min()
+
+
+def test_async_monitors_match_synchronous_ones():
+    """vlbm_monitors_async / vlbm_monitors_decode: each step's record, copied while the
+    next step is already enqueued, equals what vlbm_monitors reports after that step."""
+    p = W.quadrant_riemann(96, 64, seed=3)
+    s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, limiter=V.LIM_PP, precision=V.FP32, device="cuda:0")
+    c = torch.tensor(p.conserved(), dtype=torch.float32, device="cuda:0")
+    s.set_conserved(c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+    bufs = [s.monitor_buffer() for _ in range(3)]
+    evs = [torch.cuda.Event() for _ in range(3)]
+    for k in range(3):
+        s.step(1)
+        s.monitors_async(bufs[k])
+        evs[k].record(s.stream)
+    sync = s.monitors()   # after the third step
+    seen = []
+    for k in range(3):
+        evs[k].synchronize()
+        seen.append(s.decode_monitors(bufs[k]))
+    assert [m["n"] for m in seen] == [1, 2, 3]
+    assert seen[2] == sync
+    assert seen[0]["t"] < seen[1]["t"] < seen[2]["t"]
+    s.close()
