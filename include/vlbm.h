@@ -254,7 +254,7 @@ VLBM_API int vlbm_profile_read(vlbm_state *s, double *kernel_ms, int64_t *launch
 
 /* Many independent grids of uneven sizes (one gamma, limiter and precision)
  * advanced together: every time step is one launch of the row-marching kernel
- * over the work items (grid, strip of 120 columns, chunk of rows) of all grids,
+ * over the work items (grid, strip of 120 columns, band of rows) of all grids,
  * persistent CTAs taking items from a shared counter; steps are replayed from
  * a CUDA graph of 64 launches. Each grid keeps its own dynamic kinetic speed
  * a^n = 4 lambda^n (Sec. 4 preamble), time, monitors and ghost frame. */
@@ -267,8 +267,10 @@ typedef struct vlbm_batch vlbm_batch;
                                 the CTA count, within [16, chunk] (guided self-scheduling;
                                 a single vlbm_state always uses it, with chunk 128) */
 
-/* Work decomposition: rows per work item, CTAs per SM, item order; items and
- * CTAs of the resulting launch (outputs). */
+/* Work decomposition: rows per work item (the largest band under GUIDED), CTAs
+ * per SM, item order; items and CTAs of the resulting launch (outputs). A new
+ * batch starts with GUIDED bands of at most 128 rows and as many CTAs per SM as
+ * the kernel's occupancy allows. */
 typedef struct {
     int32_t chunk, ctas_per_sm, order;
     int32_t items, ctas;

@@ -44,7 +44,7 @@ struct vlbm_batch {
     cudaStream_t stream = nullptr;
     int sms = 1;
     // work decomposition (tunable)
-    int chunk = 32, ctas_per_sm = 3, order = VLBM_ORDER_LPT;
+    int chunk = kFusedMaxChunk, ctas_per_sm = 3, order = VLBM_ORDER_GUIDED;   // until set or autotuned
     int nitems = 0;
     std::vector<unsigned char> desc_host;
     std::vector<WorkItem> items_host;
