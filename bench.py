@@ -326,11 +326,12 @@ def run_ours(args):
     peaks, peak_src = _peaks()
     achieved = BYTES_PER_LU * cells / (kernel_ms / launches / 1e3) / 1e9 if launches else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": _ncu_traffic(),
+            "frac": achieved / peaks["hbm_gbs"] if achieved else None,
+            "traffic": _ncu_traffic() if args.n == N_SIDE else None,
             "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})",
             "kernel": "k_step_fused<float, PP>", "kernel_ms_avg": kernel_ms / launches if launches else None}
     nsum = _ncu_summary()
-    if nsum:   # ncu figures of the same kernel (profiles/): DRAM bytes per cell update, FP64 share
+    if nsum and args.n == N_SIDE:   # ncu figures of the same kernel (profiles/): DRAM bytes per cell update, FP64 share
         roof["dram_bytes_per_lu"] = nsum["dram_bytes_per_launch_full_size"] / (N_SIDE * N_SIDE)
         roof["fp64_pipe_pct"] = nsum.get("fp64_pipe_pct")
 
