@@ -219,6 +219,27 @@ def cpu_baseline(n_side: int = N_SIDE, target_s: float = 15.0, max_steps: int = 
                       f"one thread"}
 
 
+def cpu_baseline_batched(probs, steps: int = 50, budget_s: float = 10.0):
+    """The FP64 oracle on this host's cores over the batched workload's grids, in index
+    order, a fixed window of `steps` steps each, until `budget_s` seconds have passed."""
+    from oracle import oracle as O
+
+    cores = os.cpu_count() or 1
+    O.set_threads(cores)
+    lu, grids, t0 = 0, 0, time.perf_counter()
+    for p in probs:
+        cfg = O.Config(p.nx, p.ny, p.bc, O.LIM_PP, p.gamma, 0.5, EPS, SPONGE)
+        O.run(cfg, p.conserved(), p.dx, nsteps=steps)
+        lu += p.nx * p.ny * steps
+        grids += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": lu / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"the first {grids} of the {len(probs)} grids, {steps} steps each from t = 0, on "
+                      f"{cores} threads (FP64 oracle, OpenMP over rows)"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -352,7 +373,7 @@ def run_ours(args):
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof}
         if not args.no_batched:
-            line["batched"] = bench_batched(dev)
+            line["batched"] = bench_batched(dev, cpu=world == 1 and not args.no_cpu_baseline)
         if not args.no_adjoint:
             line["adjoint"] = bench_adjoint(dev)
         if world == 1 and not args.no_cpu_baseline:
@@ -363,7 +384,7 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def bench_batched(dev, steps: int = 500, count: int = 256):
+def bench_batched(dev, steps: int = 500, count: int = 256, cpu: bool = False):
     """256 seeded quadrant problems of uneven sides (multiples of 64 up to 1024), FP32 PP:
     one launch per step over all grids (graph-replayed, autotuned decomposition) against
     the same problems stepped one grid at a time with one launch per grid and step."""
@@ -433,7 +454,8 @@ def bench_batched(dev, steps: int = 500, count: int = 256):
                                "one-thread-per-cell kernel below 2^19 cells)",
             "tuning": tuning,
             "statuses_nonzero": sum(1 for x in status if x),
-            "fp64_theta_p_faces_last_step": fp64_faces}
+            "fp64_theta_p_faces_last_step": fp64_faces,
+            "cpu_baseline": cpu_baseline_batched(probs) if cpu else None}
 
 
 def bench_adjoint(dev, n: int = 512, steps: int = 500, every: int = 50):
