@@ -240,6 +240,13 @@ def cpu_baseline_batched(probs, steps: int = 50, budget_s: float = 10.0):
                       f"{cores} threads (FP64 oracle, OpenMP over rows)"}
 
 
+def workload_config(n: int, world: int) -> dict:
+    """The workload both arms time (the reference arm on a bounded sample of its steps)."""
+    return {"workload": f"blast {n}x{n} near-vacuum (rho=1, p=1e-6, E=1 in 2x2 centre), reflective walls, "
+                        "2nd order + PP limiter eps=1e-13, dynamic a^n",
+            "nx": n, "ny": n, "limiter": "PP", "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -249,7 +256,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"blast {args.n}x{args.n}, PP eps=1e-13, reflective walls (oracle sample)"},
+            "config": dict(workload_config(args.n, args.gpus), precision="fp64 (FP64 oracle)"),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -361,15 +368,13 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"blast {p.nx}x{p.ny} near-vacuum (rho=1, p=1e-6, E=1 in 2x2 centre), "
-                                       "reflective walls, 2nd order + PP limiter eps=1e-13, FP32 state "
-                                       "with FP64 theta_p solve, dynamic a^n",
-                           "nx": p.nx, "ny": p.ny, "precision": "fp32", "limiter": "PP",
-                           "l2": "state 2x1.34 GB >> L2 129 MB; no flush",
-                           "parallelism": f"replicas x{world}",
-                           "steps_total": args.warmup + args.steps,
-                           "positivity_violations": mon["bad_cells"] + mon["nonfinite_cells"],
-                           "first_bad_step": mon["first_bad_step"], "status": mon["status"]},
+                "config": dict(workload_config(p.nx, world),
+                               precision="fp32 (FP32 populations; FP64 theta_p solve where the float "
+                                         "bounds cannot settle a face; FP64 sums)",
+                               l2="state 2x1.34 GB >> L2 129 MB; no flush",
+                               steps_total=args.warmup + args.steps,
+                               positivity_violations=mon["bad_cells"] + mon["nonfinite_cells"],
+                               first_bad_step=mon["first_bad_step"], status=mon["status"]),
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof}
         if not args.no_batched:
