@@ -22,7 +22,8 @@
 //  P3  theta of the x-faces of row R - 1 and of y-face R - 3/2 (Sec. 3.3-3.4);
 //      then u*, dF of the x-faces of row R and of y-face R - 1/2.
 // Barriers: S1 after P1 (the ring row R and the previous row's theta are
-// complete), S2 after P2 (LMP / RLMP only).
+// complete); the bounds a thread needs of its right neighbour (LMP / RLMP) it forms
+// itself from the shared rows.
 //  P4  collide + stream of row O (eq. blending_u1 / blending_u), stores, ghost
 //      images, monitors.
 // Output rows start on 32-byte sector boundaries (kOX = 8, strips of 120 floats),
@@ -45,7 +46,6 @@ struct FusedSmem {
     T raw[kRawSlots][kNPlane][kFB];
     T X[kXSlots][16][kFB];     // u (0..3), f (4..7), d_1 (8..11), d_2 (12..15)
     T rsx[2][kFB];             // rho* of x-face (b, b+1)
-    T mu[2][kFB], nu[2][kFB];  // density bounds
     T thx[2][kFB];             // theta of x-face (b, b+1)
     unsigned long long bar[kRawSlots];
     int item;
@@ -224,17 +224,33 @@ struct FusedCtx {
         }
     }
 
-    // LMP density bounds (eq. LMP_minmax) of row R - 1, own column: rho of the cell
-    // and rho* of its four faces.
-    __device__ __forceinline__ void bounds(int R, T rsy_new, int bl, T &mu, T &nu) const {
-        const int rp = (R - 1) & 1;
-        const T v0 = h1.u[0], v1 = S.rsx[rp][bl], v2 = S.rsx[rp][b];
-        mu = fmin(fmin(fmin(v0, v1), fmin(v2, rsy_prev)), rsy_new);
-        nu = fmax(fmax(fmax(v0, v1), fmax(v2, rsy_prev)), rsy_new);
-        if (LIM == VLBM_LIM_RLMP) {  // Sec. 3.3.2
+    // LMP density bounds (eq. LMP_minmax): min / max of rho of a cell and rho* of its
+    // west, east, south and north faces (exact), RLMP scaled (Sec. 3.3.2).
+    __device__ __forceinline__ void minmax5(T v0, T v1, T v2, T v3, T v4, T &mu, T &nu) const {
+        mu = fmin(fmin(fmin(v0, v1), fmin(v2, v3)), v4);
+        nu = fmax(fmax(fmax(v0, v1), fmax(v2, v3)), v4);
+        if (LIM == VLBM_LIM_RLMP) {
             mu = RN<T>::mul(mu, T(0.999));
             nu = RN<T>::mul(nu, T(1.001));
         }
+    }
+
+    // Bounds of row R - 1, own column.
+    __device__ __forceinline__ void bounds(int R, T rsy_new, int bl, T &mu, T &nu) const {
+        const int rp = (R - 1) & 1;
+        minmax5(h1.u[0], S.rsx[rp][bl], S.rsx[rp][b], rsy_prev, rsy_new, mu, nu);
+    }
+
+    // Bounds of row R - 1 of the column to the right (br), from the shared rows R - 2 ..
+    // R (rho and the y-momentum, the y-flux of rho) and the x-faces' rho*: the same
+    // operations on the same values as that column's own thread, so the same bits,
+    // without a barrier to publish them.
+    __device__ __forceinline__ void bounds_right(int R, int br, T &mu, T &nu) const {
+        const int rp = (R - 1) & 1, x0 = (R - 2) & 3, x1 = (R - 1) & 3, x2 = R & 3;
+        const T r1 = S.X[x1][0][br], m1 = S.X[x1][2][br];
+        const T syp = face_star(S.X[x0][0][br], S.X[x0][2][br], r1, m1, k);
+        const T syn = face_star(r1, m1, S.X[x2][0][br], S.X[x2][2][br], k);
+        minmax5(r1, S.rsx[rp][b], S.rsx[rp][br], syp, syn, mu, nu);
     }
 
     // The rows of an item before row y0 + 1: no output row of the item uses their
@@ -274,13 +290,10 @@ struct FusedCtx {
 
         const int bl = b > 0 ? b - 1 : 0, br = b < kFB - 1 ? b + 1 : b;
         // ---------------------------------------------------------------- P2
-        T mu1 = T(0), nu1 = T(0);
+        T mu1 = T(0), nu1 = T(0), muR = T(0), nuR = T(0);
         if (LIM == VLBM_LIM_LMP || LIM == VLBM_LIM_RLMP) {
-            const int rp = (R - 1) & 1;
             bounds(R, rsy_new, bl, mu1, nu1);
-            S.mu[rp][b] = mu1;
-            S.nu[rp][b] = nu1;
-            __syncthreads();                                              // S2
+            bounds_right(R, br, muR, nuR);
         }
         // ---------------------------------------------------------------- P3
         T tx, ty;
@@ -311,9 +324,7 @@ struct FusedCtx {
                 trx = pp_density_target(xs_us[0], xs_df[0], k);
                 try_ = pp_density_target(ys_us[0], ys_df[0], k);
             } else {
-                const int rp = (R - 1) & 1;
-                trx = theta_rho_lmp(xs_us[0], xs_df[0], S.mu[rp][b], S.nu[rp][b], S.mu[rp][br],
-                                    S.nu[rp][br], k);
+                trx = theta_rho_lmp(xs_us[0], xs_df[0], mu1, nu1, muR, nuR, k);
                 try_ = theta_rho_lmp(ys_us[0], ys_df[0], mu2, nu2, mu1, nu1, k);
             }
             unsigned int nx64 = 0, ny64 = 0;
