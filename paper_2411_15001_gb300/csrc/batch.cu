@@ -77,8 +77,8 @@ static bool grid_ok(const vlbm_grid &g) {
 }
 
 // Workspace layout: the grids' state buffers, then n control blocks, n descriptors
-// (arrays indexed by grid), the work counter and the item table (sized for the
-// smallest chunk).
+// (arrays indexed by grid), the work counter and the item table (sized for bands
+// of the smallest height, max_items).
 static size_t plan_layout(vlbm_batch *b, int n, const vlbm_grid *grids, int elem) {
     b->L.resize(n);
     b->buf_off.resize(n);
