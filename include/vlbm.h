@@ -344,8 +344,11 @@ VLBM_API const char *vlbm_batch_last_error(const vlbm_batch *b);
  * it) are covered on every grid (with a boundary the bounds of the first ghost
  * layer reach the second, and both layers are folded back), a^n held or
  * differentiated (d theta / da then includes the bound's dependence on a through
- * rho* of the face where it was taken). VLBM_ADJOINT_DIFF_A with a prescribed
- * boundary state returns VLBM_E_UNSUPPORTED.
+ * rho* of the face where it was taken). With VLBM_ADJOINT_DIFF_A and a prescribed
+ * boundary state, the prescribed ghosts' populations M_k(u_field; a^n) add their
+ * dL/da^n (the field itself is piecewise constant in time: no time derivative),
+ * and a step whose lambda^n is set by the prescribed states hands nothing to the
+ * cells.
  *
  * Memory: checkpoints of the state every ckpt_every steps, a segment buffer of
  * ckpt_every + 1 states for the recomputation, and two cotangent buffers, all in

@@ -93,13 +93,16 @@ static cudaError_t launch_adjoint_init(const T *init_state, const Layout &L, con
 
 // Transpose of the ghost fill on the padded cotangent (np ghost layers), then its
 // interior into cot.
+// With abar (a differentiated a^n), the prescribed ghosts' dL/da^n is added at the
+// step's constants k and time t.
 template <typename T>
-static cudaError_t fold_ghosts(T *pad, int np, const vlbm_state *s, T *cot, cudaStream_t st) {
+static cudaError_t fold_ghosts(T *pad, int np, const vlbm_state *s, T *cot, cudaStream_t st, const StepConsts<T> *k,
+                               const double *t, double *abar) {
     int bc[4];
     uniform_types(s->bd, bc);
     const int nx = s->grid.nx, ny = s->grid.ny;
-    k_adjoint_fold_y<T><<<(nx + 2 * np + 127) / 128, 128, 0, st>>>(pad, nx, ny, np, s->bd, bc[2], bc[3]);
-    k_adjoint_fold_x<T><<<(ny + 127) / 128, 128, 0, st>>>(pad, nx, ny, np, s->bd, bc[0], bc[1]);
+    k_adjoint_fold_y<T><<<(nx + 2 * np + 127) / 128, 128, 0, st>>>(pad, nx, ny, np, s->bd, bc[2], bc[3], k, t, abar);
+    k_adjoint_fold_x<T><<<(ny + 127) / 128, 128, 0, st>>>(pad, nx, ny, np, s->bd, bc[0], bc[1], k, t, abar);
     const dim3 blk(32, 8), grd((nx + 31) / 32, (ny + 7) / 8);
     k_adjoint_unpad<T><<<grd, blk, 0, st>>>(pad, nx, ny, np, cot);
     return cudaGetLastError();
@@ -116,12 +119,12 @@ struct ARed {
 // cell where lambda(st) is largest; the slots are reset for the next step.
 template <typename T>
 static cudaError_t hand_over_abar(const T *st, const Layout &L, double gamma, double alpha, ARed *red, T *cot,
-                                  cudaStream_t s) {
+                                  const double *lam_bc, cudaStream_t s) {
     const dim3 blk(32, 8), grd((L.nx + 31) / 32, (L.ny + 7) / 8);
     k_lambda_max<T><<<grd, blk, 0, s>>>(st, L.plane, L.pitch, L.nx, L.ny, (T)gamma, &red->key);
     k_lambda_argmax<T><<<grd, blk, 0, s>>>(st, L.plane, L.pitch, L.nx, L.ny, (T)gamma, &red->key, &red->idx);
     k_lambda_apply<T><<<1, 1, 0, s>>>(st, L.plane, L.pitch, L.nx, gamma, alpha, &red->abar, &red->key, &red->idx, cot,
-                                      (long long)L.nx * L.ny);
+                                      (long long)L.nx * L.ny, lam_bc);
     return cudaGetLastError();
 }
 
@@ -135,8 +138,9 @@ template <> const StepConsts<double> *ctl_consts<double>(const DevCtl *C) { retu
 namespace {
 
 constexpr size_t kCtlBytes = ((sizeof(DevCtl) + 255) / 256) * 256;
-constexpr size_t kConstSlot = 128;   // one StepConsts<T> of the constants history
-static_assert(sizeof(StepConsts<double>) <= kConstSlot && sizeof(StepConsts<float>) <= kConstSlot, "slot");
+constexpr size_t kConstSlot = 128;   // one StepConsts<T> of the constants history, then t^n
+constexpr size_t kSlotTime = 120;    // offset of t^n (double) in a slot
+static_assert(sizeof(StepConsts<double>) <= kSlotTime && sizeof(StepConsts<float>) <= kSlotTime, "slot");
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -147,7 +151,7 @@ struct Plan {
     size_t seg_off;       // k + 1 state slots (slot 0 is only ever a TMA window start)
     size_t segctl_off;    // control block of the recomputation
     size_t desc_off;      // 2 k InstDesc of the row-marching kernel (by parity of n)
-    size_t khist_off;     // the step constants (a^n) of each step of a segment
+    size_t khist_off;     // the step constants (a^n) and the time t^n of each step of a segment
     size_t cot_off;       // two cotangent buffers of 20 compact planes
     size_t cot_bytes;
     size_t red_off;       // the dL/da hand-over slots
@@ -333,6 +337,9 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
             if (!fixed_a)
                 e = cudaMemcpyAsync(khist + (m - s0) * kConstSlot, ctl_consts<T>(segctl), sizeof(StepConsts<T>),
                                     cudaMemcpyDeviceToDevice, s->stream);
+            if (e == cudaSuccess && diff_a)
+                e = cudaMemcpyAsync(khist + (m - s0) * kConstSlot + kSlotTime, &segctl->t, sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s->stream);
             if (e == cudaSuccess && m < e0) e = recompute_step<T>(s, scratch, p, every, m, m - s0);
         }
         if (e == cudaSuccess) e = dirichlet_slot<T>(s, scratch, p, e0, e0 - s0);   // the segment's last state
@@ -343,11 +350,13 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
             A.cot_out = A.ext ? pad : cot[cur ^ 1];
             A.k = fixed_a ? ctl_consts<T>(segctl) : (const StepConsts<T> *)(khist + (m - s0) * kConstSlot);
             e = launch_adjoint_step<T>(A, s->limiter, s->stream);
-            if (e == cudaSuccess && A.ext) e = fold_ghosts<T>(pad, A.pad, s, cot[cur ^ 1], s->stream);
+            if (e == cudaSuccess && A.ext)
+                e = fold_ghosts<T>(pad, A.pad, s, cot[cur ^ 1], s->stream, A.k,
+                                   (const double *)(khist + (m - s0) * kConstSlot + kSlotTime), A.abar);
             if (e != cudaSuccess) return cuda_fail(s, e, "adjoint step launch");
             cur ^= 1;
             if (diff_a && m > 0) {   // a^m came from lambda of s^m (a^0 waits for the init map)
-                e = hand_over_abar<T>(A.fwd, s->L, s->gamma, s->alpha, red, cot[cur], s->stream);
+                e = hand_over_abar<T>(A.fwd, s->L, s->gamma, s->alpha, red, cot[cur], &segctl->lam_bc, s->stream);
                 if (e != cudaSuccess) return cuda_fail(s, e, "kinetic-speed cotangent launch");
             }
         }
@@ -356,7 +365,7 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     e = launch_adjoint_init<T>((const T *)ck0, s->L, ctl_consts<T>((const DevCtl *)(ck0 + round256(buf))), cot[cur],
                                (T *)dLdu0, diff_a ? &red->abar : nullptr, s->stream);
     if (e == cudaSuccess && diff_a)
-        e = hand_over_abar<T>((const T *)ck0, s->L, s->gamma, s->alpha, red, (T *)dLdu0, s->stream);
+        e = hand_over_abar<T>((const T *)ck0, s->L, s->gamma, s->alpha, red, (T *)dLdu0, &segctl->lam_bc, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "initialisation adjoint launch");
     return VLBM_OK;
 }
@@ -395,8 +404,6 @@ int vlbm_adjoint(vlbm_state *s, const void *d_u0, int64_t nsteps, int32_t ckpt_e
     if (!s) return fail(nullptr, VLBM_E_INVAL, "state is NULL");
     if (nsteps < 0 || ckpt_every < 1) return fail(s, VLBM_E_INVAL, "need nsteps >= 0 and ckpt_every >= 1");
     if (!d_dLduN || !d_dLdu0) return fail(s, VLBM_E_INVAL, "cotangent pointer is NULL");
-    if (s->adj_mode == VLBM_ADJOINT_DIFF_A && s->a_fixed <= 0.0 && s->bd.has_dir)
-        return fail(s, VLBM_E_UNSUPPORTED, "differentiating a^n with a prescribed boundary state");
     DeviceGuard g(s->device);
     const Plan p = plan_of(s, nsteps, ckpt_every);
     int rc = check_scratch(s, d_scratch, scratch_bytes, p);

@@ -803,15 +803,19 @@ __global__ void __launch_bounds__(256) k_lambda_argmax(const T *st, long long pl
 
 // One thread: cot[q][idx] += abar * 2 / (1 - alpha) * d lambda / d u_q at the argmax
 // cell (lambda = |v| + sqrt(gamma p / rho)); then the slots are reset.
+// When the prescribed boundary states' speed lam_bc exceeds every cell's (the step
+// compares them the same way), lambda^n does not depend on the state: nothing is added.
 template <typename T>
 __global__ void k_lambda_apply(const T *st, long long plane, int pitch, int nx, double gamma, double alpha,
-                               double *abar, unsigned long long *key, unsigned int *idx, T *cot, long long N) {
+                               double *abar, unsigned long long *key, unsigned int *idx, T *cot, long long N,
+                               const double *lam_bc) {
     const unsigned int id = *idx;
     const double ab = *abar;
+    const bool bc_wins = *lam_bc > key_to_double(*key);
     *abar = 0.0;
     *key = 0ull;
     *idx = 0xffffffffu;
-    if (id == 0xffffffffu || ab == 0.0) return;
+    if (id == 0xffffffffu || ab == 0.0 || bc_wins) return;
     const int i = (int)(id % (unsigned)nx), j = (int)(id / (unsigned)nx);
     const CellLoad<T> L{st, plane, pitch};
     T ut[4];
@@ -857,39 +861,69 @@ __device__ __forceinline__ void fold_one(T *cot, long long Np, int w, int pad, i
     }
 }
 
+// dL/da^n of a prescribed ghost: its populations are M_k(u_field; a^n), u_field the
+// field at the cell's centre at t^n (piecewise constant in t: no time derivative
+// almost everywhere); dM_{1,3}/da = -F/(2a^2), dM_{2,4}/da = +F/(2a^2).
 template <typename T>
-__global__ void k_adjoint_fold_y(T *cot, int nx, int ny, int pad, Bound bd, int bc2, int bc3) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;   // one thread per column -pad .. nx + pad - 1
+__device__ __forceinline__ double prescribed_abar(const T *cot, long long Np, long long g, const Bound &bd, int gi,
+                                                  int gj, double t, const StepConsts<T> &k) {
+    T u[4], f[4], gf[4];
+    field_state(bd, gi, gj, t, u);
+    euler_fluxes(u, k.gm1, f, gf);
+    const T h = k.inv2a / k.a;
+    double ab = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        ab += (double)(((cot[(8 + c) * Np + g] - cot[(4 + c) * Np + g]) * f[c] +
+                        (cot[(16 + c) * Np + g] - cot[(12 + c) * Np + g]) * gf[c]) * h);
+    return ab;
+}
+
+template <typename T>
+__global__ void k_adjoint_fold_y(T *cot, int nx, int ny, int pad, Bound bd, int bc2, int bc3,
+                                 const StepConsts<T> *k, const double *t, double *abar) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;   // one thread per column -pad .. nx + pad - 1
     const int w = nx + 2 * pad;
-    if (t >= w) return;
-    const int gi = t - pad;
+    if (tid >= w) return;
+    const int gi = tid - pad;
     const long long Np = (long long)w * (ny + 2 * pad);
+    double ab = 0.0;
     for (int l = 0; l < 2 * pad; ++l) {
         const int gj = l < pad ? -1 - l : ny + (l - pad);
         const int s = gj < 0 ? 2 : 3;
         const int type = (s == 2 ? bc2 : bc3) >= 0 ? (s == 2 ? bc2 : bc3) : side_type(bd, s, gi);
-        if (type == VLBM_BC_DIRICHLET) continue;
+        if (type == VLBM_BC_DIRICHLET) {
+            if (abar) ab += prescribed_abar(cot, Np, (long long)(gj + pad) * w + (gi + pad), bd, gi, gj, *t, *k);
+            continue;
+        }
         bool my;
         const int sj = ghost_source_typed(gj, ny, type, &my);
         fold_one(cot, Np, w, pad, gi, gj, gi, sj, false, my);
     }
+    if (abar && ab != 0.0) atomicAdd(abar, ab);
 }
 
 template <typename T>
-__global__ void k_adjoint_fold_x(T *cot, int nx, int ny, int pad, Bound bd, int bc0, int bc1) {
+__global__ void k_adjoint_fold_x(T *cot, int nx, int ny, int pad, Bound bd, int bc0, int bc1,
+                                 const StepConsts<T> *k, const double *t, double *abar) {
     const int gj = blockIdx.x * blockDim.x + threadIdx.x;   // one thread per interior row
     if (gj >= ny) return;
     const int w = nx + 2 * pad;
     const long long Np = (long long)w * (ny + 2 * pad);
+    double ab = 0.0;
     for (int l = 0; l < 2 * pad; ++l) {
         const int gi = l < pad ? -1 - l : nx + (l - pad);
         const int s = gi < 0 ? 0 : 1;
         const int type = (s == 0 ? bc0 : bc1) >= 0 ? (s == 0 ? bc0 : bc1) : side_type(bd, s, gj);
-        if (type == VLBM_BC_DIRICHLET) continue;
+        if (type == VLBM_BC_DIRICHLET) {   // (the corners the y fold moved here included)
+            if (abar) ab += prescribed_abar(cot, Np, (long long)(gj + pad) * w + (gi + pad), bd, gi, gj, *t, *k);
+            continue;
+        }
         bool mx;
         const int si = ghost_source_typed(gi, nx, type, &mx);
         fold_one(cot, Np, w, pad, gi, gj, si, gj, mx, false);
     }
+    if (abar && ab != 0.0) atomicAdd(abar, ab);
 }
 
 // Interior of a padded cotangent into compact planes.

@@ -431,16 +431,45 @@ def test_adjoint_fd_with_boundaries(case, limiter, kernel):
     s.close()
 
 
-def test_adjoint_rejects_diff_a_with_prescribed_states():
-    p, _ = _boxed("dirichlet-split")
-    b = V.make_boundary(p.bc, p.bc_hi, p.split, p.x0, p.y0, p.bfield)
-    s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, limiter=V.LIM_PP, precision=V.FP64, device=DEV, boundary=b)
+@pytest.mark.parametrize("kernel", [V.KERNEL_SIMPLE, V.KERNEL_FUSED])
+@pytest.mark.parametrize("case", ["pp", "lmp", "pp-fast-field", "lmp-fast-field"])
+def test_adjoint_dynamic_speed_with_prescribed_states(case, kernel):
+    """ADJOINT_DIFF_A with prescribed boundary states (two sides, and a south side that
+    switches from mirror to zero gradient): a prescribed ghost's populations are its
+    Maxwellians at a^n, so the fold adds their dL/da^n; when the prescribed state is
+    faster than every cell (fast-field) lambda^n does not depend on the state. Against
+    autograd of the restatement whose ghost constants follow a^n."""
+    from tests.test_torch_reference import _box_cfg, boxed_waves
+    limiter = V.LIM_LMP if case.startswith("lmp") else V.LIM_PP
+    cons, dx, kw = boxed_waves("dirichlet-split")
+    cons = cons * (1.0 + 1e-3 * np.random.default_rng(13).uniform(-1.0, 1.0, cons.shape))
+    ny, nx = cons.shape[1:]
+    if case.endswith("fast-field"):
+        st = W._conserved_state(1.0, 2.5, 0.0, 1.0, 1.4)
+        kw["field"] = O.Field(st, st, ())
+    r, m1, m2, E = kw["field"].inside
+    v2 = (m1 * m1 + m2 * m2) / (r * r)
+    lam_bc = float(np.sqrt(v2) + np.sqrt(1.4 * 0.4 * (E - 0.5 * r * v2) / r))
+    boundary = V.make_boundary(kw["bc"], kw["bc_hi"], kw["split"], 0.0, 0.0, kw["field"])
+    s = V.VLBM(nx, ny, dx, bc=kw["bc"], limiter=limiter, precision=V.FP64, kernel=kernel, device=DEV,
+               boundary=boundary)
     s.set_adjoint_mode(V.ADJOINT_DIFF_A)
-    u0 = torch.tensor(p.conserved(), dtype=torch.float64, device=DEV)
-    sc = s.adjoint_scratch(4, 2)
-    with pytest.raises(V.VLBMError):
-        s.adjoint(u0.clone(), 4, 2, sc, u0=u0)
+    nsteps, every = 12, 5
+    rng = np.random.default_rng(7)
+    w = torch.tensor(rng.uniform(0.5, 1.5, size=(4, ny, nx)), dtype=torch.float64, device=DEV)
+    tgt = torch.tensor(cons * 0.97, dtype=torch.float64, device=DEV)
+    u0 = torch.tensor(cons, dtype=torch.float64, device=DEV)
+    uN, g = _adjoint(s, u0, nsteps, every, w, tgt)
+    assert s.monitors()["status"] == 0
     s.close()
+    fr = TR.ghost_frame(_box_cfg(nx, ny, limiter, kw, dx), 1.0, const_in_a=True)
+    x = torch.tensor(cons, dtype=torch.float64, requires_grad=True)
+    sN = TR.rollout_dynamic_frame(x, nsteps, limiter, fr, lam_bc=lam_bc)
+    assert np.abs(sN[:4].detach().numpy() - uN.cpu().numpy()).max() <= 1e-12 * np.abs(cons).max()
+    (0.5 * (w.cpu() * (sN[:4] - tgt.cpu()) ** 2).sum()).backward()
+    g_ref = x.grad.numpy()
+    err = np.abs(g.cpu().numpy() - g_ref)
+    assert err.max() <= 1e-9 * np.abs(g_ref).max(), (err.max(), np.unravel_index(err.argmax(), err.shape))
 
 
 @pytest.mark.parametrize("kernel", [V.KERNEL_SIMPLE, V.KERNEL_FUSED])

@@ -228,3 +228,24 @@ def test_frame_dynamic_rollout_matches_oracle(case):
     got = TR.rollout_dynamic_frame(torch.tensor(cons), 8, O.LIM_RLMP, fr).numpy()
     ref = O.run(cfg, cons, dx, nsteps=8)["state"]
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_frame_dynamic_rollout_with_prescribed_states_matches_oracle():
+    """With prescribed states the frame's constants follow a^n (their Maxwellians), and
+    lambda^n covers the states' speed: the dynamic rollout follows the oracle's run."""
+    cons, dx, kw = boxed_waves("dirichlet-split")
+    ny, nx = cons.shape[1:]
+    for fast in (False, True):
+        kw2 = dict(kw)
+        if fast:   # a prescribed state faster than every cell: a^n = 4 lambda_bc
+            st = W._conserved_state(1.0, 2.5, 0.0, 1.0, 1.4)
+            kw2["field"] = O.Field(st, st, ())
+        cfg = _box_cfg(nx, ny, O.LIM_LMP, kw2, dx)
+        fr = TR.ghost_frame(cfg, 1.0, const_in_a=True)
+        st = kw2["field"].inside
+        r, m1, m2, E = st
+        v2 = (m1 * m1 + m2 * m2) / (r * r)
+        lam_bc = float(np.sqrt(v2) + np.sqrt(1.4 * 0.4 * (E - 0.5 * r * v2) / r))
+        got = TR.rollout_dynamic_frame(torch.tensor(cons), 8, O.LIM_LMP, fr, lam_bc=lam_bc).numpy()
+        ref = O.run(cfg, cons, dx, nsteps=8)["state"]
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), fast

@@ -196,14 +196,16 @@ def rollout_dynamic(u0, nsteps, limiter, alpha=0.5, gamma=1.4, eps=1e-16):
     return s
 
 
-def ghost_frame(cfg, a, t=0.0, sponge=0):
+def ghost_frame(cfg, a, t=0.0, sponge=0, const_in_a=False):
     """The oracle's ghost fill (two layers, x rule then y rule) as a gather: every
     entry of the padded (20, ny + 4, nx + 4) array is sign x one state entry, or a
     constant (a prescribed state's value, which does not depend on the state). The
     map is read off the oracle by filling a state whose entries are distinct codes
     (and twice those codes: a constant does not change). With sponge = w > 0, the
     faces with theta = 0 of the sponge layer (Sec. 4.2: every face of a cell within
-    w cells of a zero-gradient side, ghost cells included; sides of one type)."""
+    w cells of a zero-gradient side, ghost cells included; sides of one type).
+    const_in_a: also the constants as c0 + c1 / a (a prescribed ghost's populations are
+    its Maxwellians, affine in 1 / a), read off fills at a and 2a, for a^n that varies."""
     import numpy as np
 
     from oracle import oracle as O
@@ -219,6 +221,10 @@ def ghost_frame(cfg, a, t=0.0, sponge=0):
     frame = {"src": torch.tensor(np.where(lin, np.abs(e1) - 1.0, 0.0).astype(np.int64)),
              "sign": torch.tensor(np.where(lin, np.sign(e1), 0.0)),
              "cval": torch.tensor(np.where(const, e1, 0.0))}
+    if const_in_a:
+        e3 = O.fill_ghosts(cfg, code, 2.0 * a, t)
+        frame["c1"] = torch.tensor(np.where(const, 2.0 * a * (e1 - e3), 0.0))
+        frame["c0"] = torch.tensor(np.where(const, 2.0 * e3 - e1, 0.0))
     if sponge > 0:
         I, J = np.meshgrid(np.arange(-2, nx + 2), np.arange(-2, ny + 2))
         zg = [b == 1 for b in cfg.bc]
@@ -232,7 +238,8 @@ def ghost_frame(cfg, a, t=0.0, sponge=0):
 def step_frame(s, a, limiter, frame, alpha=0.5, gamma=1.4, eps=1e-16):
     """One step of a grid with a boundary: the ghost frame gathered from s, the step
     on the padded array, its interior returned."""
-    P = frame["sign"] * s.reshape(-1)[frame["src"]] + frame["cval"]
+    cval = frame["c0"] + frame["c1"] / a if "c1" in frame else frame["cval"]
+    P = frame["sign"] * s.reshape(-1)[frame["src"]] + cval
     out = _core(P, a, limiter, alpha, gamma, eps, frame.get("sponge_x"), frame.get("sponge_y"))
     return out[:, 2:-2, 2:-2]
 
@@ -244,12 +251,19 @@ def rollout_frame(u0, nsteps, a, limiter, frame, alpha=0.5, gamma=1.4, eps=1e-16
     return s
 
 
-def rollout_dynamic_frame(u0, nsteps, limiter, frame, alpha=0.5, gamma=1.4, eps=1e-16):
-    """rollout_dynamic inside a ghost frame without prescribed states (whose constant
-    ghost populations would depend on a^n)."""
-    a = 2.0 * speed_max(u0, gamma) / (1.0 - alpha)
+def rollout_dynamic_frame(u0, nsteps, limiter, frame, alpha=0.5, gamma=1.4, eps=1e-16, lam_bc=0.0):
+    """rollout_dynamic inside a ghost frame; with prescribed states the frame carries
+    its constants as functions of a (const_in_a), and lambda^n also covers the
+    prescribed states' speed lam_bc (Sec. 4 preamble; cells win a tie)."""
+    lb = torch.tensor(lam_bc, dtype=u0.dtype)
+
+    def speed(u):
+        sc = speed_max(u, gamma)
+        return torch.where(lb > sc, lb, sc)
+
+    a = 2.0 * speed(u0) / (1.0 - alpha)
     s = init_populations(u0, a, alpha, gamma)
     for _ in range(nsteps):
         s = step_frame(s, a, limiter, frame, alpha, gamma, eps)
-        a = 2.0 * speed_max(s[0:4], gamma) / (1.0 - alpha)
+        a = 2.0 * speed(s[0:4]) / (1.0 - alpha)
     return s
