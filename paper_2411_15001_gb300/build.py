@@ -23,8 +23,9 @@ def sources():
 
 
 def _deps():
+    inc = os.path.join(HERE, "..", "include")
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [
-        os.path.join(HERE, "..", "include", "vlbm.h")]
+        os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
 
 
 def _compile(src: str, verbose: bool) -> str:

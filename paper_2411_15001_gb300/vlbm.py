@@ -150,6 +150,9 @@ _SIGS = {
     "vlbm_destroy": (None, [_P]),
     "vlbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vlbm_last_error_detail": (ctypes.c_int, [_P, ctypes.c_char_p, _SZ]),
+    # test hooks (include/vlbm_testing.h)
+    "vlbm_test_theta_faces": (ctypes.c_int, [_I64, _D, _D, _D, _P, _P, _P, _P]),
+    "vlbm_test_wait_probe": (ctypes.c_int, [_P, ctypes.c_uint32]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -343,6 +346,19 @@ def vlbm_last_error_detail(s=None) -> str:
     return buf.value.decode()
 
 
+THETA_STAGE_NONE, THETA_STAGE_SCREEN, THETA_STAGE_INTERVAL, THETA_STAGE_FP64 = range(4)
+
+
+def vlbm_test_theta_faces(n: int, a: float, alpha: float, eps: float, d_faces, d_theta, d_stage, stream) -> int:
+    """FP32 theta of n caller-supplied faces (test hook, include/vlbm_testing.h)."""
+    return _lib.vlbm_test_theta_faces(n, a, alpha, eps, d_faces, d_theta, d_stage, stream)
+
+
+def vlbm_test_wait_probe(s, limit_ns: int) -> int:
+    """Arm (limit_ns > 0) or disarm the row-marching kernel's wait probe (test hook)."""
+    return _lib.vlbm_test_wait_probe(s, limit_ns)
+
+
 def _check(rc: int, s=None) -> int:
     if rc != OK:
         raise VLBMError(rc, vlbm_last_error_detail(s))
@@ -350,6 +366,31 @@ def _check(rc: int, s=None) -> int:
 
 
 # ------------------------------------------------------------------ torch front end
+class _StreamOrder:
+    """Orders a library call on the solver's stream against torch's current stream of
+    the device: the solver's stream first waits for the work already enqueued on the
+    current stream (so the inputs the caller just produced are complete), and the
+    current stream then waits for the call's work (so outputs are complete, and
+    inputs and scratch freed afterwards through the caching allocator are not reused
+    while the call still reads them). Nothing is done when the two are the same stream."""
+
+    def __init__(self, owner):
+        self.owner = owner
+
+    def __enter__(self):
+        t = self.owner.torch
+        self.cur = t.cuda.current_stream(self.owner.device)
+        self.same = self.cur == self.owner.stream
+        if not self.same:
+            self.owner.stream.wait_stream(self.cur)
+        return self
+
+    def __exit__(self, *exc):
+        if not self.same:
+            self.cur.wait_stream(self.owner.stream)
+        return False
+
+
 class VLBM:
     """One 2D grid advanced by the blended D2Q5 vectorial LBM on a CUDA device.
 
@@ -379,6 +420,7 @@ class VLBM:
             raise VLBMError(E_INVAL, "invalid grid")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace.record_stream(self.stream)
         rc, self._s = vlbm_init(self.grid, gamma, lam, limiter, precision, self.opts,
                                 self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
         _check(rc)
@@ -392,13 +434,16 @@ class VLBM:
 
     def set_conserved(self, rho, mom, E):
         """rho, E: (ny, nx); mom: (2, ny, nx) -- device tensors in the solver's dtype."""
-        _check(vlbm_set_conserved(self._s, self._ptr(rho), self._ptr(mom), self._ptr(E)), self._s)
+        with _StreamOrder(self):
+            _check(vlbm_set_conserved(self._s, self._ptr(rho), self._ptr(mom), self._ptr(E)), self._s)
 
     def step(self, nsteps: int = 1):
-        _check(vlbm_step(self._s, int(nsteps)), self._s)
+        with _StreamOrder(self):
+            _check(vlbm_step(self._s, int(nsteps)), self._s)
 
     def step_to(self, t_end: float, max_steps: int = 10 ** 9) -> int:
-        rc = vlbm_step_to(self._s, float(t_end), int(max_steps))
+        with _StreamOrder(self):
+            rc = vlbm_step_to(self._s, float(t_end), int(max_steps))
         return _check(rc, self._s)
 
     def moments(self):
@@ -406,7 +451,8 @@ class VLBM:
         rho = t.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)
         mom = t.empty((2, self.ny, self.nx), dtype=self.dtype, device=self.device)
         E = t.empty((self.ny, self.nx), dtype=self.dtype, device=self.device)
-        _check(vlbm_moments(self._s, rho.data_ptr(), mom.data_ptr(), E.data_ptr()), self._s)
+        with _StreamOrder(self):
+            _check(vlbm_moments(self._s, rho.data_ptr(), mom.data_ptr(), E.data_ptr()), self._s)
         return rho, mom, E
 
     @staticmethod
@@ -431,7 +477,8 @@ class VLBM:
         """Enqueue on the solver's stream a copy of the monitors, as the work enqueued so far
         leaves them, into the pinned buffer `buf` (vlbm_monitors_async); read them with
         decode_monitors(buf) once the copy has completed."""
-        _check(vlbm_monitors_async(self._s, buf.data_ptr()), self._s)
+        with _StreamOrder(self):
+            _check(vlbm_monitors_async(self._s, buf.data_ptr()), self._s)
 
     def decode_monitors(self, buf) -> dict:
         rc, m = vlbm_monitors_decode(buf.data_ptr())
@@ -448,11 +495,13 @@ class VLBM:
 
     def save(self):
         buf = self.torch.empty(vlbm_checkpoint_bytes(self._s), dtype=self.torch.uint8, device=self.device)
-        _check(vlbm_save(self._s, buf.data_ptr()), self._s)
+        with _StreamOrder(self):
+            _check(vlbm_save(self._s, buf.data_ptr()), self._s)
         return buf
 
     def load(self, buf):
-        _check(vlbm_load(self._s, buf.data_ptr()), self._s)
+        with _StreamOrder(self):
+            _check(vlbm_load(self._s, buf.data_ptr()), self._s)
 
     def state_planes(self):
         """(20, ny, nx) copy of the current state (u, then u_1..u_4) via a checkpoint."""
@@ -478,8 +527,9 @@ class VLBM:
 
     def rollout(self, nsteps: int, ckpt_every: int, scratch):
         """Advance nsteps from the state set_conserved left, checkpointing into scratch."""
-        _check(vlbm_rollout(self._s, int(nsteps), int(ckpt_every), scratch.data_ptr(), scratch.numel()),
-               self._s)
+        with _StreamOrder(self):
+            _check(vlbm_rollout(self._s, int(nsteps), int(ckpt_every), scratch.data_ptr(), scratch.numel()),
+                   self._s)
 
     def set_adjoint_mode(self, mode: int):
         """ADJOINT_HOLD_A (default) or ADJOINT_DIFF_A: whether the adjoint differentiates
@@ -492,8 +542,9 @@ class VLBM:
         With u0 the call sets the state from it and runs the rollout itself; without
         it, the checkpoints of the preceding rollout (same arguments) are used."""
         g = self.torch.empty((4, self.ny, self.nx), dtype=self.dtype, device=self.device)
-        _check(vlbm_adjoint(self._s, self._ptr(u0), int(nsteps), int(ckpt_every), self._ptr(dLduN),
-                            g.data_ptr(), scratch.data_ptr(), scratch.numel()), self._s)
+        with _StreamOrder(self):
+            _check(vlbm_adjoint(self._s, self._ptr(u0), int(nsteps), int(ckpt_every), self._ptr(dLduN),
+                                g.data_ptr(), scratch.data_ptr(), scratch.numel()), self._s)
         return g
 
     def close(self):
@@ -534,6 +585,7 @@ class VLBMBatch:
             raise VLBMError(E_INVAL, "invalid grids")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.workspace.record_stream(self.stream)
         rc, self._b = vlbm_batch_init(self._grids, gamma, limiter, precision, self.opts,
                                       self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
         if rc != OK:
@@ -547,10 +599,12 @@ class VLBMBatch:
         for t in (rho, mom, E):
             if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
                 raise ValueError("tensor must be contiguous, on the batch's device, in its dtype")
-        self._chk(vlbm_batch_set_conserved(self._b, i, rho.data_ptr(), mom.data_ptr(), E.data_ptr()))
+        with _StreamOrder(self):
+            self._chk(vlbm_batch_set_conserved(self._b, i, rho.data_ptr(), mom.data_ptr(), E.data_ptr()))
 
     def step(self, nsteps: int = 1):
-        self._chk(vlbm_batch_step(self._b, int(nsteps)))
+        with _StreamOrder(self):
+            self._chk(vlbm_batch_step(self._b, int(nsteps)))
 
     def moments(self, i):
         nx, ny = self.shapes[i]
@@ -558,14 +612,16 @@ class VLBMBatch:
         rho = t.empty((ny, nx), dtype=self.dtype, device=self.device)
         mom = t.empty((2, ny, nx), dtype=self.dtype, device=self.device)
         E = t.empty((ny, nx), dtype=self.dtype, device=self.device)
-        self._chk(vlbm_batch_moments(self._b, i, rho.data_ptr(), mom.data_ptr(), E.data_ptr()))
+        with _StreamOrder(self):
+            self._chk(vlbm_batch_moments(self._b, i, rho.data_ptr(), mom.data_ptr(), E.data_ptr()))
         return rho, mom, E
 
     def state_planes(self, i):
         nx, ny = self.shapes[i]
         el = 8 if self.precision == FP64 else 4
         buf = self.torch.empty(64 + 20 * nx * ny * el, dtype=self.torch.uint8, device=self.device)
-        self._chk(vlbm_batch_save(self._b, i, buf.data_ptr()))
+        with _StreamOrder(self):
+            self._chk(vlbm_batch_save(self._b, i, buf.data_ptr()))
         return buf[64:].view(self.dtype).view(20, ny, nx)
 
     def monitors(self, i) -> dict:
@@ -586,7 +642,8 @@ class VLBMBatch:
         self._chk(vlbm_batch_set_tuning(self._b, vlbm_batch_tuning(chunk, ctas_per_sm, order, 0, 0)))
 
     def autotune(self, trial_steps: int = 3):
-        rc, t, ms = vlbm_batch_autotune(self._b, int(trial_steps))
+        with _StreamOrder(self):
+            rc, t, ms = vlbm_batch_autotune(self._b, int(trial_steps))
         self._chk(rc)
         return {"chunk": t.chunk, "ctas_per_sm": t.ctas_per_sm, "order": t.order, "items": t.items,
                 "ctas": t.ctas, "ms_per_step": ms}
@@ -612,14 +669,21 @@ def _rollout_function():
         forward(rho, mom, E, solver, nsteps, ckpt_every) -> (rho^N, mom^N, E^N); the
         backward pass is the library's adjoint (vlbm_adjoint) over the checkpoints
         the forward pass stored; a dynamic a^n is held or differentiated as the
-        solver's set_adjoint_mode says."""
+        solver's set_adjoint_mode says. One solver may serve several forwards before
+        their backwards: a backward whose forward is no longer the solver's latest
+        rollout passes u_0 to vlbm_adjoint, which then runs that rollout again."""
 
         @staticmethod
         def forward(ctx, rho, mom, E, solver, nsteps, ckpt_every):
             scratch = solver.adjoint_scratch(nsteps, ckpt_every)
             solver.set_conserved(rho.contiguous(), mom.contiguous(), E.contiguous())
             solver.rollout(nsteps, ckpt_every, scratch)
-            ctx.solver, ctx.nsteps, ctx.every, ctx.scratch = solver, nsteps, ckpt_every, scratch
+            token = object()
+            solver._rollout_token = token
+            ctx.solver, ctx.nsteps, ctx.every, ctx.scratch, ctx.token = solver, nsteps, ckpt_every, scratch, token
+            ctx.u0 = torch.cat([rho.detach().reshape(1, solver.ny, solver.nx),
+                                mom.detach().reshape(2, solver.ny, solver.nx),
+                                E.detach().reshape(1, solver.ny, solver.nx)]).to(solver.dtype).contiguous()
             return solver.moments()
 
         @staticmethod
@@ -630,8 +694,10 @@ def _rollout_function():
             dLduN = t.cat([z(g_rho, (s.ny, s.nx)).reshape(1, s.ny, s.nx),
                            z(g_mom, (2, s.ny, s.nx)).reshape(2, s.ny, s.nx),
                            z(g_E, (s.ny, s.nx)).reshape(1, s.ny, s.nx)]).to(s.dtype).contiguous()
-            g = s.adjoint(dLduN, ctx.nsteps, ctx.every, ctx.scratch)
-            ctx.scratch = None
+            latest = getattr(s, "_rollout_token", None) is ctx.token
+            g = s.adjoint(dLduN, ctx.nsteps, ctx.every, ctx.scratch, u0=None if latest else ctx.u0)
+            s._rollout_token = ctx.token          # the checkpoints now hold this rollout
+            ctx.scratch = ctx.u0 = None
             return g[0], g[1:3], g[3], None, None, None
 
     return VLBMRollout

@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "vlbm.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     return sorted(set(re.findall(r"VLBM_API[^;(]*?\b(vlbm_\w+)\s*\(", src)))
 
 
@@ -27,8 +28,18 @@ def V():
 def test_header_declares_the_api():
     names = _declared()
     for n in ("vlbm_init", "vlbm_step", "vlbm_moments", "vlbm_set_conserved", "vlbm_step_to",
-              "vlbm_monitors", "vlbm_save", "vlbm_load", "vlbm_destroy", "vlbm_strerror"):
+              "vlbm_monitors", "vlbm_save", "vlbm_load", "vlbm_destroy", "vlbm_strerror",
+              "vlbm_test_theta_faces", "vlbm_test_wait_probe"):
         assert n in names
+
+
+def test_test_hooks_reject_bad_arguments(V):
+    assert V.vlbm_test_theta_faces(-1, 1.0, 0.5, 0.0, None, None, None, None) == V.E_INVAL
+    assert V.vlbm_test_theta_faces(0, 1.0, 0.5, 0.0, None, None, None, None) == V.OK
+    assert V.vlbm_test_theta_faces(4, 1.0, 0.5, 0.0, None, None, None, None) == V.E_INVAL
+    assert V.vlbm_test_theta_faces(4, 0.0, 0.5, 0.0, 8, 8, 8, None) == V.E_INVAL
+    assert V.vlbm_test_theta_faces(4, 1.0, 0.4, 0.0, 8, 8, 8, None) == V.E_INVAL
+    assert V.vlbm_test_wait_probe(None, 1000) == V.E_INVAL
 
 
 def test_exports_every_declared_symbol(V):
