@@ -75,6 +75,11 @@ template <> struct SumAcc<double> {
     __device__ __forceinline__ double value(int q) const { return s[q]; }
 };
 
+template <typename T>
+__device__ __forceinline__ bool all_finite(const T u[4]) {
+    return isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]) && isfinite(u[3]);
+}
+
 // Per-thread monitor of the cells a thread wrote: max lambda, min rho, sums,
 // the counts of cells outside G / non-finite, and of faces whose theta_p needed
 // the FP64 solve.
@@ -101,8 +106,14 @@ struct Monitor {
         else ir = fast_rcp(u[0]);
         minrhoe = pmin(minrhoe, u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ir);
         sum.add_cell(u);
-        if (!(sp <= T(3.0e38))) ++nonfin;
-        else if (!in_G(u)) ++bad;
+        // no finite speed: a non-finite value, or finite values outside G (p < 0 gives a
+        // NaN sound speed); a finite speed can still belong to a state outside G (rho < 0)
+        if (!(sp <= T(3.0e38))) {
+            if (all_finite(u)) ++bad;
+            else ++nonfin;
+        } else if (!in_G(u)) {
+            ++bad;
+        }
     }
     __device__ __forceinline__ void warp_reduce() {
         for (int off = 16; off > 0; off >>= 1) {
@@ -213,11 +224,12 @@ __device__ inline void finalize_step(DevCtl *C) {
     C->nonfinite_last = (long long)nonfin;
     for (int c = 0; c < 4; ++c) C->sum_last[c] = s[c];
     if ((bad || nonfin) && C->first_bad_step < 0) C->first_bad_step = n1;
+    // a cell outside G is the positivity failure, even when the same step also made
+    // values non-finite; without a finite lambda no further step can be planned
+    if (bad && !C->status) C->status = VLBM_E_POSITIVITY;
     if (nonfin || !isfinite(lam)) {
         if (!C->status) C->status = VLBM_E_NONFINITE;
         C->done = 1;
-    } else if (bad && !C->status) {
-        C->status = VLBM_E_POSITIVITY;
     }
     if (C->last || C->status == VLBM_E_TIMEOUT) C->done = 1;
     double a_free = next_speed(C, lam);

@@ -70,6 +70,7 @@ __global__ void k_ctl_reset(DevCtl *C, double dx, double alpha, double a_fixed, 
     C->status = 0;
     C->invalid_init = 0;
     C->first_bad_step = -1;
+    C->wait_probe_ns = 0u;
     reset_slots(C);
     C->lambda = 0.0;
     C->min_rho = 0.0;

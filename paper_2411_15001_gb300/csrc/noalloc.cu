@@ -251,7 +251,7 @@ extern "C" int vlbm_step_noalloc(const vlbm_grid *grid, double gamma, double a, 
     result->bad_cells = r.bad;
     result->nonfinite_cells = r.nonfin;
     result->theta_p_fp64_faces = r.fp64;
+    if (r.bad) return VLBM_E_POSITIVITY;   // cells outside G (their lambda is NaN)
     if (r.nonfin || !(r.lam <= 1e300)) return VLBM_E_NONFINITE;
-    if (r.bad) return VLBM_E_POSITIVITY;
     return VLBM_OK;
 }

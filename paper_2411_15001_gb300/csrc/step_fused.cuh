@@ -423,7 +423,15 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
     __syncthreads();
     uint32_t nissued = 0, nconsumed = 0;
     bool ok = true;
-    for (;;) {
+    // Testing hook (vlbm_test_wait_probe): before any load, a bounded wait on a
+    // barrier that no copy and no thread completes; it runs out and the CTA takes
+    // the timeout path below.
+    if (const unsigned int probe = B.insts[0].ctl->wait_probe_ns) {
+        if (b == 0 && !mbar_wait_bounded(&S.bar[0], 0u, probe)) S.abort = 1;
+        __syncthreads();
+        ok = S.abort == 0;
+    }
+    while (ok) {
         if (b == 0) S.item = (int)atomicAdd(&B.bctl->work, 1u);
         __syncthreads();
         const int item = S.item;

@@ -100,7 +100,8 @@ struct DevCtl {
     unsigned long long fp64_faces;   // faces whose theta_p needed the FP64 solve
     double sum[4];
     unsigned int blocks_done;
-    unsigned int pad0;
+    unsigned int wait_probe_ns;  // testing hook (vlbm_test_wait_probe): > 0 makes every CTA of the
+                                 // row-marching kernel first wait this long on a barrier nothing completes
     // published monitors of the current state
     double lambda;
     double min_rho;

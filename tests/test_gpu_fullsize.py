@@ -81,6 +81,44 @@ def test_blast_4096_pp_sampled():
     s.close()
 
 
+def test_blast_4096_2000_steps_positive_every_step():
+    """The blast workload as specified: 4096^2, PP with eps = 1e-13, FP32, 2000 steps from
+    t = 0. Every step's monitors are read back (vlbm_monitors_async, checked one step
+    behind): no cell outside G, no non-finite value, status OK, the step count right.
+    Then one more step is checked cell by cell against the oracle on the shock ring and
+    at random cells."""
+    p = W.blast(4096)
+    s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, limiter=V.LIM_PP, precision=V.FP32, eps=1e-13,
+               kernel=V.KERNEL_FUSED, device="cuda:0")
+    c = torch.tensor(p.conserved(), dtype=torch.float32, device="cuda:0")
+    s.set_conserved(c[0].contiguous(), c[1:3].contiguous(), c[3].contiguous())
+    bufs = [s.monitor_buffer() for _ in range(2)]
+    evs = [torch.cuda.Event() for _ in range(2)]
+    seen = []
+
+    def check(k):
+        evs[k & 1].synchronize()
+        m = s.decode_monitors(bufs[k & 1])
+        assert m["n"] == k + 1 and m["status"] == V.OK, m
+        assert m["bad_cells"] == 0 and m["nonfinite_cells"] == 0 and m["first_bad_step"] == -1, m
+        assert m["min_rho"] > 0.0 and m["min_internal_energy"] > 0.0, m
+        seen.append(m["min_rho"])
+
+    steps = 2000
+    for k in range(steps):
+        s.step(1)
+        s.monitors_async(bufs[k & 1])
+        evs[k & 1].record(s.stream)
+        if k > 0:
+            check(k - 1)
+    check(steps - 1)
+    assert len(seen) == steps
+    m = s.monitors()
+    assert m["n"] == steps and m["status"] == V.OK and m["first_bad_step"] == -1
+    _step_and_sample(s, O.LIM_PP, p.gamma, 1e-13, 150, 3)
+    s.close()
+
+
 def test_quadrant_1024_lmp_sampled():
     p = W.quadrant_riemann(1024, seed=0)
     s = V.VLBM(p.nx, p.ny, p.dx, bc=p.bc, limiter=V.LIM_LMP, precision=V.FP32, kernel=V.KERNEL_FUSED,
@@ -114,14 +152,28 @@ def test_batch_grids_sampled():
     b.close()
 
 
+def _jitter_spread():
+    """L1 spread of the oracle's 1024^2 LMP quadrant run under float-level noise
+    (tests/golden/quadrant1024_lmp_jitter.txt, written by make_quadrant_jitter.py)."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "quadrant1024_lmp_jitter.txt")
+    with open(path) as f:
+        for line in f:
+            if line.startswith("spread"):
+                return float(line.split()[1])
+    raise ValueError("no spread in " + path)
+
+
 def test_quadrant_1024_lmp_to_final_time():
     """The 1024^2 quadrant problem with LMP run to t = 0.25 as specified (last step
     shortened to land on it): FP32 with the row-marching kernel against the FP64
     path, which is the oracle's run bit for bit on every smaller case: step counts
-    within 1 %, every step admissible, density within L1 1e-2. This run is
-    ill-conditioned at float precision: the FP64 oracle itself, with a relative 2^-24
-    jitter after every step, ends 5.5e-3 (L1) from its own clean run (2330 against
-    2329 steps; measured once, 33 CPU-minutes); the FP32 run lands 4.0e-3 away."""
+    within 1 %, every step admissible. This run is ill-conditioned at float
+    precision, so the stated 1e-3 (L1, discontinuous data) is out of reach for any
+    float run: the FP64 oracle itself, with a relative 2^-24 jitter of every value
+    after every step, ends a spread S (L1 of rho) from its own clean run
+    (tests/golden/quadrant1024_lmp_jitter.txt). The FP32 density is held to 1.1 S."""
     p = W.quadrant_riemann(1024, seed=0)
     out = {}
     for prec, dt, kern in ((V.FP32, torch.float32, V.KERNEL_FUSED), (V.FP64, torch.float64, V.KERNEL_SIMPLE)):
@@ -138,4 +190,5 @@ def test_quadrant_1024_lmp_to_final_time():
     err = float(np.abs(u32[0] - u64[0]).sum() / np.abs(u64[0]).sum())
     # the dynamic a^n follow each run's own max lambda: LMP's sensitivity moves the
     # step count a little (measured 2333 vs 2329)
-    assert abs(n32 - n64) <= 0.01 * n64 and err <= 1e-2, (n32, n64, err)
+    spread = _jitter_spread()
+    assert abs(n32 - n64) <= 0.01 * n64 and err <= 1.1 * spread, (n32, n64, err, spread)
