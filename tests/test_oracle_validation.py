@@ -12,6 +12,7 @@ import pytest
 from oracle import oracle as O
 from paper_2411_15001_gb300 import workloads as W
 from tests import exact_riemann as ER
+from tests.exact_wave import near_vacuum_wave_exact
 
 
 def _run_checked(cfg, p, t_end):
@@ -29,7 +30,7 @@ def _l1(a, b):
 
 def test_near_vacuum_exact_solution_is_the_initial_state_at_t0():
     x = np.linspace(-1, 1, 17)
-    assert np.allclose(W.near_vacuum_wave_exact(x, 0.0), 1.0 + 0.9999995 * np.sin(np.pi * x), atol=1e-14)
+    assert np.allclose(near_vacuum_wave_exact(x, 0.0), 1.0 + 0.9999995 * np.sin(np.pi * x), atol=1e-14)
 
 
 def test_near_vacuum_wave():
@@ -37,7 +38,7 @@ def test_near_vacuum_wave():
     for N in (50, 100, 200):
         p = W.near_vacuum_wave(N)
         x = -1.0 + (np.arange(N) + 0.5) * p.dx
-        ex = W.near_vacuum_wave_exact(x, 0.1)
+        ex = near_vacuum_wave_exact(x, 0.1)
         for lim in (O.LIM_FIRST, O.LIM_PP, O.LIM_RLMP):
             cfg = O.Config(N, 4, p.bc, lim, 3.0, 0.5, 1e-16)
             r = _run_checked(cfg, p, 0.1)
