@@ -35,12 +35,14 @@ extern "C" {
 VLBM_API int vlbm_test_theta_faces(int64_t n, double a, double alpha, double eps, const void *d_faces,
                                    void *d_theta, void *d_stage, void *stream);
 
-/* Arm the wait probe of the row-marching kernel for the state's next steps: every
- * CTA of each following launch first waits, bounded by limit_ns nanoseconds, on an
- * mbarrier that no copy and no thread completes. The wait runs out, and the CTA
- * takes the kernel's timeout path: it has issued no load, processes no work item,
- * records VLBM_E_TIMEOUT (reported by the next synchronising call) and leaves the
- * work counter reset for the next launch; the state does not advance. limit_ns = 0
+/* Arm the wait probe of the row-marching kernel for the state's next steps: while it
+ * is armed, vlbm_step and vlbm_step_to launch the kernel's probe instantiation (the
+ * same source with one addition, and one launch per step, no graph replay), in
+ * which every CTA first waits, bounded by limit_ns nanoseconds, on an mbarrier that
+ * no copy and no thread completes. The wait runs out, and the CTA takes the kernel's
+ * timeout path: it has issued no load, processes no work item, records
+ * VLBM_E_TIMEOUT (reported by the next synchronising call) and leaves the work
+ * counter reset for the next launch; the state does not advance. limit_ns = 0
  * disarms the probe, as do vlbm_set_conserved and vlbm_load. Only the row-marching
  * kernel (VLBM_KERNEL_FUSED) waits on barriers. Asynchronous on the state's stream.
  * Errors: VLBM_E_INVAL (s NULL or nothing loaded), VLBM_E_CUDA. */

@@ -69,6 +69,11 @@ static int elem_of(int32_t precision) {
 
 
 static cudaError_t step_kernel_only(vlbm_state *s) {
+    if (use_fused(s) && s->probe_armed) {
+        if (s->precision == VLBM_FP64)
+            return launch_step_fused_probe<double>(batch_args_of<double>(s), s->limiter, s->fused_grid, s->stream);
+        return launch_step_fused_probe<float>(batch_args_of<float>(s), s->limiter, s->fused_grid, s->stream);
+    }
     if (use_fused(s)) {
         if (s->precision == VLBM_FP64)
             return launch_step_fused<double>(batch_args_of<double>(s), s->limiter, s->fused_grid, s->stream);
@@ -249,7 +254,7 @@ static cudaError_t build_graph(vlbm_state *s) {
 // n steps: whole groups of kGraphSteps replayed from the graph (not while the
 // per-launch kernel timing is on), the rest as single launches.
 cudaError_t vlbm::api::step_many(vlbm_state *s, int64_t n) {
-    if (!s->profiling && n >= kGraphSteps) {
+    if (!s->profiling && !s->probe_armed && n >= kGraphSteps) {
         cudaError_t e = cudaSuccess;
         if (!s->gexec)
             e = s->precision == VLBM_FP64 ? build_graph<double>(s) : build_graph<float>(s);
@@ -397,6 +402,7 @@ int vlbm::api::set_conserved(vlbm_state *s, const void *d_rho, const void *d_mom
     s->loaded = true;
     s->tend_active = false;
     s->at_init = true;
+    s->probe_armed = false;
     if (h.invalid_init)
         return fail(s, VLBM_E_INVAL, "initial state has cells outside G or not finite");
     return VLBM_OK;
@@ -557,6 +563,7 @@ int vlbm_load(vlbm_state *s, const void *d_src) {
                                       : launch_load<float>(args_of<float>(s), d_src, s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "load launch");
     s->loaded = true;
+    s->probe_armed = false;
     s->tend_active = true;  // the restored header may carry a final time
     s->at_init = false;
     s->roll_scratch = nullptr;

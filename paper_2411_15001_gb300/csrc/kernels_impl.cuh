@@ -75,19 +75,19 @@ const void *ghosts_kernel_fn<VLBM_T>() {
 }
 
 namespace {
-template <int LIM>
+template <int LIM, bool PROBE = false>
 cudaError_t fused_one(const FusedBatchArgs<VLBM_T> &B, int grid, cudaStream_t s) {
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     const size_t smem = sizeof(FusedSmem<VLBM_T>);
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(k_step_fused<VLBM_T, LIM>,
+        cudaError_t e = cudaFuncSetAttribute(k_step_fused<VLBM_T, LIM, PROBE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    k_step_fused<VLBM_T, LIM><<<grid, kFB, smem, s>>>(B);
+    k_step_fused<VLBM_T, LIM, PROBE><<<grid, kFB, smem, s>>>(B);
     return cudaGetLastError();
 }
 
@@ -123,6 +123,19 @@ const void *fused_kernel_fn<VLBM_T>(int limiter, size_t *smem) {
         case VLBM_LIM_PP: return (const void *)k_step_fused<VLBM_T, VLBM_LIM_PP>;
         case VLBM_LIM_LMP: fused_blocks_per_sm<VLBM_LIM_LMP>(); return (const void *)k_step_fused<VLBM_T, VLBM_LIM_LMP>;
         default: fused_blocks_per_sm<VLBM_LIM_RLMP>(); return (const void *)k_step_fused<VLBM_T, VLBM_LIM_RLMP>;
+    }
+}
+
+template <>
+cudaError_t launch_step_fused_probe<VLBM_T>(const FusedBatchArgs<VLBM_T> &B, int limiter, int grid,
+                                            cudaStream_t s) {
+    switch (limiter) {
+        case VLBM_LIM_FIRST_ORDER: return fused_one<VLBM_LIM_FIRST_ORDER, true>(B, grid, s);
+        case VLBM_LIM_NONE: return fused_one<VLBM_LIM_NONE, true>(B, grid, s);
+        case VLBM_LIM_PP: return fused_one<VLBM_LIM_PP, true>(B, grid, s);
+        case VLBM_LIM_LMP: return fused_one<VLBM_LIM_LMP, true>(B, grid, s);
+        case VLBM_LIM_RLMP: return fused_one<VLBM_LIM_RLMP, true>(B, grid, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -26,6 +26,7 @@ struct vlbm_state {
     std::vector<unsigned char> desc_host;   // InstDesc<T> of this grid
     std::vector<vlbm::WorkItem> items_host;  // work items in launch order (guided bands)
     bool profiling;
+    bool probe_armed;   // vlbm_test_wait_probe: launch the probe instantiation, no graphs
     std::vector<cudaEvent_t> ev;   // event pairs of timed launches
     size_t ev_used;
     bool loaded;        // set_conserved or load has run

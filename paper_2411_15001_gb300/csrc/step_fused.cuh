@@ -403,7 +403,10 @@ __device__ void drain_loads(FusedSmem<T> &S, uint32_t nissued, uint32_t nconsume
     }
 }
 
-template <typename T, int LIM>
+// PROBE: the instantiation that vlbm_test_wait_probe selects (the others carry no
+// probe code): before any load, every CTA makes a bounded wait on a barrier that no
+// copy and no thread completes; it runs out and the CTA takes the timeout path below.
+template <typename T, int LIM, bool PROBE = false>
 __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
     k_step_fused(FusedBatchArgs<T> B) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -423,15 +426,13 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
     __syncthreads();
     uint32_t nissued = 0, nconsumed = 0;
     bool ok = true;
-    // Testing hook (vlbm_test_wait_probe): before any load, a bounded wait on a
-    // barrier that no copy and no thread completes; it runs out and the CTA takes
-    // the timeout path below.
-    if (const unsigned int probe = B.insts[0].ctl->wait_probe_ns) {
-        if (b == 0 && !mbar_wait_bounded(&S.bar[0], 0u, probe)) S.abort = 1;
+    if constexpr (PROBE) {
+        const unsigned int probe = B.insts[0].ctl->wait_probe_ns;
+        if (b == 0 && !mbar_wait_bounded(&S.bar[0], 0u, probe > 0u ? probe : 1u)) S.abort = 1;
         __syncthreads();
         ok = S.abort == 0;
     }
-    while (ok) {
+    if (ok) for (;;) {
         if (b == 0) S.item = (int)atomicAdd(&B.bctl->work, 1u);
         __syncthreads();
         const int item = S.item;

@@ -59,6 +59,7 @@ int vlbm_test_wait_probe(vlbm_state *s, uint32_t limit_ns) {
     k_set_wait_probe<<<1, 1, 0, s->stream>>>(s->ctl, limit_ns);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(s, e, "wait probe launch");
+    s->probe_armed = limit_ns > 0;
     return VLBM_OK;
 }
 

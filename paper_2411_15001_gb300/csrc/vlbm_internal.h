@@ -100,8 +100,8 @@ struct DevCtl {
     unsigned long long fp64_faces;   // faces whose theta_p needed the FP64 solve
     double sum[4];
     unsigned int blocks_done;
-    unsigned int wait_probe_ns;  // testing hook (vlbm_test_wait_probe): > 0 makes every CTA of the
-                                 // row-marching kernel first wait this long on a barrier nothing completes
+    unsigned int wait_probe_ns;  // testing hook (vlbm_test_wait_probe): how long every CTA of the probe
+                                 // instantiation of the row-marching kernel waits on a barrier nothing completes
     // published monitors of the current state
     double lambda;
     double min_rho;
@@ -237,6 +237,9 @@ template <typename T> cudaError_t launch_step_simple(const StepArgs<T> &a, cudaS
 // Row-marching kernel over the work items of one or more grids, `grid` persistent CTAs.
 template <typename T> cudaError_t launch_step_fused(const FusedBatchArgs<T> &a, int limiter, int grid,
                                                    cudaStream_t s);
+// The instantiation with the wait probe of vlbm_test_wait_probe (same launch shape).
+template <typename T> cudaError_t launch_step_fused_probe(const FusedBatchArgs<T> &a, int limiter, int grid,
+                                                         cudaStream_t s);
 template <typename T> int fused_occupancy(int limiter);   // CTAs per SM of the fused kernel
 // Kernel function and dynamic shared memory of the fused kernel, for graph nodes.
 template <typename T> const void *fused_kernel_fn(int limiter, size_t *smem);

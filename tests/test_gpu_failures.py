@@ -40,10 +40,12 @@ def _solver(p, limiter, precision, kernel=V.KERNEL_AUTO, **kw):
     return s
 
 
-@pytest.mark.parametrize("prec, rel", [(V.FP64, 1e-14), (V.FP32, 2e-6)])
+@pytest.mark.parametrize("prec, rel", [(V.FP64, 1e-14), (V.FP32, 5e-6)])
 def test_speed_monitor_is_euclidean(prec, rel):
     # (rho, v1, v2, p) = (1, 3, 4, 1), gamma = 1.4: lambda = |v| + c = 5 + sqrt(1.4); the
-    # max-norm speed of Prop. convex_preservation_O1 would give 4 + sqrt(1.4)
+    # max-norm speed of Prop. convex_preservation_O1 would give 4 + sqrt(1.4). In FP32
+    # the monitor is an upper bound of the exact speed of the float state (with the
+    # float gamma and gamma - 1 the kernels use), at most a few 1e-6 above it.
     nx = ny = 16
     dt = torch.float64 if prec == V.FP64 else torch.float32
     rho = torch.ones((ny, nx), dtype=dt, device=DEV)
@@ -55,11 +57,17 @@ def test_speed_monitor_is_euclidean(prec, rel):
                    device=DEV)
         s.set_conserved(rho, mom, E)
         lam = 5.0 + math.sqrt(1.4)
+        if prec == V.FP32:   # p = (gamma - 1)(E - |m|^2 / 2 rho) = 2.5 (gamma - 1), float constants
+            lam = 5.0 + math.sqrt(float(np.float32(1.4)) * float(np.float32(1.4 - 1.0)) * 2.5)
         m = s.monitors()
         assert m["lambda"] == pytest.approx(lam, rel=rel) and m["a"] == pytest.approx(4 * lam, rel=rel)
+        if prec == V.FP32:
+            assert m["lambda"] >= lam, (m["lambda"], lam)
         s.step(3)                                          # a uniform flow stays uniform
         m = s.monitors()
         assert m["status"] == V.OK and m["lambda"] == pytest.approx(lam, rel=rel), m
+        if prec == V.FP32:
+            assert m["lambda"] >= lam, (m["lambda"], lam)
         s.close()
 
 
@@ -142,7 +150,7 @@ def test_bounded_wait_runs_out_and_is_reported(prec):
     assert V.vlbm_sync(s._s) == V.E_TIMEOUT
     m = s.monitors()
     assert m["status"] == V.E_TIMEOUT and m["n"] == 2, m          # no step completed
-    s.step(64)                                                    # graph replays time out too
+    s.step(64)                                                    # (single launches while armed)
     m = s.monitors()
     assert m["status"] == V.E_TIMEOUT and m["n"] == 2, m
     # the context is intact: a new initial state disarms the probe, and the run that

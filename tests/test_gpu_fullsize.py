@@ -5,7 +5,9 @@ cell (the update of a cell reads only cells within distance 2, so the patch edge
 never reaches the centre), at the kinetic speed the GPU used.
 
 The GPU arithmetic is FP32 and the oracle's FP64 on the same (FP32) inputs; the
-tolerance, 1e-4 of the largest magnitude of that plane in the patch, covers FP32
+tolerance, 1e-4 of the largest magnitude of that component in the patch -- over the
+conserved plane and its four populations, which the update sums (a momentum at
+rest is rounding noise of the populations' size) -- covers FP32
 rounding (~1e-6 of that scale, more where terms cancel) and the FP32 theta_p,
 which may sit up to 6.1e-5 below the exact value where the limiter acts (a
 certified lower bound, tight to 2^-14). Workloads:
@@ -39,7 +41,8 @@ def _check_samples(before, after, cells, a, limiter, gamma, eps, tol=1e-4):
         patch = np.ascontiguousarray(before[:, j - R:j + R + 1, i - R:i + R + 1], dtype=np.float64)
         ref = O.step(cfg, patch, a)[:, R, R]
         got = after[:, j, i].astype(np.float64)
-        scale = np.abs(patch).reshape(20, -1).max(axis=1)
+        comp = np.abs(patch).reshape(5, 4, -1).max(axis=(0, 2))     # per component c: planes c, 4+c, ..
+        scale = np.tile(comp, 5)
         err = float((np.abs(got - ref) / np.maximum(scale, 1e-300)).max())
         worst = max(worst, err)
         assert err <= tol, (j, i, err, got, ref)

@@ -23,7 +23,10 @@ pytestmark = pytest.mark.gpu
 
 # how far below theta_p each stage may sit (relative): the screen returns min(1,
 # theta_rho) itself; the float interval is tight to 2^-14 (+ 16 u for the
-# reciprocals); the double-precision stage loses a few float roundings
+# reciprocals); the double-precision stage is held to the bound it documents
+# (tests/theta_faces.py: fp64_stage_model -- tight to a few float roundings unless
+# gamma_0, gamma_1 or c cancel, where its error bound grows with the cancellation)
+# within the float roundings of its last steps
 TOL = {0: 0.0, 1: 0.0, 2: 6.5e-5, 3: 4e-6}
 
 
@@ -65,12 +68,19 @@ def blast_faces(n=256, steps=240, eps=1e-13):
 def _check(F, a, eps, label):
     kappa = a / 4.0
     th, st = gpu_theta(F, a, eps)
-    res = TF.check_certificate(F, th, st, kappa, eps, TOL)
+    res = TF.check_certificate(F, th, st, kappa, eps, TOL, model=TF.fp64_stage_model(F, kappa, eps))
     hist = {k: int((st == k).sum()) for k in range(4)}
     print(f"{label}: {len(F)} faces, stages none/screen/interval/fp64 = "
           f"{hist[0]}/{hist[1]}/{hist[2]}/{hist[3]}, min theta {th.min():.3g}")
     for what, idx in res.items():
         assert idx.size == 0, (label, what, idx.size, F[idx[:3]], th[idx[:3]], st[idx[:3]])
+    s3 = np.nonzero((st == 3) & (th < np.minimum(1.0, F[:, 8])))[0]
+    if s3.size:   # how far below theta_p the double-precision stage sat (for the record)
+        tp = np.array([O.theta_p(kappa, eps, F[i, :4].astype(np.float64), F[i, 4:8].astype(np.float64))
+                       for i in s3[:2000]])
+        ok = tp > 1e-6
+        gap = (1.0 - th[s3[:2000]][ok] / tp[ok]) if ok.any() else np.zeros(1)
+        print(f"   stage 3 below theta_p (oracle, first 2000): median {np.median(gap):.2e}, max {gap.max():.2e}")
     # the oracle's theta_p where its plain double evaluation is accurate
     good = np.nonzero(TF.gamma0_ratio(F[:, :4]) > 1e-7)[0]
     f = F[good].astype(np.float64)
@@ -78,8 +88,9 @@ def _check(F, a, eps, label):
     ref = np.maximum(np.minimum(np.minimum(1.0, f[:, 8]), tp), 0.0)
     g = th[good].astype(np.float64)
     tol = np.array([TOL[int(k)] for k in st[good]])
+    low = np.where(st[good] == 3, np.minimum(ref, TF.fp64_stage_model(F[good], kappa, eps)), ref)
     over = np.nonzero(g > ref * (1.0 + 1e-9))[0]
-    under = np.nonzero(g < ref * (1.0 - tol) - 3.0 * eps)[0]
+    under = np.nonzero(g < low * (1.0 - tol) - 3.0 * eps)[0]
     assert over.size == 0, (label, "above the oracle", F[good][over[:3]], g[over[:3]], ref[over[:3]])
     assert under.size == 0, (label, "below the oracle", F[good][under[:3]], g[under[:3]], ref[under[:3]])
     return hist

@@ -152,3 +152,28 @@ def test_float_screen_passes_only_proved_faces(kind):
         f = F[failed].astype(np.float64)
         tp = np.array([O.theta_p(kappa, eps, f[i, :4], f[i, 4:8]) for i in range(len(f))])
         assert (tp < th[failed]).mean() > 0.5
+
+
+@pytest.mark.parametrize("kind", ["random", "near_vacuum", "cancelling", "large_jump", "boundary"])
+def test_double_stage_bound_is_sound_and_tight_where_conditioned(kind):
+    """The bound the double-precision stage documents (theta_faces.fp64_stage_model) never
+    exceeds theta_p (exact endpoint check), and on faces where gamma_0 cancels by at most
+    1e-7 of its terms it is within the documented error, 2^-52 over that ratio (a few
+    1e-9), of the oracle's theta_p."""
+    rng = np.random.default_rng(31)
+    kappa, eps = 2.0, 1e-13
+    F = _faces(kind, rng, 3000, kappa)
+    model = TF.fp64_stage_model(F, kappa, eps)
+    t = np.minimum(1.0, F[:, 8].astype(np.float64))
+    th = np.maximum(np.minimum(model, t), 0.0)
+    pos = np.nonzero(th > 0)[0]
+    ok = TF.endpoints_in_closed_G(F[pos, :4].astype(np.float64), F[pos, 4:8].astype(np.float64),
+                                  TF.half_length(th[pos] * (1 - 1e-12), eps, kappa))
+    assert ok.all(), pos[~ok][:5]
+    ratio = TF.gamma0_ratio(F[:, :4])
+    good = np.nonzero(ratio > 1e-7)[0]
+    f = F[good].astype(np.float64)
+    tp = np.array([O.theta_p(kappa, eps, f[i, :4], f[i, 4:8]) for i in range(len(f))])
+    ref = np.maximum(np.minimum(t[good], tp), 0.0)
+    rel = 1e-12 + 8 * 2.0 ** -52 / ratio[good]
+    assert np.all(th[good] >= ref * (1 - rel) - 2 * eps), np.max((ref - th[good]) / np.maximum(ref, 1e-300))

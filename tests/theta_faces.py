@@ -72,12 +72,13 @@ def half_length(theta, eps, kappa, up=True):
     return s * (1.0 + 4 * U64) if up else s * (1.0 - 4 * U64)
 
 
-def check_certificate(faces, theta, stage, kappa, eps, tol):
+def check_certificate(faces, theta, stage, kappa, eps, tol, model=None):
     """Per-face checks of a theta computed for float32 `faces` (n, 9):
     - 0 <= theta <= min(1, theta_rho) (theta = 0 where min(1, theta_rho) <= 0);
     - soundness: theta > 0 => theta <= theta_p exactly (endpoints in the closure of G);
     - tightness: theta = min(1, theta_rho), or theta_p < theta / (1 - tol[stage]) + 3 eps
-      (endpoints at that larger theta leave G).
+      (endpoints at that larger theta leave G); for faces of stage 3, when `model` (the
+      bound that stage documents, per face) is given: theta >= model (1 - tol[3]) - eps.
     Returns a dict of index arrays of the faces that fail each check."""
     f = np.asarray(faces, dtype=np.float32).astype(np.float64)
     th = np.asarray(theta, dtype=np.float32).astype(np.float64)
@@ -89,11 +90,57 @@ def check_certificate(faces, theta, stage, kappa, eps, tol):
     ok = endpoints_in_closed_G(us[pos], df[pos], half_length(th[pos], eps, kappa, up=True))
     bad_sound = pos[~ok]
     below = np.nonzero(th < t)[0]
+    if model is not None:
+        s3 = below[stage[below] == 3]
+        bad_model = s3[th[s3] < np.minimum(model[s3], t[s3]) * (1.0 - tol[3]) - eps]
+        below = below[stage[below] != 3]
+    else:
+        bad_model = np.zeros(0, dtype=np.int64)
     tl = np.asarray([tol[int(k)] for k in stage[below]]) if below.size else np.zeros(0)
     th_hi = th[below] / (1.0 - tl) + 3.0 * eps
     still_in = endpoints_in_closed_G(us[below], df[below], half_length(th_hi, eps, kappa, up=False))
-    bad_tight = below[still_in & (th_hi < t[below])]
+    bad_tight = np.concatenate([below[still_in & (th_hi < t[below])], bad_model])
     return {"range": bad_range, "sound": bad_sound, "tight": bad_tight}
+
+
+def _sum_dd(*terms):
+    """Sum of exact double terms, accurate to ~2^-104 of their magnitudes (TwoSum cascade)."""
+    s, c = terms[0], np.zeros_like(terms[0])
+    for t in terms[1:]:
+        s, e = _two_sum(s, t)
+        c = c + e
+    return s + c
+
+
+def fp64_stage_model(faces, kappa, eps):
+    """The lower bound of theta_p that the FP32 kernels' double-precision stage documents
+    (Sec. 3.4, eq. GQL), per face: gamma_0 = m1^2 + m2^2 - 2 rho E, gamma_1 / 2 and the
+    quadratic's coefficient c, each a chain of fused multiply-adds whose rounding error is
+    at most 2^-52 times the sum of the chain's partial results; the intervals D = -2 gamma_0
+    in [D_lo, D_hi], |gamma_1| <= G_hi, c <= c_hi; Delta <= G_hi^2 + 2 max(D c);
+    theta >= kappa min(rho / |drho|, D_lo / (G_hi + sqrt(Delta_hi))) - 2 eps. Evaluated here
+    with the chains summed accurately; 0 where D_lo <= 0."""
+    f = np.asarray(faces, dtype=np.float32).astype(np.float64)
+    rs, m1, m2, E, dr, dm1, dm2, dE = f[:, :8].T
+    g0i = _sum_dd(m2 * m2, -2.0 * rs * E)
+    g0 = _sum_dd(m1 * m1, m2 * m2, -2.0 * rs * E)
+    e0 = (np.abs(g0i) + np.abs(g0)) * 2.0 ** -52
+    D_lo, D_hi = -2.0 * (g0 + e0), -2.0 * (g0 - e0)
+    h1 = _sum_dd(dm1 * m1, dm2 * m2)
+    h2 = _sum_dd(dE * rs, -(dm1 * m1), -(dm2 * m2))
+    h3 = _sum_dd(dr * E, dE * rs, -(dm1 * m1), -(dm2 * m2))
+    G_hi = 2.0 * (np.abs(h3) + (np.abs(h1) + np.abs(h2) + np.abs(h3)) * 2.0 ** -52)
+    ci = _sum_dd(dm2 * dm2, -2.0 * dr * dE)
+    cq = _sum_dd(dm1 * dm1, dm2 * dm2, -2.0 * dr * dE)
+    c_hi = cq + (np.abs(ci) + np.abs(cq)) * 2.0 ** -52
+    Dc_hi = np.where(c_hi >= 0.0, D_hi * c_hi, D_lo * c_hi)
+    N_hi = G_hi + np.sqrt(np.maximum(G_hi * G_hi + 2.0 * Dc_hi, 0.0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = np.where(np.abs(dr) > 0, rs / np.abs(dr), np.inf)
+        inv = np.where(N_hi > 0, np.minimum(inv, D_lo / N_hi), inv)
+    th = kappa * inv - 2.0 * eps
+    th = np.where(np.isinf(inv), 1.0, th)
+    return np.where((D_lo > 0.0) & (rs > 0.0), np.maximum(th, 0.0), 0.0)
 
 
 # ---------------------------------------------------------------- face generators
