@@ -48,6 +48,7 @@ struct FusedSmem {
     T rsx[2][kFB];             // rho* of x-face (b, b+1)
     T thx[2][kFB];             // theta of x-face (b, b+1)
     unsigned long long bar[kRawSlots];
+    unsigned long long rowbar;   // per-row split barrier (PP and the fixed thetas): one arrival per warp
     int item;
     int abort;
 };
@@ -142,7 +143,7 @@ struct FusedCtx {
     T *__restrict__ out;
     Monitor<T> &mon;
     int b, zin;
-    uint32_t &nissued, &nconsumed;
+    uint32_t &nissued, &nconsumed, &nrowbar;
     int xb, xpad, c, y0, y1, R1;
     // Face states of the x-face (c+1/2) of row R-1 and of the y-face between rows R-2
     // and R-1. PP and the fixed thetas carry them from the previous row; LMP / RLMP,
@@ -278,25 +279,10 @@ struct FusedCtx {
         return true;
     }
 
-    // One row iteration; returns false if a wait timed out (the CTA then stops).
-    __device__ __forceinline__ bool row(int R) {
-        Hist<T> h0;
-        // ---------------------------------------------------------------- P1
-        const T rsy_new = p1(R, h0);
-        const int xs = R & 3;
-        __syncthreads();                                                  // S1
-        if (S.abort) return false;
-        if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
-
-        const int bl = b > 0 ? b - 1 : 0, br = b < kFB - 1 ? b + 1 : b;
-        // ---------------------------------------------------------------- P2
-        T mu1 = T(0), nu1 = T(0), muR = T(0), nuR = T(0);
-        if (LIM == VLBM_LIM_LMP || LIM == VLBM_LIM_RLMP) {
-            bounds(R, rsy_new, bl, mu1, nu1);
-            bounds_right(R, br, muR, nuR);
-        }
-        // ---------------------------------------------------------------- P3
-        T tx, ty;
+    // Theta of the x-face (c, c+1) of row R - 1 and of the y-face (R - 2, R - 1) of the
+    // own column (P3), with the sponge layer; (mu1, nu1) and (muR, nuR) are the density
+    // bounds of row R - 1 of the own column and of the one to the right (LMP / RLMP).
+    __device__ __forceinline__ void thetas(int R, int br, T mu1, T nu1, T muR, T nuR, T &tx, T &ty) {
         // theta is needed for the x-faces of columns kFHalo-1 .. kFHalo+kFOut-1 and the
         // y-faces of the strip's own columns, inside the grid. The other threads hold
         // halo padding or (past the last column) TMA fill, on which the FP32 screen
@@ -340,6 +326,40 @@ struct FusedCtx {
             const bool c1 = sp.cell(c, R - 1);
             if (c1 || sp.cell(c + 1, R - 1)) tx = T(0);        // x-face (c, c+1) of row R-1
             if (c1 || sp.cell(c, R - 2)) ty = T(0);            // y-face (R-2, R-1) of column c
+        }
+    }
+
+    // One row iteration; returns false if a wait timed out (the CTA then stops).
+    __device__ __forceinline__ bool row(int R) {
+        Hist<T> h0;
+        // ---------------------------------------------------------------- P1
+        const T rsy_new = p1(R, h0);
+        const int xs = R & 3;
+        const int bl = b > 0 ? b - 1 : 0, br = b < kFB - 1 ? b + 1 : b;
+        T mu1 = T(0), nu1 = T(0), muR = T(0), nuR = T(0);
+        T tx, ty;
+        if constexpr (kRecompute) {
+            __syncthreads();                                              // S1
+            if (S.abort) return false;
+            if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
+            // -------------------------------------------------------- P2
+            bounds(R, rsy_new, bl, mu1, nu1);
+            bounds_right(R, br, muR, nuR);
+            // -------------------------------------------------------- P3
+            thetas(R, br, mu1, nu1, muR, nuR, tx, ty);
+        } else {
+            // S1 split in two: this warp's ring writes are released by its arrival; the
+            // thetas of the previous row's faces read only registers, so they run before
+            // the wait for the other warps' arrivals (a warp that finished P1 early does
+            // useful work instead of stalling at a full barrier). The thetas are stored
+            // after the wait: their slot was read by neighbours in the previous row's P4.
+            __syncwarp();
+            if ((b & 31) == 0) mbar_arrive(&S.rowbar);
+            thetas(R, br, mu1, nu1, muR, nuR, tx, ty);
+            if (!mbar_wait_bounded(&S.rowbar, nrowbar & 1u)) S.abort = 1;
+            ++nrowbar;
+            if (S.abort) return false;
+            if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
         }
         S.thx[(R - 1) & 1][b] = tx;
         mu2 = mu1;
@@ -420,11 +440,12 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
     }
     if (b == 0) {
         for (int s = 0; s < kRawSlots; ++s) mbar_init(&S.bar[s], 1);
+        mbar_init(&S.rowbar, kFB / 32);
         S.abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
-    uint32_t nissued = 0, nconsumed = 0;
+    uint32_t nissued = 0, nconsumed = 0, nrowbar = 0;
     bool ok = true;
     if constexpr (PROBE) {
         const unsigned int probe = B.insts[0].ctl->wait_probe_ns;
@@ -454,7 +475,7 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         Monitor<T> mon;
         mon.init();
         FusedCtx<T, LIM> X{S, &D.tmap, geo, k, (n & 1) ? D.buf0 : D.buf1, mon, b, (n & 1) ? kNPlane : 0,
-                           nissued, nconsumed};
+                           nissued, nconsumed, nrowbar};
         X.y0 = it.y0;
         X.y1 = it.y1;
         X.xb = kFOut * it.strip - kFHalo;

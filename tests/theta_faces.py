@@ -116,8 +116,10 @@ def fp64_stage_model(faces, kappa, eps):
     """The lower bound of theta_p that the FP32 kernels' double-precision stage documents
     (Sec. 3.4, eq. GQL), per face: gamma_0 = m1^2 + m2^2 - 2 rho E, gamma_1 / 2 and the
     quadratic's coefficient c, each a chain of fused multiply-adds whose rounding error is
-    at most 2^-52 times the sum of the chain's partial results; the intervals D = -2 gamma_0
-    in [D_lo, D_hi], |gamma_1| <= G_hi, c <= c_hi; Delta <= G_hi^2 + 2 max(D c);
+    at most e = 2^-52 times the sum of the chain's partial results. The stage widens its
+    computed value by e; its computed value may itself sit e from the exact one, so in
+    terms of the exact values: D = -2 gamma_0 >= D_lo = -2 (gamma_0 + 2 e0), |gamma_1| <= G_hi
+    = 2 (|gamma_1 / 2| + 2 e1), c <= c_hi = c + 2 ec; Delta <= G_hi^2 + 2 max(D c);
     theta >= kappa min(rho / |drho|, D_lo / (G_hi + sqrt(Delta_hi))) - 2 eps. Evaluated here
     with the chains summed accurately; 0 where D_lo <= 0."""
     f = np.asarray(faces, dtype=np.float32).astype(np.float64)
@@ -125,14 +127,14 @@ def fp64_stage_model(faces, kappa, eps):
     g0i = _sum_dd(m2 * m2, -2.0 * rs * E)
     g0 = _sum_dd(m1 * m1, m2 * m2, -2.0 * rs * E)
     e0 = (np.abs(g0i) + np.abs(g0)) * 2.0 ** -52
-    D_lo, D_hi = -2.0 * (g0 + e0), -2.0 * (g0 - e0)
+    D_lo, D_hi = -2.0 * (g0 + 2.0 * e0), -2.0 * (g0 - 2.0 * e0)
     h1 = _sum_dd(dm1 * m1, dm2 * m2)
     h2 = _sum_dd(dE * rs, -(dm1 * m1), -(dm2 * m2))
     h3 = _sum_dd(dr * E, dE * rs, -(dm1 * m1), -(dm2 * m2))
-    G_hi = 2.0 * (np.abs(h3) + (np.abs(h1) + np.abs(h2) + np.abs(h3)) * 2.0 ** -52)
+    G_hi = 2.0 * (np.abs(h3) + 2.0 * (np.abs(h1) + np.abs(h2) + np.abs(h3)) * 2.0 ** -52)
     ci = _sum_dd(dm2 * dm2, -2.0 * dr * dE)
     cq = _sum_dd(dm1 * dm1, dm2 * dm2, -2.0 * dr * dE)
-    c_hi = cq + (np.abs(ci) + np.abs(cq)) * 2.0 ** -52
+    c_hi = cq + 2.0 * (np.abs(ci) + np.abs(cq)) * 2.0 ** -52
     Dc_hi = np.where(c_hi >= 0.0, D_hi * c_hi, D_lo * c_hi)
     N_hi = G_hi + np.sqrt(np.maximum(G_hi * G_hi + 2.0 * Dc_hi, 0.0))
     with np.errstate(divide="ignore", invalid="ignore"):
