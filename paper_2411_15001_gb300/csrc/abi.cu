@@ -40,10 +40,9 @@ Layout make_layout(int nx, int ny, int elem) {
     L.nx = nx;
     L.ny = ny;
     L.elem = elem;
-    L.pitch = ((nx + kOX + 2 + 31) / 32) * 32;
+    L.pitch = ((nx + 2 * kOX + 7) / 8) * 8;
     L.rows = ny + 2 * kOY;
-    L.plane = (((long long)L.pitch * L.rows + 63) / 64) * 64;
-    L.buf_bytes = (size_t)L.plane * kNPlane * elem;
+    L.buf_bytes = (((size_t)L.rows * kNGroup * L.pitch * 4 * elem + 255) / 256) * 256;
     L.ctl_offset = 2 * L.buf_bytes;
     L.desc_offset = L.ctl_offset + ((sizeof(DevCtl) + 255) / 256) * 256;
     // descriptor block: InstDesc (512 B), BatchCtl (256 B), item table (bands of at
@@ -104,7 +103,6 @@ static void build_desc(vlbm_state *s) {
     d.tmap = s->tmap;
     d.buf0 = (T *)s->ws;
     d.buf1 = (T *)((char *)s->ws + s->L.buf_bytes);
-    d.plane = s->L.plane;
     d.pitch = s->L.pitch;
     d.nx = s->grid.nx;
     d.ny = s->grid.ny;
@@ -158,8 +156,13 @@ cudaError_t vlbm::api::step_once(vlbm_state *s) {
 }
 
 namespace vlbm {
-// TMA descriptor of the two state buffers of a grid seen as one 3D tensor
-// [40 planes][ny + 4 rows][pitch columns]; a box is 128 columns x 1 row x 20 planes.
+// TMA descriptor of the two state buffers of a grid seen as one 4D tensor
+// [2 buffers][ny + 4 rows][5 groups][4 pitch values] (a group row -- every column's
+// four components -- is one contiguous dimension); a box is 64 columns (256 values) of
+// all five groups of one row, so a strip row of 128 columns is two boxes. The box's
+// innermost extent is 1 KB (FP32): a box with 16-byte innermost rows (one cell's group)
+// was measured 4 % slower on the 4096^2 step. The innermost coordinate, 4 x the column,
+// is always a multiple of 16 bytes, so a box may start at any column.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -177,11 +180,12 @@ bool encode_state_tmap(CUtensorMap *out, void *base, const Layout &L) {
         }
         encode = (EncodeTiledFn)fn;
     }
-    const cuuint64_t dims[3] = {(cuuint64_t)L.pitch, (cuuint64_t)L.rows, (cuuint64_t)(2 * kNPlane)};
-    const cuuint64_t strides[2] = {(cuuint64_t)L.pitch * L.elem, (cuuint64_t)L.plane * L.elem};
-    const cuuint32_t box[3] = {(cuuint32_t)kFusedBox, 1u, (cuuint32_t)kNPlane};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult r = encode(out, L.elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+    const cuuint64_t dims[4] = {(cuuint64_t)4 * L.pitch, (cuuint64_t)kNGroup, (cuuint64_t)L.rows, 2u};
+    const cuuint64_t strides[3] = {(cuuint64_t)4 * L.pitch * L.elem, (cuuint64_t)kNGroup * 4 * L.pitch * L.elem,
+                                   (cuuint64_t)L.buf_bytes};
+    const cuuint32_t box[4] = {(cuuint32_t)(4 * kFusedBox / 2), (cuuint32_t)kNGroup, 1u, 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    CUresult r = encode(out, L.elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                         base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -357,7 +361,7 @@ int vlbm_init(const vlbm_grid *grid, double gamma, double lambda, int32_t limite
                                                       : fused_occupancy<float>(limiter);
             const long long ctas = (long long)per_sm * (sms > 0 ? sms : 1);
             // guided bands of at most kFusedMaxChunk rows
-            long long work = (long long)((grid->nx + kFusedOut - 1) / kFusedOut) * grid->ny;
+            long long work = (long long)strip_count(grid->nx) * grid->ny;
             s->items_host.resize(max_items(grid->nx, grid->ny));
             s->nitems = append_items(s->items_host.data(), 0, grid->nx, grid->ny, kFusedMaxChunk, true, work, ctas);
             s->items_host.resize(s->nitems);

@@ -87,7 +87,7 @@ template <typename T>
 static cudaError_t launch_adjoint_init(const T *init_state, const Layout &L, const StepConsts<T> *kc, const T *cot,
                                        T *grad, double *abar, cudaStream_t s) {
     const dim3 blk(32, 8), grd((L.nx + 31) / 32, (L.ny + 7) / 8);
-    k_adjoint_init<T><<<grd, blk, 0, s>>>(init_state, L.plane, L.pitch, L.nx, L.ny, kc, cot, grad, abar);
+    k_adjoint_init<T><<<grd, blk, 0, s>>>(init_state, L.pitch, L.nx, L.ny, kc, cot, grad, abar);
     return cudaGetLastError();
 }
 
@@ -121,9 +121,9 @@ template <typename T>
 static cudaError_t hand_over_abar(const T *st, const Layout &L, double gamma, double alpha, ARed *red, T *cot,
                                   const double *lam_bc, cudaStream_t s) {
     const dim3 blk(32, 8), grd((L.nx + 31) / 32, (L.ny + 7) / 8);
-    k_lambda_max<T><<<grd, blk, 0, s>>>(st, L.plane, L.pitch, L.nx, L.ny, (T)gamma, &red->key);
-    k_lambda_argmax<T><<<grd, blk, 0, s>>>(st, L.plane, L.pitch, L.nx, L.ny, (T)gamma, &red->key, &red->idx);
-    k_lambda_apply<T><<<1, 1, 0, s>>>(st, L.plane, L.pitch, L.nx, gamma, alpha, &red->abar, &red->key, &red->idx, cot,
+    k_lambda_max<T><<<grd, blk, 0, s>>>(st, L.pitch, L.nx, L.ny, (T)gamma, &red->key);
+    k_lambda_argmax<T><<<grd, blk, 0, s>>>(st, L.pitch, L.nx, L.ny, (T)gamma, &red->key, &red->idx);
+    k_lambda_apply<T><<<1, 1, 0, s>>>(st, L.pitch, L.nx, gamma, alpha, &red->abar, &red->key, &red->idx, cot,
                                       (long long)L.nx * L.ny, lam_bc);
     return cudaGetLastError();
 }
@@ -313,7 +313,6 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     }
     int cur = 0;
     AdjArgs<T> A;
-    A.plane = s->L.plane;
     A.pitch = s->L.pitch;
     A.nx = s->grid.nx;
     A.ny = s->grid.ny;

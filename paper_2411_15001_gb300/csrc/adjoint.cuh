@@ -35,7 +35,6 @@ namespace vlbm {
 template <typename T>
 struct AdjArgs {
     const T *fwd;          // forward state s^n (padded, ghost frame filled)
-    long long plane;
     int pitch, nx, ny;
     const T *cot_in;       // cotangent of s^{n+1}: 20 compact planes
     T *cot_out;            // cotangent of s^n: 20 compact planes
@@ -310,7 +309,7 @@ __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
     const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - e, j = (int)(blockIdx.y * blockDim.y + threadIdx.y) - e;
     if (i >= A.nx || j >= A.ny) return;
     const StepConsts<T> k = *A.k;
-    const CellLoad<T> L{A.fwd, A.plane, A.pitch};
+    const CellLoad<T> L{A.fwd, A.pitch};
     const long long N = (long long)A.nx * A.ny, NL = lmp_cells(A);
     auto out_cell = [&](int x, int y) -> long long {   // cotangent index of cell (x, y)'s outputs
         if (EXT) return ((unsigned)x >= (unsigned)A.nx || (unsigned)y >= (unsigned)A.ny) ? -1 : (long long)y * A.nx + x;
@@ -405,7 +404,7 @@ __global__ void __launch_bounds__(256) k_adj_lmp_bounds(AdjArgs<T> A) {
     const T mb = P[kLmub * NL + cC], nb = P[kLnub * NL + cC];
     if (mb == T(0) && nb == T(0)) return;
     const StepConsts<T> k = *A.k;
-    const CellLoad<T> L{A.fwd, A.plane, A.pitch};
+    const CellLoad<T> L{A.fwd, A.pitch};
     T mu, nu;
     int a, b;
     lmp_bounds<T, LIM>(L, i, j, k, &mu, &nu, &a, &b);
@@ -426,7 +425,7 @@ __global__ void __launch_bounds__(256) k_adj_lmp_bounds(AdjArgs<T> A) {
 template <typename T, int LIM, bool DA, bool EXT>
 __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j) {
     const StepConsts<T> k = *A.k;
-    CellLoad<T> L{A.fwd, A.plane, A.pitch};
+    CellLoad<T> L{A.fwd, A.pitch};
     const long long N = (long long)A.nx * A.ny;
     // ---------------------------------------------------------- forward quantities
     T uC[4], uW[4], uE[4], uS[4], uN[4];
@@ -682,7 +681,7 @@ __global__ void __launch_bounds__(256) k_adj_lmp_ring(AdjArgs<T> A) {
     }
     if (any) {   // only then is the cell's state read (a ring cell on a corner may hold none)
         const StepConsts<T> k = *A.k;
-        const CellLoad<T> L{A.fwd, A.plane, A.pitch};
+        const CellLoad<T> L{A.fwd, A.pitch};
         T u[4], wx[4], wy[4], rx[4], ry[4];
         L.u4(0, i, j, u);
 #pragma unroll
@@ -724,7 +723,7 @@ __global__ void __launch_bounds__(256) k_adjoint_step(AdjArgs<T> A) {
 // read from the padded initial state and a^0 held fixed.
 // With abar (not NULL), also the init map's part of dL/da^0: u_k^0 = M_k(u_0; a^0).
 template <typename T>
-__global__ void __launch_bounds__(256) k_adjoint_init(const T *init_state, long long plane, int pitch, int nx,
+__global__ void __launch_bounds__(256) k_adjoint_init(const T *init_state, int pitch, int nx,
                                                       int ny, const StepConsts<T> *kc, const T *cot, T *grad,
                                                       double *abar) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -733,7 +732,7 @@ __global__ void __launch_bounds__(256) k_adjoint_init(const T *init_state, long 
     if (i < nx && j < ny) {
         const long long N = (long long)nx * ny, c = (long long)j * nx + i;
         const T w = kc->w, inv2a = kc->inv2a, gm1 = kc->gm1;
-        const CellLoad<T> L{init_state, plane, pitch};
+        const CellLoad<T> L{init_state, pitch};
         T u[4], wx[4], wy[4], rx[4], ry[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -768,13 +767,13 @@ __global__ void __launch_bounds__(256) k_adjoint_init(const T *init_state, long 
 // Pass 1: *key = max over the cells of s (padded) of the ordered key of lambda,
 // computed as the forward run's monitors compute it.
 template <typename T>
-__global__ void __launch_bounds__(256) k_lambda_max(const T *st, long long plane, int pitch, int nx, int ny, T gamma,
+__global__ void __launch_bounds__(256) k_lambda_max(const T *st, int pitch, int nx, int ny, T gamma,
                                                     unsigned long long *key) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     unsigned long long kk = 0ull;
     if (i < nx && j < ny) {
-        const CellLoad<T> L{st, plane, pitch};
+        const CellLoad<T> L{st, pitch};
         T u[4];
         L.u4(0, i, j, u);
         kk = ordered_key((double)cell_speed(u, gamma, gamma - T(1)));
@@ -790,12 +789,12 @@ __global__ void __launch_bounds__(256) k_lambda_max(const T *st, long long plane
 // Pass 2: *idx = the smallest cell index j nx + i whose lambda is the max (the
 // subgradient of the max taken at one of its cells).
 template <typename T>
-__global__ void __launch_bounds__(256) k_lambda_argmax(const T *st, long long plane, int pitch, int nx, int ny, T gamma,
+__global__ void __launch_bounds__(256) k_lambda_argmax(const T *st, int pitch, int nx, int ny, T gamma,
                                                        const unsigned long long *key, unsigned int *idx) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= nx || j >= ny) return;
-    const CellLoad<T> L{st, plane, pitch};
+    const CellLoad<T> L{st, pitch};
     T u[4];
     L.u4(0, i, j, u);
     if (ordered_key((double)cell_speed(u, gamma, gamma - T(1))) == *key) atomicMin(idx, (unsigned)(j * nx + i));
@@ -806,7 +805,7 @@ __global__ void __launch_bounds__(256) k_lambda_argmax(const T *st, long long pl
 // When the prescribed boundary states' speed lam_bc exceeds every cell's (the step
 // compares them the same way), lambda^n does not depend on the state: nothing is added.
 template <typename T>
-__global__ void k_lambda_apply(const T *st, long long plane, int pitch, int nx, double gamma, double alpha,
+__global__ void k_lambda_apply(const T *st, int pitch, int nx, double gamma, double alpha,
                                double *abar, unsigned long long *key, unsigned int *idx, T *cot, long long N,
                                const double *lam_bc) {
     const unsigned int id = *idx;
@@ -817,7 +816,7 @@ __global__ void k_lambda_apply(const T *st, long long plane, int pitch, int nx, 
     *idx = 0xffffffffu;
     if (id == 0xffffffffu || ab == 0.0 || bc_wins) return;
     const int i = (int)(id % (unsigned)nx), j = (int)(id / (unsigned)nx);
-    const CellLoad<T> L{st, plane, pitch};
+    const CellLoad<T> L{st, pitch};
     T ut[4];
     L.u4(0, i, j, ut);
     const double r = ut[0], m1 = ut[1], m2 = ut[2], E = ut[3];

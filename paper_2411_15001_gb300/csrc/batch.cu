@@ -106,7 +106,6 @@ static StepArgs<T> inst_args(const vlbm_batch *b, int i) {
     StepArgs<T> A;
     A.buf0 = (T *)((char *)b->ws + b->buf_off[i]);
     A.buf1 = (T *)((char *)b->ws + b->buf_off[i] + b->L[i].buf_bytes);
-    A.plane = b->L[i].plane;
     A.pitch = b->L[i].pitch;
     A.nx = b->grids[i].nx;
     A.ny = b->grids[i].ny;
@@ -139,7 +138,7 @@ static void build_items(vlbm_batch *b) {
     const bool guided = b->order == VLBM_ORDER_GUIDED;
     long long work = 0;
     for (int i = 0; i < b->n; ++i)
-        work += (long long)((b->grids[i].nx + kFusedOut - 1) / kFusedOut) * b->grids[i].ny;
+        work += (long long)strip_count(b->grids[i].nx) * b->grids[i].ny;
     const long long ctas = (long long)b->ctas_per_sm * b->sms;
     size_t used = 0;
     for (int i : ord) {
@@ -149,7 +148,6 @@ static void build_items(vlbm_batch *b) {
         const StepArgs<T> A = inst_args<T>(b, i);
         d.buf0 = A.buf0;
         d.buf1 = A.buf1;
-        d.plane = A.plane;
         d.pitch = A.pitch;
         d.nx = A.nx;
         d.ny = A.ny;

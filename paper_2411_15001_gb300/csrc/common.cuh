@@ -8,9 +8,37 @@
 
 namespace vlbm {
 
+// Offset of value 0 of cell (i, j) in a state buffer, and of value q relative to it
+// (layout: sidx in vlbm_internal.h).
 template <typename T>
 __device__ __forceinline__ long long cidx(const StepArgs<T> &A, int i, int j) {
-    return (long long)(j + kOY) * A.pitch + (i + kOX);
+    return sidx(A.pitch, 0, i, j);
+}
+template <typename T>
+__device__ __forceinline__ long long qoff(const StepArgs<T> &A, int q) {
+    return (long long)(q >> 2) * 4 * A.pitch + (q & 3);
+}
+
+// The four values of one group of a cell (state layout in vlbm_internal.h): one vector
+// access (16 bytes in FP32, two of 16 bytes in FP64); `p` is 16-byte aligned.
+template <typename T>
+__device__ __forceinline__ void ld_group(const T *p, T v[4]) {
+    if constexpr (is_f64<T>::value) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void st_group(T *p, T a, T b, T c, T d) {
+    if constexpr (is_f64<T>::value) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+    } else {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    }
 }
 
 // NaN-propagating max / min.
@@ -96,15 +124,13 @@ struct Monitor {
         bad = nonfin = fp64 = 0u;
     }
     __device__ __forceinline__ void add_cell(const T u[4], T gamma, T gm1) {
-        const T sp = cell_speed(u, gamma, gm1);   // NaN or inf if any component is
-        lam = pmax(lam, sp);
-        minrho = pmin(minrho, u[0]);
         // internal energy in the state's precision (reported; admissibility below
         // is decided by the exact test)
-        T ir;
-        if constexpr (is_f64<T>::value) ir = 1.0 / u[0];
-        else ir = fast_rcp(u[0]);
-        minrhoe = pmin(minrhoe, u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ir);
+        T rhoe;
+        const T sp = cell_speed_rhoe(u, gamma, gm1, rhoe);   // NaN or inf if any component is
+        lam = pmax(lam, sp);
+        minrho = pmin(minrho, u[0]);
+        minrhoe = pmin(minrhoe, rhoe);
         sum.add_cell(u);
         // no finite speed: a non-finite value, or finite values outside G (p < 0 gives a
         // NaN sound speed); a finite speed can still belong to a state outside G (rho < 0)
@@ -361,11 +387,11 @@ __device__ __forceinline__ bool write_dirichlet_ghost(const StepArgs<T> &A, T *b
     const long long dst = cidx(A, gi, gj);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        buf[q * A.plane + dst] = gs.u[q];
-        buf[(4 + q) * A.plane + dst] = M1[q];
-        buf[(8 + q) * A.plane + dst] = M2[q];
-        buf[(12 + q) * A.plane + dst] = M3[q];
-        buf[(16 + q) * A.plane + dst] = M4[q];
+        buf[dst + qoff(A, q)] = gs.u[q];
+        buf[dst + qoff(A, (4 + q))] = M1[q];
+        buf[dst + qoff(A, (8 + q))] = M2[q];
+        buf[dst + qoff(A, (12 + q))] = M3[q];
+        buf[dst + qoff(A, (16 + q))] = M4[q];
     }
     return true;
 }
@@ -406,7 +432,7 @@ __global__ void k_ghosts(StepArgs<T> A) {
     const long long src = cidx(A, si, sj), dst = cidx(A, gi, gj);
     T v[kNPlane];
 #pragma unroll
-    for (int q = 0; q < kNPlane; ++q) v[q] = buf[q * A.plane + src];
+    for (int q = 0; q < kNPlane; ++q) v[q] = buf[src + qoff(A, q)];
     if (mx) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) { const T x = v[4 + c]; v[4 + c] = v[8 + c]; v[8 + c] = x; }
@@ -420,7 +446,7 @@ __global__ void k_ghosts(StepArgs<T> A) {
         for (int k = 0; k < 5; ++k) v[4 * k + 2] = -v[4 * k + 2];
     }
 #pragma unroll
-    for (int q = 0; q < kNPlane; ++q) buf[q * A.plane + dst] = v[q];
+    for (int q = 0; q < kNPlane; ++q) buf[dst + qoff(A, q)] = v[q];
 }
 
 // ----------------------------------------------------------------- initial state
@@ -440,7 +466,7 @@ __global__ void k_init_load(StepArgs<T> A, const T *__restrict__ rho, const T *_
         T u[4] = {rho[k], mom[k], mom[N + k], E[k]};
         const long long d = cidx(A, i, j);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) A.buf0[c * A.plane + d] = u[c];
+        for (int c = 0; c < 4; ++c) A.buf0[d + qoff(A, c)] = u[c];
         m.add_cell(u, gamma, gm1);
     }
     block_publish(m, C);
@@ -493,16 +519,16 @@ __global__ void k_init_pops(StepArgs<T> A) {
     const long long d = cidx(A, i, j);
     T u[4], f[4], g[4], M1[4], M2[4], M3[4], M4[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) u[c] = A.buf0[c * A.plane + d];
+    for (int c = 0; c < 4; ++c) u[c] = A.buf0[d + qoff(A, c)];
     euler_fluxes(u, k.gm1, f, g);
     maxwell_pm(u, f, k, M1, M2);
     maxwell_pm(u, g, k, M3, M4);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        A.buf0[(4 + c) * A.plane + d] = M1[c];
-        A.buf0[(8 + c) * A.plane + d] = M2[c];
-        A.buf0[(12 + c) * A.plane + d] = M3[c];
-        A.buf0[(16 + c) * A.plane + d] = M4[c];
+        A.buf0[d + qoff(A, (4 + c))] = M1[c];
+        A.buf0[d + qoff(A, (8 + c))] = M2[c];
+        A.buf0[d + qoff(A, (12 + c))] = M3[c];
+        A.buf0[d + qoff(A, (16 + c))] = M4[c];
     }
 }
 
@@ -515,12 +541,12 @@ __global__ void k_moments(StepArgs<T> A, T *rho, T *mom, T *E) {
     if (i >= A.nx || j >= A.ny) return;
     const T *buf = (A.ctl->n & 1) ? A.buf1 : A.buf0;
     const long long d = cidx(A, i, j), k = (long long)j * A.nx + i, N = (long long)A.nx * A.ny;
-    if (rho) rho[k] = buf[d];
+    if (rho) rho[k] = buf[d + qoff(A, 0)];
     if (mom) {
-        mom[k] = buf[A.plane + d];
-        mom[N + k] = buf[2 * A.plane + d];
+        mom[k] = buf[d + qoff(A, 1)];
+        mom[N + k] = buf[d + qoff(A, 2)];
     }
-    if (E) E[k] = buf[3 * A.plane + d];
+    if (E) E[k] = buf[d + qoff(A, 3)];
 }
 
 // Checkpoint: 64-byte header {n, t, a, dt, a_free, t_end, last|done<<1, status},
@@ -547,7 +573,7 @@ __global__ void k_save(StepArgs<T> A, unsigned char *dst) {
     T *out = (T *)(dst + 64);
     const long long d = cidx(A, i, j), k = (long long)j * A.nx + i, N = (long long)A.nx * A.ny;
 #pragma unroll
-    for (int q = 0; q < kNPlane; ++q) out[q * N + k] = buf[q * A.plane + d];
+    for (int q = 0; q < kNPlane; ++q) out[q * N + k] = buf[d + qoff(A, q)];
 }
 
 // Restore: the state goes into buffer (n & 1) of the stored n, so that the
@@ -562,7 +588,7 @@ __global__ void k_load(StepArgs<T> A, const unsigned char *src) {
         const T *in = (const T *)(src + 64);
         const long long d = cidx(A, i, j), k = (long long)j * A.nx + i, N = (long long)A.nx * A.ny;
 #pragma unroll
-        for (int q = 0; q < kNPlane; ++q) buf[q * A.plane + d] = in[q * N + k];
+        for (int q = 0; q < kNPlane; ++q) buf[d + qoff(A, q)] = in[q * N + k];
     }
 }
 

@@ -20,7 +20,7 @@ struct vlbm_state {
     cudaStream_t stream;
     vlbm::DevCtl *ctl;
     int device;
-    CUtensorMap tmap;   // 3D view [40 planes][rows][pitch] of both state buffers
+    CUtensorMap tmap;   // 4D view [2 buffers][rows][5 groups][4 pitch] of both state buffers
     bool have_tmap;
     int nitems, fused_grid;
     std::vector<unsigned char> desc_host;   // InstDesc<T> of this grid
@@ -68,7 +68,6 @@ inline StepArgs<T> args_of(const vlbm_state *s) {
     StepArgs<T> A;
     A.buf0 = (T *)s->ws;
     A.buf1 = (T *)((char *)s->ws + s->L.buf_bytes);
-    A.plane = s->L.plane;
     A.pitch = s->L.pitch;
     A.nx = s->grid.nx;
     A.ny = s->grid.ny;

@@ -2,18 +2,19 @@
 // row-marching pass: every cell's 20 values are read from HBM once and written
 // once, together with the ghost images of the boundary cells.
 //
-// Work. A grid is cut into strips of kFOut = 120 output columns and bands of
-// rows; a work item is one (instance, strip, band), listed by the host in the
-// order CTAs take them (tall bands first under guided scheduling). Persistent CTAs of
-// kFB = 128 threads (one column each: four halo columns on either side of the
-// strip) take items from a global counter, so items that cost more (faces whose
+// Work. A grid is cut into strips of at most kFusedOut = 124 output columns (even
+// widths, strip_of) and bands of rows; a work item is one (instance, strip, band),
+// listed by the host in the order CTAs take them (tall bands first under guided
+// scheduling). Persistent CTAs of kFB = 128 threads (one column each: two halo
+// columns on either side of the strip, the radius of the LMP stencil) take items
+// from a global counter, so items that cost more (faces whose
 // theta_p needs the FP64 solve cluster on shocks) do not hold up the step. One
 // launch can advance many independent grids (a batch); each grid has its own
 // kinetic speed, control block and completion count, and the CTA that finishes a
 // grid's last item runs that grid's end-of-step reduction.
 //
-// Rows arrive by TMA (one 3D box of 128 columns x 20 planes per row) into a
-// 3-slot ring completed on mbarriers. Per row R (output row O = R - 2, the
+// Rows arrive by TMA (two boxes of 64 columns x 5 groups of 4 values per row, see the
+// state layout in vlbm_internal.h) into a 3-slot ring completed on mbarriers. Per row R (output row O = R - 2, the
 // radius-2 stencil of the LMP bounds, eq. LMP_minmax):
 //  P1  fluxes, Maxwellians, non-equilibrium parts d_k of row R; what x-neighbours
 //      need (u, f, d_1, d_2) goes to a 4-row shared ring, what only the own column
@@ -26,8 +27,8 @@
 // itself from the shared rows.
 //  P4  collide + stream of row O (eq. blending_u1 / blending_u), stores, ghost
 //      images, monitors.
-// Output rows start on 32-byte sector boundaries (kOX = 8, strips of 120 floats),
-// so no sector is written partially by two CTAs.
+// Strips start on even columns, so no 32-byte sector of a group row is written
+// partially by two CTAs; a cell's group goes out as one vector store.
 #pragma once
 
 #include "common.cuh"
@@ -35,15 +36,14 @@
 
 namespace vlbm {
 
-constexpr int kFB = 128;       // threads per CTA = TMA box width (columns)
-constexpr int kFOut = 120;     // output columns per strip
-constexpr int kFHalo = 4;      // box columns left of the strip
+constexpr int kFB = kFusedBox;     // threads per CTA = TMA box width (columns)
+constexpr int kFHalo = kFusedHalo; // box columns left (and right) of the strip
 constexpr int kRawSlots = 3;   // TMA row ring
 constexpr int kXSlots = 4;     // shared ring of per-row neighbour data
 
 template <typename T>
 struct FusedSmem {
-    T raw[kRawSlots][kNPlane][kFB];
+    T raw[kRawSlots][2][kNGroup][kFB / 2][4];   // [slot][half of the strip][group][column][component]
     T X[kXSlots][16][kFB];     // u (0..3), f (4..7), d_1 (8..11), d_2 (12..15)
     T rsx[2][kFB];             // rho* of x-face (b, b+1)
     T thx[2][kFB];             // theta of x-face (b, b+1)
@@ -61,7 +61,6 @@ struct Hist {
 // The fields of a grid's descriptor that the row loop uses, held in registers
 // (the descriptor itself lives in global memory).
 struct Geo {
-    long long plane;
     int pitch, nx, ny;
     int bc[4];
     int sponge;
@@ -121,15 +120,21 @@ __device__ __forceinline__ void write_ghost_images(const Geo &D, T *out, int c, 
     for (int a = 0; a < ngx; ++a)
         for (int e = 0; e < ngy; ++e) {
             if (a == 0 && e == 0) continue;
-            const long long d = (long long)(gy[e] + kOY) * D.pitch + (gx[a] + kOX);
+            T *base = out + sidx(D.pitch, 0, gx[a], gy[e]);
 #pragma unroll
-            for (int q = 0; q < kNPlane; ++q) {
-                int src = q;
-                if (mxs[a] && q >= 4 && q < 12) src = q < 8 ? q + 4 : q - 4;   // u_1 <-> u_2
-                if (mys[e] && q >= 12) src = q < 16 ? q + 4 : q - 4;           // u_3 <-> u_4
-                T v = nv[src];
-                if ((mxs[a] && (q & 3) == 1) || (mys[e] && (q & 3) == 2)) v = -v;  // normal momentum
-                out[q * D.plane + d] = v;
+            for (int g = 0; g < kNGroup; ++g) {
+                // u_1 <-> u_2 across an x-wall, u_3 <-> u_4 across a y-wall; the normal
+                // momentum of every group negated
+                const int gs = (g == 1 || g == 2) ? 3 - g : ((g == 3 || g == 4) ? 7 - g : g);
+                const bool sw = (g == 1 || g == 2) ? mxs[a] : ((g == 3 || g == 4) ? mys[e] : false);
+                T v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = sw ? nv[4 * gs + q] : nv[4 * g + q];
+                if (mxs[a]) v[1] = -v[1];
+                if (mys[e]) v[2] = -v[2];
+                T *gp = base + (long long)g * 4 * D.pitch;   // scalar stores: the images are rare, and a
+#pragma unroll                                                 // vector store would pin its values to aligned registers
+                for (int q = 0; q < 4; ++q) gp[q] = v[q];
             }
         }
 }
@@ -144,7 +149,7 @@ struct FusedCtx {
     Monitor<T> &mon;
     int b, zin;
     uint32_t &nissued, &nconsumed, &nrowbar;
-    int xb, xpad, c, y0, y1, R1;
+    int xb, xpad, c, y0, y1, R1, wout;   // strip: box origin, padded origin, own column, rows, width
     // Face states of the x-face (c+1/2) of row R-1 and of the y-face between rows R-2
     // and R-1. PP and the fixed thetas carry them from the previous row; LMP / RLMP,
     // whose density bounds keep more values live, recompute them where theta needs
@@ -166,7 +171,8 @@ struct FusedCtx {
     __device__ __forceinline__ void issue(int row) {
         const int slot = nissued % kRawSlots;
         mbar_expect_tx(&S.bar[slot], (uint32_t)(kNPlane * kFB * sizeof(T)));
-        tma_load_3d(&S.raw[slot][0][0], tmap, &S.bar[slot], xpad, row + kOY, zin);
+        tma_load_4d(&S.raw[slot][0][0][0][0], tmap, &S.bar[slot], 4 * xpad, 0, row + kOY, zin);
+        tma_load_4d(&S.raw[slot][1][0][0][0], tmap, &S.bar[slot], 4 * (xpad + kFB / 2), 0, row + kOY, zin);
         ++nissued;
     }
 
@@ -183,43 +189,53 @@ struct FusedCtx {
         rsy_prev = mu2 = nu2 = thy_prev = T(0);
     }
 
-    // P1 of row R (see the file comment); returns rho* of the y-face R - 1/2.
-    __device__ __forceinline__ T p1(int R, Hist<T> &h0) {
+    // P1 of row R (see the file comment); returns rho* of the y-face R - 1/2. f and d1
+    // receive the own column's x-flux and d_1 (also in the shared ring) for next_faces.
+    __device__ __forceinline__ T p1(int R, Hist<T> &h0, T f[4], T d1[4]) {
         const int slot = nconsumed % kRawSlots;
         const uint32_t par = (nconsumed / kRawSlots) & 1u;
         ++nconsumed;
         if (!mbar_wait_bounded(&S.bar[slot], par)) S.abort = 1;
-        T u[4], f[4], g[4], M1[4], M2[4], M3[4], M4[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) u[q] = S.raw[slot][q][b];
+        T u[4], g[4], M1[4], M2[4], M3[4], M4[4], pv[4];
+        ld_group(&S.raw[slot][b >> 6][0][b & 63][0], u);
         euler_fluxes(u, k.gm1, f, g);
         maxwell_pm(u, f, k, M1, M2);
         maxwell_pm(u, g, k, M3, M4);
         const int xs = R & 3;
+        // each population group is read right where its non-equilibrium part is formed
+        ld_group(&S.raw[slot][b >> 6][1][b & 63][0], pv);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const T d1 = RN<T>::sub(M1[q], S.raw[slot][4 + q][b]);
-            const T d2 = RN<T>::sub(M2[q], S.raw[slot][8 + q][b]);
-            h0.d3[q] = RN<T>::sub(M3[q], S.raw[slot][12 + q][b]);
-            h0.d4[q] = RN<T>::sub(M4[q], S.raw[slot][16 + q][b]);
-            h0.u[q] = u[q];
-            h0.g[q] = g[q];
             S.X[xs][q][b] = u[q];
             S.X[xs][4 + q][b] = f[q];
-            S.X[xs][8 + q][b] = d1;
-            S.X[xs][12 + q][b] = d2;
+            d1[q] = RN<T>::sub(M1[q], pv[q]);
+            S.X[xs][8 + q][b] = d1[q];
+        }
+        ld_group(&S.raw[slot][b >> 6][2][b & 63][0], pv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) S.X[xs][12 + q][b] = RN<T>::sub(M2[q], pv[q]);   // d_2
+        ld_group(&S.raw[slot][b >> 6][3][b & 63][0], pv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h0.d3[q] = RN<T>::sub(M3[q], pv[q]);
+        ld_group(&S.raw[slot][b >> 6][4][b & 63][0], pv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            h0.d4[q] = RN<T>::sub(M4[q], pv[q]);
+            h0.u[q] = u[q];
+            h0.g[q] = g[q];
         }
         return face_star(h1.u[0], h1.g[0], u[0], g[0], k);  // y-face R - 1/2
     }
 
     // Face states of the x-face (b, b+1) of row R and of the y-face R - 1/2 (PP and
     // the fixed thetas), for theta in the next row.
-    __device__ __forceinline__ void next_faces(int R, const Hist<T> &h0, T rsy_new, int br) {
+    __device__ __forceinline__ void next_faces(int R, const Hist<T> &h0, T rsy_new, int br, const T f[4],
+                                               const T d1[4]) {
         const int xs = R & 3;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            xs_us[q] = face_star(S.X[xs][q][b], S.X[xs][4 + q][b], S.X[xs][q][br], S.X[xs][4 + q][br], k);
-            xs_df[q] = face_dflux(S.X[xs][8 + q][b], S.X[xs][12 + q][br], k);
+            xs_us[q] = face_star(h0.u[q], f[q], S.X[xs][q][br], S.X[xs][4 + q][br], k);
+            xs_df[q] = face_dflux(d1[q], S.X[xs][12 + q][br], k);
             ys_us[q] = q == 0 ? rsy_new : face_star(h1.u[q], h1.g[q], h0.u[q], h0.g[q], k);
             ys_df[q] = face_dflux(h1.d3[q], h0.d4[q], k);
         }
@@ -261,7 +277,8 @@ struct FusedCtx {
     // y0, the bounds of row y0 - 1 (LMP / RLMP).
     __device__ __forceinline__ bool row_warm(int R) {
         Hist<T> h0;
-        const T rsy_new = p1(R, h0);
+        T fo[4], d1o[4];
+        const T rsy_new = p1(R, h0, fo, d1o);
         __syncthreads();                                                  // S1
         if (S.abort) return false;
         if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
@@ -271,7 +288,7 @@ struct FusedCtx {
             const int xs = R & 3;
             S.rsx[R & 1][b] = face_star(h0.u[0], S.X[xs][4][b], S.X[xs][0][br], S.X[xs][4][br], k);
         } else {
-            next_faces(R, h0, rsy_new, br);
+            next_faces(R, h0, rsy_new, br, fo, d1o);
         }
         rsy_prev = rsy_new;
         h2 = h1;
@@ -283,11 +300,11 @@ struct FusedCtx {
     // own column (P3), with the sponge layer; (mu1, nu1) and (muR, nuR) are the density
     // bounds of row R - 1 of the own column and of the one to the right (LMP / RLMP).
     __device__ __forceinline__ void thetas(int R, int br, T mu1, T nu1, T muR, T nuR, T &tx, T &ty) {
-        // theta is needed for the x-faces of columns kFHalo-1 .. kFHalo+kFOut-1 and the
+        // theta is needed for the x-faces of columns kFHalo-1 .. kFHalo+wout-1 and the
         // y-faces of the strip's own columns, inside the grid. The other threads hold
         // halo padding or (past the last column) TMA fill, on which the FP32 screen
         // would fail and send the face to the FP64 solve: they skip theta.
-        const bool live = b >= kFHalo - 1 && b < kFHalo + kFOut && c < D.nx;
+        const bool live = b >= kFHalo - 1 && b < kFHalo + wout && c < D.nx;
         if (LIM == VLBM_LIM_FIRST_ORDER) {
             tx = ty = T(0);
         } else if (LIM == VLBM_LIM_NONE) {
@@ -317,7 +334,7 @@ struct FusedCtx {
             tx = combine_theta(trx, xs_us, xs_df, k, nx64);
             ty = combine_theta(try_, ys_us, ys_df, k, ny64);
             // faces counted once: an x-face by the cell west of it, a y-face by the one south of it
-            const bool col_own = b >= kFHalo && b < kFHalo + kFOut && c < D.nx;
+            const bool col_own = b >= kFHalo && b < kFHalo + wout && c < D.nx;
             if (col_own && R - 1 >= y0 && R - 1 < y1) mon.fp64 += nx64;
             if (col_own && R - 2 >= y0 && R - 2 < y1) mon.fp64 += ny64;
         }
@@ -332,8 +349,9 @@ struct FusedCtx {
     // One row iteration; returns false if a wait timed out (the CTA then stops).
     __device__ __forceinline__ bool row(int R) {
         Hist<T> h0;
+        T fo[4], d1o[4];
         // ---------------------------------------------------------------- P1
-        const T rsy_new = p1(R, h0);
+        const T rsy_new = p1(R, h0, fo, d1o);
         const int xs = R & 3;
         const int bl = b > 0 ? b - 1 : 0, br = b < kFB - 1 ? b + 1 : b;
         T mu1 = T(0), nu1 = T(0), muR = T(0), nuR = T(0);
@@ -368,7 +386,7 @@ struct FusedCtx {
             // rho* of the x-face (b, b+1) of row R, for the next row's density bounds
             S.rsx[R & 1][b] = face_star(h0.u[0], S.X[xs][4][b], S.X[xs][0][br], S.X[xs][4][br], k);
         } else {
-            next_faces(R, h0, rsy_new, br);
+            next_faces(R, h0, rsy_new, br, fo, d1o);
         }
         rsy_prev = rsy_new;
         // No barrier before P4: it reads theta of row R-2's x-faces (written by the
@@ -397,10 +415,11 @@ struct FusedCtx {
             p3n[q] = blend_pop(maxwell_plus(h2.u[q], h2.g[q], k), h2.d3[q], tn);
         }
         thy_prev = ty;
-        if (O >= y0 && O < y1 && b >= kFHalo && b < kFHalo + kFOut && c < D.nx) {
-            const long long d = (long long)(O + kOY) * D.pitch + (c + kOX);
+        if (O >= y0 && O < y1 && b >= kFHalo && b < kFHalo + wout && c < D.nx) {
+            T *base = out + sidx(D.pitch, 0, c, O);
 #pragma unroll
-            for (int q = 0; q < kNPlane; ++q) out[q * D.plane + d] = nv[q];
+            for (int g = 0; g < kNGroup; ++g)
+                st_group(base + (long long)g * 4 * D.pitch, nv[4 * g], nv[4 * g + 1], nv[4 * g + 2], nv[4 * g + 3]);
             if (c < 2 || c >= D.nx - 2 || O < 2 || O >= D.ny - 2) write_ghost_images(D, out, c, O, nv, &desc()->bd);
             mon.add_cell(nv, k.gamma, k.gm1);
         }
@@ -434,7 +453,7 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
     const int b = threadIdx.x;
     // TMA destinations must be 128-byte aligned; dynamic shared memory follows
     // the static block of the reductions, so check rather than assume.
-    if (smem_addr(&S.raw[0][0][0]) & 127u) {
+    if (smem_addr(&S.raw[0][0][0][0][0]) & 127u) {
         if (b == 0) atomicCAS(&B.insts[0].ctl->status, 0, VLBM_E_UNSUPPORTED);
         return;
     }
@@ -464,7 +483,6 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         DevCtl *C = D.ctl;
         if (C->done) continue;
         Geo geo;
-        geo.plane = D.plane;
         geo.pitch = D.pitch;
         geo.nx = D.nx;
         geo.ny = D.ny;
@@ -474,11 +492,12 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         const StepConsts<T> k = consts_of<T>(C);
         Monitor<T> mon;
         mon.init();
-        FusedCtx<T, LIM> X{S, &D.tmap, geo, k, (n & 1) ? D.buf0 : D.buf1, mon, b, (n & 1) ? kNPlane : 0,
+        FusedCtx<T, LIM> X{S, &D.tmap, geo, k, (n & 1) ? D.buf0 : D.buf1, mon, b, (n & 1) ? 1 : 0,
                            nissued, nconsumed, nrowbar};
         X.y0 = it.y0;
         X.y1 = it.y1;
-        X.xb = kFOut * it.strip - kFHalo;
+        X.wout = (int)((unsigned)it.xw >> 24);
+        X.xb = (it.xw & 0xffffff) - kFHalo;
         X.xpad = X.xb + kOX;
         X.c = X.xb + b;
         // LMP / RLMP start at row y0 - 2 (the bounds of row y0 - 1 need rho* of the

@@ -13,14 +13,11 @@ namespace vlbm {
 template <typename T>
 struct CellLoad {
     const T *__restrict__ in;
-    long long plane;
     int pitch;
-    __device__ __forceinline__ T v(int q, int i, int j) const {
-        return in[q * plane + (long long)(j + kOY) * pitch + (i + kOX)];
-    }
+    __device__ __forceinline__ T v(int q, int i, int j) const { return in[sidx(pitch, q, i, j)]; }
+    // values q0 .. q0 + 3 of cell (i, j), q0 a multiple of 4: a whole group, one vector load
     __device__ __forceinline__ void u4(int q0, int i, int j, T out[4]) const {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) out[c] = v(q0 + c, i, j);
+        ld_group(in + sidx(pitch, q0, i, j), out);
     }
 };
 
@@ -114,8 +111,8 @@ __device__ __forceinline__ void face_state(const T uL[4], const T fL[4], const T
 }
 
 // One cell of the blended collide + limit + stream step, gathering its radius-2
-// stencil through the loader L (L.v(q, i, j) = plane q at cell (i, j), ghost
-// cells included). Writes the cell's 20 new values to nv (u, then u_1..u_4).
+// stencil through the loader L (L.v(q, i, j) = value q of cell (i, j), ghost cells
+// included; L.u4(q0, i, j, out) = values q0 .. q0 + 3). Writes the cell's 20 new values to nv (u, then u_1..u_4).
 template <typename T, int LIM, typename Loader>
 __device__ __forceinline__ void cell_step(const Loader &L, int i, int j, const StepConsts<T> &k,
                                           const Sponge &sp, T nv[kNPlane], unsigned int &n_fp64) {
@@ -140,16 +137,27 @@ __device__ __forceinline__ void cell_step(const Loader &L, int i, int j, const S
     maxwell_pm(uN, gN, k, dum, M4N);
     // non-equilibrium parts d_k = M_k - u_k of the cells the update reads
     T d1C[4], d2C[4], d3C[4], d4C[4], d1W[4], d2E[4], d3S[4], d4N[4];
+    {
+        T p1C[4], p2C[4], p3C[4], p4C[4], p1W[4], p2E[4], p3S[4], p4N[4];
+        L.u4(4, i, j, p1C);
+        L.u4(8, i, j, p2C);
+        L.u4(12, i, j, p3C);
+        L.u4(16, i, j, p4C);
+        L.u4(4, i - 1, j, p1W);
+        L.u4(8, i + 1, j, p2E);
+        L.u4(12, i, j - 1, p3S);
+        L.u4(16, i, j + 1, p4N);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        d1C[c] = RN<T>::sub(M1C[c], L.v(4 + c, i, j));
-        d2C[c] = RN<T>::sub(M2C[c], L.v(8 + c, i, j));
-        d3C[c] = RN<T>::sub(M3C[c], L.v(12 + c, i, j));
-        d4C[c] = RN<T>::sub(M4C[c], L.v(16 + c, i, j));
-        d1W[c] = RN<T>::sub(M1W[c], L.v(4 + c, i - 1, j));
-        d2E[c] = RN<T>::sub(M2E[c], L.v(8 + c, i + 1, j));
-        d3S[c] = RN<T>::sub(M3S[c], L.v(12 + c, i, j - 1));
-        d4N[c] = RN<T>::sub(M4N[c], L.v(16 + c, i, j + 1));
+        for (int c = 0; c < 4; ++c) {
+            d1C[c] = RN<T>::sub(M1C[c], p1C[c]);
+            d2C[c] = RN<T>::sub(M2C[c], p2C[c]);
+            d3C[c] = RN<T>::sub(M3C[c], p3C[c]);
+            d4C[c] = RN<T>::sub(M4C[c], p4C[c]);
+            d1W[c] = RN<T>::sub(M1W[c], p1W[c]);
+            d2E[c] = RN<T>::sub(M2E[c], p2E[c]);
+            d3S[c] = RN<T>::sub(M3S[c], p3S[c]);
+            d4N[c] = RN<T>::sub(M4N[c], p4N[c]);
+        }
     }
     T usW[4], dfW[4], usE[4], dfE[4], usS[4], dfS[4], usN[4], dfN[4];
     face_state(uW, fW, uC, fC, d1W, d2C, k, usW, dfW);   // x-face i-1/2
@@ -187,7 +195,7 @@ __global__ void __launch_bounds__(256) k_step_simple(StepArgs<T> A) {
     DevCtl *C = A.ctl;
     if (C->done) return;
     const long long n = C->n;
-    CellLoad<T> L{(n & 1) ? A.buf1 : A.buf0, A.plane, A.pitch};
+    CellLoad<T> L{(n & 1) ? A.buf1 : A.buf0, A.pitch};
     T *__restrict__ out = (n & 1) ? A.buf0 : A.buf1;
     const StepConsts<T> k = consts_of<T>(C);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -197,9 +205,9 @@ __global__ void __launch_bounds__(256) k_step_simple(StepArgs<T> A) {
     if (i < A.nx && j < A.ny) {
         T nv[kNPlane];
         cell_step<T, LIM>(L, i, j, k, Sponge(A.sponge, A.nx, A.ny, A.bc), nv, mon.fp64);
-        const long long d = (long long)(j + kOY) * A.pitch + (i + kOX);
+        const long long d = cidx(A, i, j);
 #pragma unroll
-        for (int q = 0; q < kNPlane; ++q) out[q * A.plane + d] = nv[q];
+        for (int q = 0; q < kNPlane; ++q) out[d + qoff(A, q)] = nv[q];
         mon.add_cell(nv, k.gamma, k.gm1);
     }
     block_publish(mon, C);

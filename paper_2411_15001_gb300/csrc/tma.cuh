@@ -62,14 +62,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint3
     }
 }
 
-// 3D tiled TMA load of box (x, y, z) of `map` into shared memory, completing
-// on `bar` (transaction bytes counted there).
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, unsigned long long *bar,
-                                            int x, int y, int z) {
+// 4D tiled TMA load of the box at coordinates (c0 .. c3) of `map` into shared
+// memory, completing on `bar` (transaction bytes counted there).
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, unsigned long long *bar,
+                                            int c0, int c1, int c2, int c3) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
         : "memory");
 }
 

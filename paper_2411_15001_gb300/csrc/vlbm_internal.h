@@ -12,25 +12,31 @@
 
 namespace vlbm {
 
-// Padded plane layout. Cell (i, j), -2 <= i < nx+2, -2 <= j < ny+2, of plane q
-// in a state buffer lives at q * plane + (j + kOY) * pitch + (i + kOX).
-// Padded columns 6, 7 and nx+8, nx+9 hold the two ghost layers of the x sides,
-// rows 0, 1 and ny+2, ny+3 those of the y sides. kOX = 8 and a pitch that is a
-// multiple of 32 elements put interior column 0 of every row on a 32-byte
-// sector boundary: the row-marching kernel writes strips of 120 columns that
-// start on sector boundaries, and its TMA boxes (four columns left of a strip)
-// start on 16-byte boundaries.
-constexpr int kOX = 8;
+// State buffer layout: padded rows, each holding the five groups of four values of
+// its cells -- the conserved u, then the populations u_1..u_4 (u_5 is never stored),
+// each group's four components (rho, m1, m2, E) contiguous -- group after group:
+//   value q of cell (i, j), -2 <= i < nx+2, -2 <= j < ny+2, lives at
+//   (((j + kOY) * kNGroup + q / 4) * pitch + (i + kOX)) * 4 + q % 4.
+// A cell's group is one 16-byte (FP32) or 32-byte (FP64) vector, so a warp moves 32
+// consecutive cells' group as one contiguous, sector-aligned 512 (1024) bytes, and a
+// thread loads or stores a whole group with one vector access. Padded columns 0, 1
+// and nx+2, nx+3 hold the two ghost layers of the x sides, rows 0, 1 and ny+2, ny+3
+// those of the y sides; pitch (cells) is a multiple of 8.
+constexpr int kOX = 2;
 constexpr int kOY = 2;
 constexpr int kNPlane = 20;   // u (4) and u_1..u_4 (4 each); u_5 is never stored
+constexpr int kNGroup = 5;    // groups of four values per cell
+
+__host__ __device__ __forceinline__ long long sidx(int pitch, int q, int i, int j) {
+    return (((long long)(j + kOY) * kNGroup + (q >> 2)) * pitch + (i + kOX)) * 4 + (q & 3);
+}
 
 struct Layout {
     int nx, ny;
-    int pitch;          // elements per padded row (multiple of 32)
+    int pitch;          // cells per padded row of one group (nx + 2 kOX, a multiple of 8)
     int rows;           // ny + 4
-    long long plane;    // elements per plane (multiple of 64)
     int elem;           // bytes per element (4 or 8)
-    size_t buf_bytes;   // bytes of one 20-plane buffer
+    size_t buf_bytes;   // bytes of one 20-value state buffer
     size_t ctl_offset;  // byte offset of the control block in the workspace
     size_t desc_offset; // byte offset of the row-marching kernel's descriptor block
     size_t total;       // workspace bytes
@@ -152,9 +158,8 @@ inline void uniform_types(const Bound &B, int bc[4]) {
 // One grid as the row-marching kernel sees it (device memory, 64-byte aligned).
 template <typename T>
 struct alignas(256) InstDesc {
-    CUtensorMap tmap;     // 3D view [40 planes][ny + 4 rows][pitch] of both state buffers
+    CUtensorMap tmap;     // 4D view [2 buffers][ny + 4 rows][5 groups][4 pitch] of both state buffers
     T *buf0, *buf1;
-    long long plane;
     int pitch, nx, ny;
     int bc[4];
     int nitems;           // this grid's work items in the launch
@@ -193,10 +198,10 @@ struct BatchCtl {
     unsigned int work, ctas_done;
 };
 
-// One work item of the row-marching kernel: rows [y0, y1) of strip `strip`
-// (output columns 120 strip .. 120 strip + 119) of grid `inst`.
+// One work item of the row-marching kernel: rows [y0, y1) of the strip of output
+// columns [x0, x0 + w) of grid `inst` (xw = x0 | w << 24; w <= kFusedOut).
 struct alignas(16) WorkItem {
-    int inst, strip, y0, y1;
+    int inst, xw, y0, y1;
 };
 
 template <typename T>
@@ -210,9 +215,8 @@ struct FusedBatchArgs {
 
 template <typename T>
 struct StepArgs {
-    T *buf0, *buf1;     // the two 20-plane state buffers
-    long long plane;    // plane stride (elements)
-    int pitch;
+    T *buf0, *buf1;     // the two state buffers
+    int pitch;          // cells per padded row of one group
     int nx, ny;
     int bc[4];          // west, east, south, north: the uniform type, -1 where a side switches
     int limiter;
@@ -250,10 +254,21 @@ template <typename T> const void *ghosts_kernel_fn();
 void simple_launch_shape(int nx, int ny, dim3 *grid, dim3 *block);
 void ghosts_launch_shape(int nx, int ny, dim3 *grid, dim3 *block);
 bool encode_state_tmap(CUtensorMap *out, void *base, const Layout &L);
-constexpr int kFusedOut = 120;                             // output columns per strip
-constexpr int kFusedBox = 128;                             // TMA box width (columns)
+constexpr int kFusedBox = 128;                             // TMA box width (columns) = threads per CTA
+constexpr int kFusedHalo = 2;                              // box columns on either side of a strip
+constexpr int kFusedOut = kFusedBox - 2 * kFusedHalo;      // most output columns of a strip (124)
 constexpr int kFusedMinChunk = 16;                         // rows per work item, bounds
 constexpr int kFusedMaxChunk = 128;
+
+// Strips of a grid of nx columns: as few as hold kFusedOut columns each, of even widths
+// as equal as possible (the last takes an odd remainder), so that every strip starts on
+// an even column (a 32-byte sector of FP32 groups) and no strip is nearly empty.
+inline int strip_count(int nx) { return (nx + kFusedOut - 1) / kFusedOut; }
+inline void strip_of(int nx, int s, int *x0, int *w) {
+    const int ns = strip_count(nx), pairs = nx / 2, base = pairs / ns, extra = pairs % ns;
+    *x0 = 2 * (s * base + (s < extra ? s : extra));
+    *w = s == ns - 1 ? nx - *x0 : 2 * (base + (s < extra ? 1 : 0));
+}
 
 // Work items of one grid appended to `out`, strip-fastest within each band of
 // rows. Uniform order: bands of `hmax` rows. Guided order (guided self-scheduling,
@@ -266,7 +281,7 @@ constexpr int kFusedMaxChunk = 128;
 // minimum heights of 8-32 rows were within 2.5 % of it.
 inline int append_items(WorkItem *out, int inst, int nx, int ny, int hmax, bool guided,
                         long long &work_left, long long ctas) {
-    const int strips = (nx + kFusedOut - 1) / kFusedOut;
+    const int strips = strip_count(nx);
     int n = 0;
     for (int y = 0; y < ny;) {
         long long h = hmax;
@@ -277,7 +292,9 @@ inline int append_items(WorkItem *out, int inst, int nx, int ny, int hmax, bool 
         }
         if (h > ny - y) h = ny - y;
         for (int s = 0; s < strips; ++s) {
-            if (out) out[n] = WorkItem{inst, s, y, y + (int)h};
+            int x0, w;
+            strip_of(nx, s, &x0, &w);
+            if (out) out[n] = WorkItem{inst, x0 | (w << 24), y, y + (int)h};
             ++n;
         }
         work_left -= (long long)strips * h;
@@ -287,7 +304,7 @@ inline int append_items(WorkItem *out, int inst, int nx, int ny, int hmax, bool 
 }
 // Upper bound of append_items' count for any order with hmax >= kFusedMinChunk.
 inline size_t max_items(int nx, int ny) {
-    const size_t strips = (nx + kFusedOut - 1) / kFusedOut;
+    const size_t strips = strip_count(nx);
     return strips * ((ny + kFusedMinChunk - 1) / kFusedMinChunk + 1);
 }
 template <typename T> cudaError_t launch_moments(const StepArgs<T> &a, T *rho, T *mom, T *E,
