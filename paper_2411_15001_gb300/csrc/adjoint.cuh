@@ -328,12 +328,17 @@ __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
     euler_fluxes(uN, k.gm1, fN, gN);
     T usE[4], dfE[4], usN[4], dfN[4], tbE = T(0), tbN = T(0);
     T dusE[4], ddfE[4], dusN[4], ddfN[4];   // DA: d u* / da, d dF / da of the two faces
+    T p1C[4], p2E[4], p3C[4], p4N[4];   // population groups, one vector load each
+    L.u4(4, i, j, p1C);
+    L.u4(8, i + 1, j, p2E);
+    L.u4(12, i, j, p3C);
+    L.u4(16, i, j + 1, p4N);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const T d1C = RN<T>::sub(maxwell_plus(uC[c], fC[c], k), L.v(4 + c, i, j));
-        const T d2E = RN<T>::sub(maxwell_minus(uE[c], fE[c], k), L.v(8 + c, i + 1, j));
-        const T d3C = RN<T>::sub(maxwell_plus(uC[c], gC[c], k), L.v(12 + c, i, j));
-        const T d4N = RN<T>::sub(maxwell_minus(uN[c], gN[c], k), L.v(16 + c, i, j + 1));
+        const T d1C = RN<T>::sub(maxwell_plus(uC[c], fC[c], k), p1C[c]);
+        const T d2E = RN<T>::sub(maxwell_minus(uE[c], fE[c], k), p2E[c]);
+        const T d3C = RN<T>::sub(maxwell_plus(uC[c], gC[c], k), p3C[c]);
+        const T d4N = RN<T>::sub(maxwell_minus(uN[c], gN[c], k), p4N[c]);
         if (DA) {
             dusE[c] = (fE[c] - fC[c]) * k.inv2k / k.a;
             ddfE[c] = (d1C - d2E) - (fC[c] + fE[c]) * k.inv2a;
@@ -441,16 +446,27 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
     euler_fluxes(uS, k.gm1, fS, gS);
     euler_fluxes(uN, k.gm1, fN, gN);
     T d1C[4], d2C[4], d3C[4], d4C[4], d1W[4], d2E[4], d3S[4], d4N[4];
+    {
+        T pg[8][4];   // population groups, one vector load each
+        L.u4(4, i, j, pg[0]);
+        L.u4(8, i, j, pg[1]);
+        L.u4(12, i, j, pg[2]);
+        L.u4(16, i, j, pg[3]);
+        L.u4(4, i - 1, j, pg[4]);
+        L.u4(8, i + 1, j, pg[5]);
+        L.u4(12, i, j - 1, pg[6]);
+        L.u4(16, i, j + 1, pg[7]);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        d1C[c] = RN<T>::sub(maxwell_plus(uC[c], fC[c], k), L.v(4 + c, i, j));
-        d2C[c] = RN<T>::sub(maxwell_minus(uC[c], fC[c], k), L.v(8 + c, i, j));
-        d3C[c] = RN<T>::sub(maxwell_plus(uC[c], gC[c], k), L.v(12 + c, i, j));
-        d4C[c] = RN<T>::sub(maxwell_minus(uC[c], gC[c], k), L.v(16 + c, i, j));
-        d1W[c] = RN<T>::sub(maxwell_plus(uW[c], fW[c], k), L.v(4 + c, i - 1, j));
-        d2E[c] = RN<T>::sub(maxwell_minus(uE[c], fE[c], k), L.v(8 + c, i + 1, j));
-        d3S[c] = RN<T>::sub(maxwell_plus(uS[c], gS[c], k), L.v(12 + c, i, j - 1));
-        d4N[c] = RN<T>::sub(maxwell_minus(uN[c], gN[c], k), L.v(16 + c, i, j + 1));
+        for (int c = 0; c < 4; ++c) {
+            d1C[c] = RN<T>::sub(maxwell_plus(uC[c], fC[c], k), pg[0][c]);
+            d2C[c] = RN<T>::sub(maxwell_minus(uC[c], fC[c], k), pg[1][c]);
+            d3C[c] = RN<T>::sub(maxwell_plus(uC[c], gC[c], k), pg[2][c]);
+            d4C[c] = RN<T>::sub(maxwell_minus(uC[c], gC[c], k), pg[3][c]);
+            d1W[c] = RN<T>::sub(maxwell_plus(uW[c], fW[c], k), pg[4][c]);
+            d2E[c] = RN<T>::sub(maxwell_minus(uE[c], fE[c], k), pg[5][c]);
+            d3S[c] = RN<T>::sub(maxwell_plus(uS[c], gS[c], k), pg[6][c]);
+            d4N[c] = RN<T>::sub(maxwell_minus(uN[c], gN[c], k), pg[7][c]);
+        }
     }
     T us[4][4], df[4][4];   // faces W, E, S, N
 #pragma unroll
@@ -734,9 +750,9 @@ __global__ void __launch_bounds__(256) k_adjoint_init(const T *init_state, int p
         const T w = kc->w, inv2a = kc->inv2a, gm1 = kc->gm1;
         const CellLoad<T> L{init_state, pitch};
         T u[4], wx[4], wy[4], rx[4], ry[4];
+        L.u4(0, i, j, u);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            u[q] = L.v(q, i, j);
             const T p1 = cot[(4 + q) * N + c], p2 = cot[(8 + q) * N + c];
             const T p3 = cot[(12 + q) * N + c], p4 = cot[(16 + q) * N + c];
             grad[q * N + c] = cot[q * N + c] + w * (p1 + p2 + p3 + p4);

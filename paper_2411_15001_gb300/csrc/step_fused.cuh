@@ -46,9 +46,8 @@ struct FusedSmem {
     T raw[kRawSlots][2][kNGroup][kFB / 2][4];   // [slot][half of the strip][group][column][component]
     T X[kXSlots][16][kFB];     // u (0..3), f (4..7), d_1 (8..11), d_2 (12..15)
     T rsx[2][kFB];             // rho* of x-face (b, b+1)
-    T thx[2][kFB];             // theta of x-face (b, b+1)
+    T thx[3][kFB];             // theta of x-face (b, b+1): PP by row R % 3, LMP / RLMP by (R - 1) & 1
     unsigned long long bar[kRawSlots];
-    unsigned long long rowbar;   // per-row split barrier (PP and the fixed thetas): one arrival per warp
     int item;
     int abort;
 };
@@ -148,18 +147,19 @@ struct FusedCtx {
     T *__restrict__ out;
     Monitor<T> &mon;
     int b, zin;
-    uint32_t &nissued, &nconsumed, &nrowbar;
+    uint32_t &nissued, &nconsumed;
     int xb, xpad, c, y0, y1, R1, wout;   // strip: box origin, padded origin, own column, rows, width
-    // Face states of the x-face (c+1/2) of row R-1 and of the y-face between rows R-2
-    // and R-1. PP and the fixed thetas carry them from the previous row; LMP / RLMP,
-    // whose density bounds keep more values live, recompute them where theta needs
-    // them (measured: 10 % faster for LMP / RLMP, no change for PP).
+    // PP and the fixed thetas form the faces of row R (x-face c+1/2, y-face R-1/2) in
+    // row R and limit them there: only two thetas of y-faces cross rows. LMP / RLMP
+    // need the density bounds of both cells of a face, complete one row later, so
+    // they limit the faces of row R-1 in row R, recomputing the face states there.
     static constexpr bool kRecompute = LIM == VLBM_LIM_LMP || LIM == VLBM_LIM_RLMP;
-    T xs_us[4], xs_df[4];   // x-face (c+1/2) of row R-1
-    T ys_us[4], ys_df[4];   // y-face between rows R-2 and R-1
-    T rsy_prev;             // rho* of that y-face
+    T xs_us[4], xs_df[4];   // LMP / RLMP: x-face (c+1/2) of row R-1
+    T ys_us[4], ys_df[4];   // LMP / RLMP: y-face between rows R-2 and R-1
+    T rsy_prev;             // rho* of the y-face between rows R-2 and R-1
     T mu2, nu2;             // bounds of row R-2 (own column)
-    T thy_prev;             // theta of the y-face between rows R-3 and R-2
+    T thy_prev;             // LMP / RLMP: theta of the y-face between rows R-3 and R-2
+    T ty1, ty2;             // PP: thetas of the y-faces (R-2, R-1) and (R-3, R-2)
     Hist<T> h1, h2;         // rows R-1, R-2 of the own column
     T p3n[4];               // u_3 of row R-2 after the step (pulled from row R-3)
 
@@ -186,7 +186,7 @@ struct FusedCtx {
             h1.d4[q] = h2.d4[q] = T(0);
             p3n[q] = T(0);
         }
-        rsy_prev = mu2 = nu2 = thy_prev = T(0);
+        rsy_prev = mu2 = nu2 = thy_prev = ty1 = ty2 = T(0);
     }
 
     // P1 of row R (see the file comment); returns rho* of the y-face R - 1/2. f and d1
@@ -227,18 +227,56 @@ struct FusedCtx {
         return face_star(h1.u[0], h1.g[0], u[0], g[0], k);  // y-face R - 1/2
     }
 
-    // Face states of the x-face (b, b+1) of row R and of the y-face R - 1/2 (PP and
-    // the fixed thetas), for theta in the next row.
-    __device__ __forceinline__ void next_faces(int R, const Hist<T> &h0, T rsy_new, int br, const T f[4],
-                                               const T d1[4]) {
+    // Face states of the x-face (b, b+1) of row R and of the y-face R - 1/2 (PP and the
+    // fixed thetas); the own column's u, x-flux and d_1 from registers, the right
+    // neighbour's from the shared ring.
+    __device__ __forceinline__ void row_faces(int R, const Hist<T> &h0, T rsy_new, int br, const T f[4],
+                                              const T d1[4], T xus[4], T xdf[4], T yus[4], T ydf[4]) const {
         const int xs = R & 3;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            xs_us[q] = face_star(h0.u[q], f[q], S.X[xs][q][br], S.X[xs][4 + q][br], k);
-            xs_df[q] = face_dflux(d1[q], S.X[xs][12 + q][br], k);
-            ys_us[q] = q == 0 ? rsy_new : face_star(h1.u[q], h1.g[q], h0.u[q], h0.g[q], k);
-            ys_df[q] = face_dflux(h1.d3[q], h0.d4[q], k);
+            xus[q] = face_star(h0.u[q], f[q], S.X[xs][q][br], S.X[xs][4 + q][br], k);
+            xdf[q] = face_dflux(d1[q], S.X[xs][12 + q][br], k);
+            yus[q] = q == 0 ? rsy_new : face_star(h1.u[q], h1.g[q], h0.u[q], h0.g[q], k);
+            ydf[q] = face_dflux(h1.d3[q], h0.d4[q], k);
         }
+    }
+
+    // PP and the fixed thetas: theta of the x-face (c, c+1) of row R and of the y-face
+    // (R - 1, R) of the own column, from their face states, with the sponge layer;
+    // stored / shifted into the slots P4 of the next rows reads.
+    __device__ __forceinline__ void row_thetas(int R, const T xus[4], const T xdf[4], const T yus[4],
+                                               const T ydf[4]) {
+        T tx, ty;
+        // theta is needed for the x-faces of columns kFHalo-1 .. kFHalo+wout-1 and the
+        // y-faces of the strip's own columns, inside the grid. The other threads hold
+        // halo padding or (past the last column) TMA fill, on which the FP32 screen
+        // would fail and send the face to the FP64 solve: they skip theta.
+        const bool live = b >= kFHalo - 1 && b < kFHalo + wout && c < D.nx;
+        if (LIM == VLBM_LIM_FIRST_ORDER) {
+            tx = ty = T(0);
+        } else if (LIM == VLBM_LIM_NONE) {
+            tx = ty = T(1);
+        } else if (!live) {
+            tx = ty = T(0);
+        } else {
+            unsigned int nx64 = 0, ny64 = 0;
+            tx = combine_theta(pp_density_target(xus[0], xdf[0], k), xus, xdf, k, nx64);
+            ty = combine_theta(pp_density_target(yus[0], ydf[0], k), yus, ydf, k, ny64);
+            // faces counted once: an x-face by the cell west of it, a y-face by the one south of it
+            const bool col_own = b >= kFHalo && b < kFHalo + wout && c < D.nx;
+            if (col_own && R >= y0 && R < y1) mon.fp64 += nx64;
+            if (col_own && R - 1 >= y0 && R - 1 < y1) mon.fp64 += ny64;
+        }
+        if (D.sponge > 0) {   // sponge layer (Sec. 4.2): theta = 0 on the faces of layer cells
+            const Sponge sp(D.sponge, D.nx, D.ny, D.bc);
+            const bool c0 = sp.cell(c, R);
+            if (c0 || sp.cell(c + 1, R)) tx = T(0);        // x-face (c, c+1) of row R
+            if (c0 || sp.cell(c, R - 1)) ty = T(0);        // y-face (R-1, R) of column c
+        }
+        S.thx[R % 3][b] = tx;
+        ty2 = ty1;
+        ty1 = ty;
     }
 
     // LMP density bounds (eq. LMP_minmax): min / max of rho of a cell and rho* of its
@@ -271,10 +309,9 @@ struct FusedCtx {
     }
 
     // The rows of an item before row y0 + 1: no output row of the item uses their
-    // thetas (x-faces below row y0, y-faces below y0 - 1/2) or their collide (rows
-    // below y0 - 1), so they only load the row and form what the next rows read --
-    // the face states (PP and the fixed thetas) or rho* of the x-faces and, in row
-    // y0, the bounds of row y0 - 1 (LMP / RLMP).
+    // collide (rows below y0 - 1), so they only load the row and form what the next
+    // rows read -- the thetas of their faces (PP and the fixed thetas) or rho* of the
+    // x-faces and, in row y0, the bounds of row y0 - 1 (LMP / RLMP).
     __device__ __forceinline__ bool row_warm(int R) {
         Hist<T> h0;
         T fo[4], d1o[4];
@@ -288,7 +325,9 @@ struct FusedCtx {
             const int xs = R & 3;
             S.rsx[R & 1][b] = face_star(h0.u[0], S.X[xs][4][b], S.X[xs][0][br], S.X[xs][4][br], k);
         } else {
-            next_faces(R, h0, rsy_new, br, fo, d1o);
+            T xus[4], xdf[4], yus[4], ydf[4];
+            row_faces(R, h0, rsy_new, br, fo, d1o, xus, xdf, yus, ydf);
+            row_thetas(R, xus, xdf, yus, ydf);
         }
         rsy_prev = rsy_new;
         h2 = h1;
@@ -296,9 +335,9 @@ struct FusedCtx {
         return true;
     }
 
-    // Theta of the x-face (c, c+1) of row R - 1 and of the y-face (R - 2, R - 1) of the
-    // own column (P3), with the sponge layer; (mu1, nu1) and (muR, nuR) are the density
-    // bounds of row R - 1 of the own column and of the one to the right (LMP / RLMP).
+    // LMP / RLMP: theta of the x-face (c, c+1) of row R - 1 and of the y-face (R - 2, R - 1)
+    // of the own column (P3), with the sponge layer; (mu1, nu1) and (muR, nuR) are the
+    // density bounds of row R - 1 of the own column and of the one to the right.
     __device__ __forceinline__ void thetas(int R, int br, T mu1, T nu1, T muR, T nuR, T &tx, T &ty) {
         // theta is needed for the x-faces of columns kFHalo-1 .. kFHalo+wout-1 and the
         // y-faces of the strip's own columns, inside the grid. The other threads hold
@@ -312,7 +351,7 @@ struct FusedCtx {
         } else if (!live) {
             tx = ty = T(0);
         } else {
-            if constexpr (kRecompute) {
+            {
                 const int xp = (R - 1) & 3;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -322,14 +361,8 @@ struct FusedCtx {
                     ys_df[q] = face_dflux(h2.d3[q], h1.d4[q], k);
                 }
             }
-            T trx, try_;
-            if (LIM == VLBM_LIM_PP) {
-                trx = pp_density_target(xs_us[0], xs_df[0], k);
-                try_ = pp_density_target(ys_us[0], ys_df[0], k);
-            } else {
-                trx = theta_rho_lmp(xs_us[0], xs_df[0], mu1, nu1, muR, nuR, k);
-                try_ = theta_rho_lmp(ys_us[0], ys_df[0], mu2, nu2, mu1, nu1, k);
-            }
+            const T trx = theta_rho_lmp(xs_us[0], xs_df[0], mu1, nu1, muR, nuR, k);
+            const T try_ = theta_rho_lmp(ys_us[0], ys_df[0], mu2, nu2, mu1, nu1, k);
             unsigned int nx64 = 0, ny64 = 0;
             tx = combine_theta(trx, xs_us, xs_df, k, nx64);
             ty = combine_theta(try_, ys_us, ys_df, k, ny64);
@@ -354,51 +387,46 @@ struct FusedCtx {
         const T rsy_new = p1(R, h0, fo, d1o);
         const int xs = R & 3;
         const int bl = b > 0 ? b - 1 : 0, br = b < kFB - 1 ? b + 1 : b;
-        T mu1 = T(0), nu1 = T(0), muR = T(0), nuR = T(0);
-        T tx, ty;
+        __syncthreads();                                                  // S1
+        if (S.abort) return false;
+        if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
+        T tw, te, ts, tn;   // thetas of the west, east, south and north faces of row R - 2
         if constexpr (kRecompute) {
-            __syncthreads();                                              // S1
-            if (S.abort) return false;
-            if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
             // -------------------------------------------------------- P2
+            T mu1, nu1, muR, nuR, tx, ty;
             bounds(R, rsy_new, bl, mu1, nu1);
             bounds_right(R, br, muR, nuR);
             // -------------------------------------------------------- P3
             thetas(R, br, mu1, nu1, muR, nuR, tx, ty);
-        } else {
-            // S1 split in two: this warp's ring writes are released by its arrival; the
-            // thetas of the previous row's faces read only registers, so they run before
-            // the wait for the other warps' arrivals (a warp that finished P1 early does
-            // useful work instead of stalling at a full barrier). The thetas are stored
-            // after the wait: their slot was read by neighbours in the previous row's P4.
-            __syncwarp();
-            if ((b & 31) == 0) mbar_arrive(&S.rowbar);
-            thetas(R, br, mu1, nu1, muR, nuR, tx, ty);
-            if (!mbar_wait_bounded(&S.rowbar, nrowbar & 1u)) S.abort = 1;
-            ++nrowbar;
-            if (S.abort) return false;
-            if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
-        }
-        S.thx[(R - 1) & 1][b] = tx;
-        mu2 = mu1;
-        nu2 = nu1;
-        if constexpr (kRecompute) {
+            S.thx[(R - 1) & 1][b] = tx;
+            mu2 = mu1;
+            nu2 = nu1;
             // rho* of the x-face (b, b+1) of row R, for the next row's density bounds
             S.rsx[R & 1][b] = face_star(h0.u[0], S.X[xs][4][b], S.X[xs][0][br], S.X[xs][4][br], k);
+            tw = S.thx[(R - 2) & 1][bl];
+            te = S.thx[(R - 2) & 1][b];
+            ts = thy_prev;
+            tn = ty;
+            thy_prev = ty;
         } else {
-            next_faces(R, h0, rsy_new, br, fo, d1o);
+            // -------------------------------------------------------- P3
+            tw = S.thx[(R - 2) % 3][bl];
+            te = S.thx[(R - 2) % 3][b];
+            ts = ty2;
+            tn = ty1;
+            T xus[4], xdf[4], yus[4], ydf[4];
+            row_faces(R, h0, rsy_new, br, fo, d1o, xus, xdf, yus, ydf);
+            row_thetas(R, xus, xdf, yus, ydf);
         }
         rsy_prev = rsy_new;
-        // No barrier before P4: it reads theta of row R-2's x-faces (written by the
-        // previous row's P3) and the ring rows of R-2, both ordered by this row's S1;
-        // every slot this row's P3 writes is read only after the next row's S1, and
-        // every slot the next row overwrites is read here before this thread reaches
-        // that S1.
+        // No barrier before P4: it reads theta of row R-2's x-faces (written two rows
+        // (PP) or one row (LMP / RLMP) ago) and the ring rows of R-2, ordered by this
+        // row's S1; every slot this row's P3 writes is read only after the next row's
+        // S1, and every slot the next row overwrites is read here before this thread
+        // reaches that S1 (PP: the theta slot R % 3 was last read by P4 of row R - 1).
         // ---------------------------------------------------------------- P4
         const int O = R - 2;
-        const int xo = O & 3, tp = O & 1;
-        const T tw = S.thx[tp][bl], te = S.thx[tp][b];
-        const T ts = thy_prev, tn = ty;
+        const int xo = O & 3;
         T nv[kNPlane];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -414,7 +442,6 @@ struct FusedCtx {
             // u_3 of row O + 1 after the step, pulled from row O with theta of y-face O + 1/2
             p3n[q] = blend_pop(maxwell_plus(h2.u[q], h2.g[q], k), h2.d3[q], tn);
         }
-        thy_prev = ty;
         if (O >= y0 && O < y1 && b >= kFHalo && b < kFHalo + wout && c < D.nx) {
             T *base = out + sidx(D.pitch, 0, c, O);
 #pragma unroll
@@ -459,12 +486,11 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
     }
     if (b == 0) {
         for (int s = 0; s < kRawSlots; ++s) mbar_init(&S.bar[s], 1);
-        mbar_init(&S.rowbar, kFB / 32);
         S.abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
-    uint32_t nissued = 0, nconsumed = 0, nrowbar = 0;
+    uint32_t nissued = 0, nconsumed = 0;
     bool ok = true;
     if constexpr (PROBE) {
         const unsigned int probe = B.insts[0].ctl->wait_probe_ns;
@@ -493,7 +519,7 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         Monitor<T> mon;
         mon.init();
         FusedCtx<T, LIM> X{S, &D.tmap, geo, k, (n & 1) ? D.buf0 : D.buf1, mon, b, (n & 1) ? 1 : 0,
-                           nissued, nconsumed, nrowbar};
+                           nissued, nconsumed};
         X.y0 = it.y0;
         X.y1 = it.y1;
         X.wout = (int)((unsigned)it.xw >> 24);

@@ -24,12 +24,6 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t
                  : "memory");
 }
 
-// Arrive on an mbarrier (release at CTA scope: this thread's earlier shared-memory
-// writes are visible to the threads that see the phase complete).
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
