@@ -115,16 +115,17 @@ struct ARed {
     unsigned int idx;
 };
 
-// dL/da^n accumulated in the slots goes to the conserved planes of cot at the
-// cell where lambda(st) is largest; the slots are reset for the next step.
+// dL/da^n accumulated in the slots goes to the conserved values of cot (a grouped
+// cotangent of the sweep, or the caller's four planes) at the cell where lambda(st)
+// is largest; the slots are reset for the next step.
 template <typename T>
 static cudaError_t hand_over_abar(const T *st, const Layout &L, double gamma, double alpha, ARed *red, T *cot,
-                                  const double *lam_bc, cudaStream_t s) {
+                                  bool grouped, const double *lam_bc, cudaStream_t s) {
     const dim3 blk(32, 8), grd((L.nx + 31) / 32, (L.ny + 7) / 8);
     k_lambda_max<T><<<grd, blk, 0, s>>>(st, L.pitch, L.nx, L.ny, (T)gamma, &red->key);
     k_lambda_argmax<T><<<grd, blk, 0, s>>>(st, L.pitch, L.nx, L.ny, (T)gamma, &red->key, &red->idx);
     k_lambda_apply<T><<<1, 1, 0, s>>>(st, L.pitch, L.nx, gamma, alpha, &red->abar, &red->key, &red->idx, cot,
-                                      (long long)L.nx * L.ny, lam_bc);
+                                      (long long)L.nx * L.ny, grouped ? 1 : 0, lam_bc);
     return cudaGetLastError();
 }
 
@@ -152,7 +153,7 @@ struct Plan {
     size_t segctl_off;    // control block of the recomputation
     size_t desc_off;      // 2 k InstDesc of the row-marching kernel (by parity of n)
     size_t khist_off;     // the step constants (a^n) and the time t^n of each step of a segment
-    size_t cot_off;       // two cotangent buffers of 20 compact planes
+    size_t cot_off;       // two cotangent buffers of nx x ny cells (grouped, kidx)
     size_t cot_bytes;
     size_t red_off;       // the dL/da hand-over slots
     size_t pad_off;       // a cotangent padded by the ghost layers the adjoint covers (grids with a boundary)
@@ -290,15 +291,17 @@ template <typename T>
 int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const Plan &p, const void *dLduN,
             void *dLdu0) {
     const size_t buf = s->L.buf_bytes;
-    const long long N = (long long)s->grid.nx * s->grid.ny;
     const bool fixed_a = s->a_fixed > 0.0;
     const bool diff_a = !fixed_a && s->adj_mode == VLBM_ADJOINT_DIFF_A;
     ARed *red = (ARed *)(scratch + p.red_off);
     T *cot[2] = {(T *)(scratch + p.cot_off), (T *)(scratch + p.cot_off + p.cot_bytes)};
     DevCtl *segctl = (DevCtl *)(scratch + p.segctl_off);
     char *khist = scratch + p.khist_off;
-    cudaError_t e = cudaMemcpyAsync(cot[0], dLduN, (size_t)4 * N * sizeof(T), cudaMemcpyDeviceToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cot[0] + 4 * N, 0, (size_t)(kNPlane - 4) * N * sizeof(T), s->stream);
+    {
+        const dim3 blk(32, 8), grd((s->grid.nx + 31) / 32, (s->grid.ny + 7) / 8);
+        k_adjoint_seed<T><<<grd, blk, 0, s->stream>>>((const T *)dLduN, s->grid.nx, s->grid.ny, cot[0]);
+    }
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && diff_a) {
         e = cudaMemsetAsync(red, 0, sizeof(ARed), s->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(&red->idx, 0xff, sizeof(unsigned int), s->stream);
@@ -355,7 +358,8 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
             if (e != cudaSuccess) return cuda_fail(s, e, "adjoint step launch");
             cur ^= 1;
             if (diff_a && m > 0) {   // a^m came from lambda of s^m (a^0 waits for the init map)
-                e = hand_over_abar<T>(A.fwd, s->L, s->gamma, s->alpha, red, cot[cur], &segctl->lam_bc, s->stream);
+                e = hand_over_abar<T>(A.fwd, s->L, s->gamma, s->alpha, red, cot[cur], true, &segctl->lam_bc,
+                                      s->stream);
                 if (e != cudaSuccess) return cuda_fail(s, e, "kinetic-speed cotangent launch");
             }
         }
@@ -364,7 +368,8 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     e = launch_adjoint_init<T>((const T *)ck0, s->L, ctl_consts<T>((const DevCtl *)(ck0 + round256(buf))), cot[cur],
                                (T *)dLdu0, diff_a ? &red->abar : nullptr, s->stream);
     if (e == cudaSuccess && diff_a)
-        e = hand_over_abar<T>((const T *)ck0, s->L, s->gamma, s->alpha, red, (T *)dLdu0, &segctl->lam_bc, s->stream);
+        e = hand_over_abar<T>((const T *)ck0, s->L, s->gamma, s->alpha, red, (T *)dLdu0, false, &segctl->lam_bc,
+                              s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "initialisation adjoint launch");
     return VLBM_OK;
 }

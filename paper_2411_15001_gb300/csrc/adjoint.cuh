@@ -36,8 +36,8 @@ template <typename T>
 struct AdjArgs {
     const T *fwd;          // forward state s^n (padded, ghost frame filled)
     int pitch, nx, ny;
-    const T *cot_in;       // cotangent of s^{n+1}: 20 compact planes
-    T *cot_out;            // cotangent of s^n: 20 compact planes
+    const T *cot_in;       // cotangent of s^{n+1}: nx x ny cells (kidx layout below)
+    T *cot_out;            // cotangent of s^n: nx x ny cells, or padded (ext)
     const StepConsts<T> *k;  // constants of the step (kinetic speed a^n as the forward run used it)
     double *abar;          // DA: accumulates dL/da^n
     int ext;               // 1: grid with a boundary (cot_out padded by `pad` cells, see above)
@@ -50,6 +50,14 @@ struct AdjArgs {
     int bc[4];             // uniform side types (-1 where a side switches), for the sponge
     int sponge;            // theta = 0 layer of the forward step (Sec. 4.2)
 };
+
+// Cotangent buffers hold, like the state, rows of five 4-value groups: value q of
+// cell (x, y) of a buffer w cells wide at ((y * 5 + q / 4) * w + x) * 4 + q % 4 (x, y
+// from 0; a padded buffer counts its ghost layers in). A cell's group is one 16-byte
+// (FP32) or 32-byte (FP64) access, and a warp's cells of one group are contiguous.
+__host__ __device__ __forceinline__ long long kidx(int w, int q, long long x, long long y) {
+    return ((y * kNGroup + (q >> 2)) * w + x) * 4 + (q & 3);
+}
 
 // w^T df/du for the Euler x-flux (dir 0) or y-flux (dir 1) at state u.
 template <typename T>
@@ -310,15 +318,18 @@ __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
     if (i >= A.nx || j >= A.ny) return;
     const StepConsts<T> k = *A.k;
     const CellLoad<T> L{A.fwd, A.pitch};
-    const long long N = (long long)A.nx * A.ny, NL = lmp_cells(A);
-    auto out_cell = [&](int x, int y) -> long long {   // cotangent index of cell (x, y)'s outputs
-        if (EXT) return ((unsigned)x >= (unsigned)A.nx || (unsigned)y >= (unsigned)A.ny) ? -1 : (long long)y * A.nx + x;
-        return lmp_ix(A, x, y);
-    };
-    const long long cC = out_cell(i, j), cE = out_cell(i + 1, j), cN = out_cell(i, j + 1);
+    const long long NL = lmp_cells(A);
     const long long lC = lmp_ix(A, i, j), lE = lmp_ix(A, i + 1, j), lN = lmp_ix(A, i, j + 1);
     T *P = A.lmp;
-    auto cot = [&](int q, long long c) -> T { return c < 0 ? T(0) : A.cot_in[q * N + c]; };
+    auto cot = [&](int q, int x, int y) -> T {   // output cotangent q of cell (x, y)
+        if (EXT) {
+            if ((unsigned)x >= (unsigned)A.nx || (unsigned)y >= (unsigned)A.ny) return T(0);
+        } else {
+            x = x < 0 ? x + A.nx : (x >= A.nx ? x - A.nx : x);
+            y = y < 0 ? y + A.ny : (y >= A.ny ? y - A.ny : y);
+        }
+        return A.cot_in[kidx(A.nx, q, x, y)];
+    };
     T uC[4], uE[4], uN[4], fC[4], gC[4], fE[4], gE[4], fN[4], gN[4];
     L.u4(0, i, j, uC);
     L.u4(0, i + 1, j, uE);
@@ -350,9 +361,9 @@ __global__ void __launch_bounds__(256) k_adj_lmp_faces(AdjArgs<T> A) {
         usN[c] = face_star(uC[c], gC[c], uN[c], gN[c], k);
         dfN[c] = face_dflux(d3C, d4N, k);
         // cotangent of theta: the pulled populations theta d and the local -theta d of u'
-        const T ubC = cot(c, cC), ubE = cot(c, cE), ubN = cot(c, cN);
-        tbE += d1C * (cot(4 + c, cE) + ubE - ubC) + d2E * (cot(8 + c, cC) + ubC - ubE);
-        tbN += d3C * (cot(12 + c, cN) + ubN - ubC) + d4N * (cot(16 + c, cC) + ubC - ubN);
+        const T ubC = cot(c, i, j), ubE = cot(c, i + 1, j), ubN = cot(c, i, j + 1);
+        tbE += d1C * (cot(4 + c, i + 1, j) + ubE - ubC) + d2E * (cot(8 + c, i, j) + ubC - ubE);
+        tbN += d3C * (cot(12 + c, i, j + 1) + ubN - ubC) + d4N * (cot(16 + c, i, j) + ubC - ubN);
     }
     T muC, nuC, muE, nuE, muN, nuN;
     int aC, bC, aE, bE, aN, bN;
@@ -431,7 +442,6 @@ template <typename T, int LIM, bool DA, bool EXT>
 __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j) {
     const StepConsts<T> k = *A.k;
     CellLoad<T> L{A.fwd, A.pitch};
-    const long long N = (long long)A.nx * A.ny;
     // ---------------------------------------------------------- forward quantities
     T uC[4], uW[4], uE[4], uS[4], uN[4];
     L.u4(0, i, j, uC);
@@ -504,31 +514,23 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
             }
     }
     // ---------------------------------------------------------- cotangents
-    // of the outputs of cell (x, y): wrapped on a periodic grid, 0 outside the
-    // interior on a grid with a boundary
-    long long cC, cW, cE, cS, cN;
-    if constexpr (EXT) {
-        auto cell_of = [&](int x, int y) -> long long {
-            if ((unsigned)x >= (unsigned)A.nx || (unsigned)y >= (unsigned)A.ny) return -1;
-            return (long long)y * A.nx + x;
-        };
-        cC = cell_of(i, j);
-        cW = cell_of(i - 1, j);
-        cE = cell_of(i + 1, j);
-        cS = cell_of(i, j - 1);
-        cN = cell_of(i, j + 1);
-    } else {
-        const int iw = i > 0 ? i - 1 : A.nx - 1, ie = i < A.nx - 1 ? i + 1 : 0;
-        const int js = j > 0 ? j - 1 : A.ny - 1, jn = j < A.ny - 1 ? j + 1 : 0;
-        cC = (long long)j * A.nx + i;
-        cW = (long long)j * A.nx + iw;
-        cE = (long long)j * A.nx + ie;
-        cS = (long long)js * A.nx + i;
-        cN = (long long)jn * A.nx + i;
+    // of the outputs of cell (x, y), a group of four at a time: wrapped on a periodic
+    // grid, 0 outside the interior on a grid with a boundary
+    int xW = i - 1, xE = i + 1, yS = j - 1, yN = j + 1;
+    if constexpr (!EXT) {
+        xW = i > 0 ? xW : A.nx - 1;
+        xE = i < A.nx - 1 ? xE : 0;
+        yS = j > 0 ? yS : A.ny - 1;
+        yN = j < A.ny - 1 ? yN : 0;
     }
-    auto cot = [&](int q, long long c) -> T {
-        if constexpr (EXT) return c < 0 ? T(0) : A.cot_in[q * N + c];
-        else return A.cot_in[q * N + c];
+    auto grp = [&](int g, int x, int y, T v[4]) {
+        if constexpr (EXT) {
+            if ((unsigned)x >= (unsigned)A.nx || (unsigned)y >= (unsigned)A.ny) {
+                v[0] = v[1] = v[2] = v[3] = T(0);
+                return;
+            }
+        }
+        ld_group(A.cot_in + kidx(A.nx, 4 * g, x, y), v);
     };
     long long lC = 0, lW = 0, lS = 0, NL = 0;   // the cell and its west / south neighbours in the LMP planes
     if constexpr (kLmp) {   // theta of the four faces as pass 1 found it
@@ -542,23 +544,32 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
         th[3] = A.lmp[kLthN * NL + lC];
     }
     T ubC[4], ubW[4], ubE[4], ubS[4], ubN[4];
+    T qC[4][4], q1E[4], q2W[4], q3N[4], q4S[4];   // population cotangents as stored
+    grp(0, i, j, ubC);
+    grp(0, xW, j, ubW);
+    grp(0, xE, j, ubE);
+    grp(0, i, yS, ubS);
+    grp(0, i, yN, ubN);
+    grp(1, i, j, qC[0]);
+    grp(2, i, j, qC[1]);
+    grp(3, i, j, qC[2]);
+    grp(4, i, j, qC[3]);
+    grp(1, xE, j, q1E);
+    grp(2, xW, j, q2W);
+    grp(3, i, yN, q3N);
+    grp(4, i, yS, q4S);
     T P1C[4], P2C[4], P3C[4], P4C[4], P1E[4], P2W[4], P3N[4], P4S[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        ubC[c] = cot(c, cC);
-        ubW[c] = cot(c, cW);
-        ubE[c] = cot(c, cE);
-        ubS[c] = cot(c, cS);
-        ubN[c] = cot(c, cN);
         // streamed populations carry the cotangent of u' as well (u' sums them)
-        P1C[c] = cot(4 + c, cC) + ubC[c];
-        P2C[c] = cot(8 + c, cC) + ubC[c];
-        P3C[c] = cot(12 + c, cC) + ubC[c];
-        P4C[c] = cot(16 + c, cC) + ubC[c];
-        P1E[c] = cot(4 + c, cE) + ubE[c];
-        P2W[c] = cot(8 + c, cW) + ubW[c];
-        P3N[c] = cot(12 + c, cN) + ubN[c];
-        P4S[c] = cot(16 + c, cS) + ubS[c];
+        P1C[c] = qC[0][c] + ubC[c];
+        P2C[c] = qC[1][c] + ubC[c];
+        P3C[c] = qC[2][c] + ubC[c];
+        P4C[c] = qC[3][c] + ubC[c];
+        P1E[c] = q1E[c] + ubE[c];
+        P2W[c] = q2W[c] + ubW[c];
+        P3N[c] = q3N[c] + ubN[c];
+        P4S[c] = q4S[c] + ubS[c];
     }
     // theta cotangents of the four faces
     T tb[4] = {T(0), T(0), T(0), T(0)};
@@ -613,14 +624,12 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
 #pragma unroll
     for (int c = 0; c < 4; ++c) out[c] += rx[c] + ry[c];
     if constexpr (kLmp) out[0] += A.lmp[kLrb * NL + lC];   // the density where a cell's bound was taken
-    if constexpr (EXT) {
-        const int w = A.nx + 2 * A.pad;
-        const long long Np = (long long)w * (A.ny + 2 * A.pad), cp = (long long)(j + A.pad) * w + (i + A.pad);
+    {
+        const int w = EXT ? A.nx + 2 * A.pad : A.nx, o = EXT ? A.pad : 0;
 #pragma unroll
-        for (int q = 0; q < kNPlane; ++q) A.cot_out[q * Np + cp] = out[q];
-    } else {
-#pragma unroll
-        for (int q = 0; q < kNPlane; ++q) A.cot_out[q * N + cC] = out[q];
+        for (int g = 0; g < kNGroup; ++g)
+            st_group(A.cot_out + kidx(w, 4 * g, i + o, j + o), out[4 * g], out[4 * g + 1], out[4 * g + 2],
+                     out[4 * g + 3]);
     }
     if constexpr (!DA) {
         return 0.0;
@@ -655,8 +664,7 @@ __device__ __forceinline__ double adjoint_cell(const AdjArgs<T> &A, int i, int j
             const T du4 = (T(1) + th[3]) * gN[c] * h + d4N[c] * dth[3];
             const T loc = dth[0] * d2C[c] + th[0] * fC[c] * h + dth[1] * d1C[c] - th[1] * fC[c] * h +
                           dth[2] * d4C[c] + th[2] * gC[c] * h + dth[3] * d3C[c] - th[3] * gC[c] * h;
-            ab += (double)(cot(4 + c, cC) * du1 + cot(8 + c, cC) * du2 + cot(12 + c, cC) * du3 +
-                           cot(16 + c, cC) * du4) +
+            ab += (double)(qC[0][c] * du1 + qC[1][c] * du2 + qC[2][c] * du3 + qC[3][c] * du4) +
                   (double)(ubC[c] * (du1 + du2 + du3 + du4 - loc));
         }
         return ab;
@@ -711,9 +719,9 @@ __global__ void __launch_bounds__(256) k_adj_lmp_ring(AdjArgs<T> A) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) out[c] += rx[c] + ry[c];
     }
-    const long long Np = (long long)w * (A.ny + 4), cp = (long long)(j + 2) * w + (i + 2);
 #pragma unroll
-    for (int q = 0; q < kNPlane; ++q) A.cot_out[q * Np + cp] = out[q];
+    for (int g = 0; g < kNGroup; ++g)
+        st_group(A.cot_out + kidx(w, 4 * g, i + 2, j + 2), out[4 * g], out[4 * g + 1], out[4 * g + 2], out[4 * g + 3]);
 }
 
 // Sum of v over the CTA's warps into *dst (every thread of the CTA calls it).
@@ -749,30 +757,27 @@ __global__ void __launch_bounds__(256) k_adjoint_init(const T *init_state, int p
         const long long N = (long long)nx * ny, c = (long long)j * nx + i;
         const T w = kc->w, inv2a = kc->inv2a, gm1 = kc->gm1;
         const CellLoad<T> L{init_state, pitch};
-        T u[4], wx[4], wy[4], rx[4], ry[4];
+        T u[4], wx[4], wy[4], rx[4], ry[4], ub[4], p[4][4], gr[4];
         L.u4(0, i, j, u);
+        ld_group(cot + kidx(nx, 0, i, j), ub);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) ld_group(cot + kidx(nx, 4 + 4 * g, i, j), p[g]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const T p1 = cot[(4 + q) * N + c], p2 = cot[(8 + q) * N + c];
-            const T p3 = cot[(12 + q) * N + c], p4 = cot[(16 + q) * N + c];
-            grad[q * N + c] = cot[q * N + c] + w * (p1 + p2 + p3 + p4);
-            wx[q] = (p1 - p2) * inv2a;
-            wy[q] = (p3 - p4) * inv2a;
+            gr[q] = ub[q] + w * (p[0][q] + p[1][q] + p[2][q] + p[3][q]);
+            wx[q] = (p[0][q] - p[1][q]) * inv2a;
+            wy[q] = (p[2][q] - p[3][q]) * inv2a;
         }
         flux_vjp(u, gm1, 0, wx, rx);
         flux_vjp(u, gm1, 1, wy, ry);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) grad[q * N + c] += rx[q] + ry[q];
+        for (int q = 0; q < 4; ++q) grad[q * N + c] = gr[q] + (rx[q] + ry[q]);
         if (abar) {   // dM_{1,3}/da = -F/(2a^2), dM_{2,4}/da = +F/(2a^2), F = f or g
             T f[4], g[4];
             euler_fluxes(u, gm1, f, g);
             const T h = inv2a / kc->a;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const T p1 = cot[(4 + q) * N + c], p2 = cot[(8 + q) * N + c];
-                const T p3 = cot[(12 + q) * N + c], p4 = cot[(16 + q) * N + c];
-                ab -= (double)(((p1 - p2) * f[q] + (p3 - p4) * g[q]) * h);
-            }
+            for (int q = 0; q < 4; ++q) ab -= (double)(((p[0][q] - p[1][q]) * f[q] + (p[2][q] - p[3][q]) * g[q]) * h);
         }
     }
     if (abar) warp_sum_atomic(ab, abar);
@@ -817,13 +822,14 @@ __global__ void __launch_bounds__(256) k_lambda_argmax(const T *st, int pitch, i
 }
 
 // One thread: cot[q][idx] += abar * 2 / (1 - alpha) * d lambda / d u_q at the argmax
-// cell (lambda = |v| + sqrt(gamma p / rho)); then the slots are reset.
+// cell (lambda = |v| + sqrt(gamma p / rho)); then the slots are reset. cot is a
+// cotangent buffer of the sweep (grouped, kidx) or the caller's four planes (N cells each).
 // When the prescribed boundary states' speed lam_bc exceeds every cell's (the step
 // compares them the same way), lambda^n does not depend on the state: nothing is added.
 template <typename T>
 __global__ void k_lambda_apply(const T *st, int pitch, int nx, double gamma, double alpha,
                                double *abar, unsigned long long *key, unsigned int *idx, T *cot, long long N,
-                               const double *lam_bc) {
+                               int grouped, const double *lam_bc) {
     const unsigned int id = *idx;
     const double ab = *abar;
     const bool bc_wins = *lam_bc > key_to_double(*key);
@@ -848,7 +854,7 @@ __global__ void k_lambda_apply(const T *st, int pitch, int nx, double gamma, dou
     for (int q = 1; q < 4; ++q) g[q] += kc * dp[q];
     const double s = ab * 2.0 / (1.0 - alpha);
     const long long cc = (long long)j * nx + i;
-    for (int q = 0; q < 4; ++q) cot[q * N + cc] += (T)(s * g[q]);
+    for (int q = 0; q < 4; ++q) cot[grouped ? kidx(nx, q, i, j) : q * N + cc] += (T)(s * g[q]);
 }
 
 }  // namespace vlbm
@@ -862,17 +868,15 @@ namespace vlbm {
 // takes every ghost of a column (y) or row (x) in turn: ghosts that share a source
 // (the layers of a zero-gradient side) never add to it at the same time.
 template <typename T>
-__device__ __forceinline__ void fold_one(T *cot, long long Np, int w, int pad, int gi, int gj, int si, int sj, bool mx,
-                                         bool my) {
-    const long long g = (long long)(gj + pad) * w + (gi + pad), d = (long long)(sj + pad) * w + (si + pad);
+__device__ __forceinline__ void fold_one(T *cot, int w, int pad, int gi, int gj, int si, int sj, bool mx, bool my) {
 #pragma unroll
     for (int q = 0; q < kNPlane; ++q) {
         int src = q;   // the mirror map is a symmetric permutation with signs: its own transpose
         if (mx && q >= 4 && q < 12) src = q < 8 ? q + 4 : q - 4;
         if (my && q >= 12) src = q < 16 ? q + 4 : q - 4;
-        T v = cot[src * Np + g];
+        T v = cot[kidx(w, src, gi + pad, gj + pad)];
         if ((mx && (q & 3) == 1) || (my && (q & 3) == 2)) v = -v;
-        cot[q * Np + d] += v;
+        cot[kidx(w, q, si + pad, sj + pad)] += v;
     }
 }
 
@@ -880,17 +884,17 @@ __device__ __forceinline__ void fold_one(T *cot, long long Np, int w, int pad, i
 // field at the cell's centre at t^n (piecewise constant in t: no time derivative
 // almost everywhere); dM_{1,3}/da = -F/(2a^2), dM_{2,4}/da = +F/(2a^2).
 template <typename T>
-__device__ __forceinline__ double prescribed_abar(const T *cot, long long Np, long long g, const Bound &bd, int gi,
-                                                  int gj, double t, const StepConsts<T> &k) {
+__device__ __forceinline__ double prescribed_abar(const T *cot, int w, int pad, const Bound &bd, int gi, int gj,
+                                                  double t, const StepConsts<T> &k) {
     T u[4], f[4], gf[4];
     field_state(bd, gi, gj, t, u);
     euler_fluxes(u, k.gm1, f, gf);
     const T h = k.inv2a / k.a;
+    auto at = [&](int q) { return cot[kidx(w, q, gi + pad, gj + pad)]; };
     double ab = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
-        ab += (double)(((cot[(8 + c) * Np + g] - cot[(4 + c) * Np + g]) * f[c] +
-                        (cot[(16 + c) * Np + g] - cot[(12 + c) * Np + g]) * gf[c]) * h);
+        ab += (double)(((at(8 + c) - at(4 + c)) * f[c] + (at(16 + c) - at(12 + c)) * gf[c]) * h);
     return ab;
 }
 
@@ -901,19 +905,18 @@ __global__ void k_adjoint_fold_y(T *cot, int nx, int ny, int pad, Bound bd, int 
     const int w = nx + 2 * pad;
     if (tid >= w) return;
     const int gi = tid - pad;
-    const long long Np = (long long)w * (ny + 2 * pad);
     double ab = 0.0;
     for (int l = 0; l < 2 * pad; ++l) {
         const int gj = l < pad ? -1 - l : ny + (l - pad);
         const int s = gj < 0 ? 2 : 3;
         const int type = (s == 2 ? bc2 : bc3) >= 0 ? (s == 2 ? bc2 : bc3) : side_type(bd, s, gi);
         if (type == VLBM_BC_DIRICHLET) {
-            if (abar) ab += prescribed_abar(cot, Np, (long long)(gj + pad) * w + (gi + pad), bd, gi, gj, *t, *k);
+            if (abar) ab += prescribed_abar(cot, w, pad, bd, gi, gj, *t, *k);
             continue;
         }
         bool my;
         const int sj = ghost_source_typed(gj, ny, type, &my);
-        fold_one(cot, Np, w, pad, gi, gj, gi, sj, false, my);
+        fold_one(cot, w, pad, gi, gj, gi, sj, false, my);
     }
     if (abar && ab != 0.0) atomicAdd(abar, ab);
 }
@@ -924,33 +927,46 @@ __global__ void k_adjoint_fold_x(T *cot, int nx, int ny, int pad, Bound bd, int 
     const int gj = blockIdx.x * blockDim.x + threadIdx.x;   // one thread per interior row
     if (gj >= ny) return;
     const int w = nx + 2 * pad;
-    const long long Np = (long long)w * (ny + 2 * pad);
     double ab = 0.0;
     for (int l = 0; l < 2 * pad; ++l) {
         const int gi = l < pad ? -1 - l : nx + (l - pad);
         const int s = gi < 0 ? 0 : 1;
         const int type = (s == 0 ? bc0 : bc1) >= 0 ? (s == 0 ? bc0 : bc1) : side_type(bd, s, gj);
         if (type == VLBM_BC_DIRICHLET) {   // (the corners the y fold moved here included)
-            if (abar) ab += prescribed_abar(cot, Np, (long long)(gj + pad) * w + (gi + pad), bd, gi, gj, *t, *k);
+            if (abar) ab += prescribed_abar(cot, w, pad, bd, gi, gj, *t, *k);
             continue;
         }
         bool mx;
         const int si = ghost_source_typed(gi, nx, type, &mx);
-        fold_one(cot, Np, w, pad, gi, gj, si, gj, mx, false);
+        fold_one(cot, w, pad, gi, gj, si, gj, mx, false);
     }
     if (abar && ab != 0.0) atomicAdd(abar, ab);
 }
 
-// Interior of a padded cotangent into compact planes.
+// Interior of a padded cotangent into an unpadded one.
 template <typename T>
 __global__ void k_adjoint_unpad(const T *cot_pad, int nx, int ny, int pad, T *cot) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= nx || j >= ny) return;
     const int w = nx + 2 * pad;
-    const long long Np = (long long)w * (ny + 2 * pad), N = (long long)nx * ny;
 #pragma unroll
-    for (int q = 0; q < kNPlane; ++q)
-        cot[q * N + (long long)j * nx + i] = cot_pad[q * Np + (long long)(j + pad) * w + i + pad];
+    for (int g = 0; g < kNGroup; ++g) {
+        T v[4];
+        ld_group(cot_pad + kidx(w, 4 * g, i + pad, j + pad), v);
+        st_group(cot + kidx(nx, 4 * g, i, j), v[0], v[1], v[2], v[3]);
+    }
+}
+
+// The sweep's first cotangent: dL/du^N (the caller's four planes) in group 0 of every
+// cell, zero population cotangents.
+template <typename T>
+__global__ void k_adjoint_seed(const T *dLduN, int nx, int ny, T *cot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    const long long N = (long long)nx * ny, c = (long long)j * nx + i;
+    st_group(cot + kidx(nx, 0, i, j), dLduN[c], dLduN[N + c], dLduN[2 * N + c], dLduN[3 * N + c]);
+#pragma unroll
+    for (int g = 1; g < kNGroup; ++g) st_group(cot + kidx(nx, 4 * g, i, j), T(0), T(0), T(0), T(0));
 }
 
 }  // namespace vlbm
