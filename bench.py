@@ -557,7 +557,7 @@ def bench_adjoint(dev, n: int = 512, steps: int = 500, every: int = 50):
     finite = bool(torch.isfinite(g).all())
     s.close()
     return {"workload": f"{n}x{n} periodic isentropic vortex + 8 Gaussian density bumps (seed 2), FP32, "
-                        f"PP, fixed a = 4 (1.05 lambda_0), {steps} steps, checkpoints every {every}, "
+                        f"PP, fixed a = 4 x 1.05 lambda_0 (about 14), {steps} steps, checkpoints every {every}, "
                         "L = dx^2/2 sum |u^N - u_target|^2, u_target = the unperturbed vortex after the "
                         "same steps",
             "forward_ms_per_step": t_f, "rollout_ms_per_step": t_r, "adjoint_ms_per_step": t_a,

@@ -82,15 +82,10 @@ static cudaError_t step_kernel_only(vlbm_state *s) {
     return launch_step_simple<float>(args_of<float>(s), s->stream);
 }
 
-static cudaError_t ghosts(vlbm_state *s) {
-    if (s->precision == VLBM_FP64) return launch_ghosts<double>(args_of<double>(s), s->stream);
-    return launch_ghosts<float>(args_of<float>(s), s->stream);
-}
-
-// Before a row-marching step of a grid with a prescribed part: its ghosts at the
-// step's t^n and a^n (the kernel writes every other ghost itself).
+// Before a step of a grid with a prescribed part: its ghosts at the step's t^n and
+// a^n (the step kernels write every other ghost of the new state themselves).
 static cudaError_t dirichlet_pass(vlbm_state *s) {
-    if (!use_fused(s) || !s->bd.has_dir) return cudaSuccess;
+    if (!s->bd.has_dir) return cudaSuccess;
     if (s->precision == VLBM_FP64) return launch_dirichlet_ghosts<double>(args_of<double>(s), s->stream);
     return launch_dirichlet_ghosts<float>(args_of<float>(s), s->stream);
 }
@@ -129,8 +124,9 @@ static cudaError_t upload_desc(vlbm_state *s) {
     return e;
 }
 
-// One time step: the collide + limit + stream kernel, then the ghost frame of
-// the new state. With profiling on, an event pair brackets the step kernel.
+// One time step: the prescribed ghosts of the state it reads (if any), then the
+// collide + limit + stream kernel, which also writes the new state's ghost frame.
+// With profiling on, an event pair brackets the step kernel.
 cudaError_t vlbm::api::step_once(vlbm_state *s) {
     cudaError_t r;
     if (s->profiling) {
@@ -151,8 +147,7 @@ cudaError_t vlbm::api::step_once(vlbm_state *s) {
         r = dirichlet_pass(s);
         if (r == cudaSuccess) r = step_kernel_only(s);
     }
-    if (r != cudaSuccess) return r;
-    return use_fused(s) ? cudaSuccess : ghosts(s);   // the fused kernel writes the ghost frame
+    return r;
 }
 
 namespace vlbm {
@@ -209,7 +204,7 @@ static cudaError_t build_graph(vlbm_state *s) {
     void *pa[] = {&A};
     cudaKernelNodeParams kg;
     memset(&kg, 0, sizeof kg);
-    const bool dir = fused && s->bd.has_dir;   // prescribed ghosts before each fused step
+    const bool dir = s->bd.has_dir;   // prescribed ghosts before each step
     if (dir) {
         kg.func = const_cast<void *>(dirichlet_ghosts_kernel_fn<T>());
         ghosts_launch_shape(s->grid.nx, s->grid.ny, &kg.gridDim, &kg.blockDim);
@@ -226,9 +221,6 @@ static cudaError_t build_graph(vlbm_state *s) {
         kp.func = const_cast<void *>(simple_kernel_fn<T>(s->limiter));
         simple_launch_shape(s->grid.nx, s->grid.ny, &kp.gridDim, &kp.blockDim);
         kp.kernelParams = pa;
-        kg.func = const_cast<void *>(ghosts_kernel_fn<T>());
-        ghosts_launch_shape(s->grid.nx, s->grid.ny, &kg.gridDim, &kg.blockDim);
-        kg.kernelParams = pa;
     }
     cudaGraphNode_t prev = nullptr;
     for (int k = 0; k < kGraphSteps && e == cudaSuccess; ++k) {
@@ -240,10 +232,6 @@ static cudaError_t build_graph(vlbm_state *s) {
         }
         e = cudaGraphAddKernelNode(&node, s->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
         prev = node;
-        if (e == cudaSuccess && !fused) {
-            e = cudaGraphAddKernelNode(&node, s->graph, &prev, 1, &kg);
-            prev = node;
-        }
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, s->graph, 0);
     if (e != cudaSuccess) {

@@ -231,11 +231,11 @@ bool build_recompute_descs(vlbm_state *s, char *scratch, const Plan &p, int32_t 
 
 // One recomputation step m = s0 + j of a segment.
 // The prescribed ghosts of slot j + 1 (the state s^m, m = s0 + j) at the control
-// block's t and a, for the row-marching kernel's recomputation and for the adjoint
-// step that reads that state.
+// block's t and a, for the recomputation step and for the adjoint step that read
+// that state.
 template <typename T>
 cudaError_t dirichlet_slot(vlbm_state *s, char *scratch, const Plan &p, int64_t m, int64_t j) {
-    if (!use_fused(s) || !s->bd.has_dir) return cudaSuccess;
+    if (!s->bd.has_dir) return cudaSuccess;
     StepArgs<T> A = args_of<T>(s);
     T *in = (T *)slot_ptr(scratch, p, s, j + 1), *out = (T *)slot_ptr(scratch, p, s, j + 2);
     A.buf0 = (m & 1) ? out : in;
@@ -260,9 +260,7 @@ cudaError_t recompute_step(vlbm_state *s, char *scratch, const Plan &p, int32_t 
     A.buf1 = (m & 1) ? in : out;
     A.ctl = (DevCtl *)(scratch + p.segctl_off);
     A.bd.ctl = A.ctl;
-    cudaError_t e = launch_step_simple<T>(A, s->stream);
-    if (e == cudaSuccess) e = launch_ghosts<T>(A, s->stream);   // reads the parity of n + 1
-    return e;
+    return launch_step_simple<T>(A, s->stream);   // writes the new state's ghost frame too
 }
 
 int rollout(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const Plan &p) {

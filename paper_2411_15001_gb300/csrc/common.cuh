@@ -405,6 +405,88 @@ __global__ void k_dirichlet_ghosts(StepArgs<T> A) {
     write_dirichlet_ghost(A, (A.ctl->n & 1) ? A.buf1 : A.buf0, gi, gj);
 }
 
+// The fields of a grid's descriptor that the step kernels' cell loops use, held in
+// registers (the descriptor itself lives in global memory).
+struct Geo {
+    int pitch, nx, ny;
+    int bc[4];
+    int sponge;
+};
+
+// Write the ghost images of interior cell (c, O) into `out`: its periodic
+// copies, zero-gradient copies or mirror images on the other side of every
+// boundary it sits next to (the inverse of the ghost_source map). Prescribed
+// (Dirichlet) parts get no images: the step that reads them evaluates the field.
+// A side that switches type does so at least two cells from its ends, so the
+// types at (c, O) hold for the corner images too.
+template <typename T>
+__device__ __forceinline__ void write_ghost_images(const Geo &D, T *out, int c, int O,
+                                                   const T nv[kNPlane], const Bound *bd) {
+    const int tW = D.bc[0] >= 0 ? D.bc[0] : side_type(*bd, 0, O);
+    const int tE = D.bc[1] >= 0 ? D.bc[1] : side_type(*bd, 1, O);
+    const int tS = D.bc[2] >= 0 ? D.bc[2] : side_type(*bd, 2, c);
+    const int tN = D.bc[3] >= 0 ? D.bc[3] : side_type(*bd, 3, c);
+    int gx[3], gy[3];
+    bool mxs[3], mys[3];
+    int ngx = 1, ngy = 1;
+    gx[0] = c;
+    mxs[0] = false;
+    gy[0] = O;
+    mys[0] = false;
+    const int nx = D.nx, ny = D.ny;
+    if (tW == VLBM_BC_PERIODIC) {
+        if (c >= nx - 2) { gx[ngx] = c - nx; mxs[ngx++] = false; }
+        if (c <= 1) { gx[ngx] = c + nx; mxs[ngx++] = false; }
+    } else {
+        if (c == 0 && tW == VLBM_BC_TRANSMISSIVE) {
+            gx[ngx] = -1; mxs[ngx++] = false;
+            gx[ngx] = -2; mxs[ngx++] = false;
+        }
+        if (c <= 1 && tW == VLBM_BC_REFLECTIVE) { gx[ngx] = -1 - c; mxs[ngx++] = true; }
+        if (c == nx - 1 && tE == VLBM_BC_TRANSMISSIVE) {
+            gx[ngx] = nx; mxs[ngx++] = false;
+            gx[ngx] = nx + 1; mxs[ngx++] = false;
+        }
+        if (c >= nx - 2 && tE == VLBM_BC_REFLECTIVE) { gx[ngx] = 2 * nx - 1 - c; mxs[ngx++] = true; }
+    }
+    if (tS == VLBM_BC_PERIODIC) {
+        if (O >= ny - 2) { gy[ngy] = O - ny; mys[ngy++] = false; }
+        if (O <= 1) { gy[ngy] = O + ny; mys[ngy++] = false; }
+    } else {
+        if (O == 0 && tS == VLBM_BC_TRANSMISSIVE) {
+            gy[ngy] = -1; mys[ngy++] = false;
+            gy[ngy] = -2; mys[ngy++] = false;
+        }
+        if (O <= 1 && tS == VLBM_BC_REFLECTIVE) { gy[ngy] = -1 - O; mys[ngy++] = true; }
+        if (O == ny - 1 && tN == VLBM_BC_TRANSMISSIVE) {
+            gy[ngy] = ny; mys[ngy++] = false;
+            gy[ngy] = ny + 1; mys[ngy++] = false;
+        }
+        if (O >= ny - 2 && tN == VLBM_BC_REFLECTIVE) { gy[ngy] = 2 * ny - 1 - O; mys[ngy++] = true; }
+    }
+    for (int a = 0; a < ngx; ++a)
+        for (int e = 0; e < ngy; ++e) {
+            if (a == 0 && e == 0) continue;
+            T *base = out + sidx(D.pitch, 0, gx[a], gy[e]);
+#pragma unroll
+            for (int g = 0; g < kNGroup; ++g) {
+                // u_1 <-> u_2 across an x-wall, u_3 <-> u_4 across a y-wall; the normal
+                // momentum of every group negated
+                const int gs = (g == 1 || g == 2) ? 3 - g : ((g == 3 || g == 4) ? 7 - g : g);
+                const bool sw = (g == 1 || g == 2) ? mxs[a] : ((g == 3 || g == 4) ? mys[e] : false);
+                T v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = sw ? nv[4 * gs + q] : nv[4 * g + q];
+                if (mxs[a]) v[1] = -v[1];
+                if (mys[e]) v[2] = -v[2];
+                T *gp = base + (long long)g * 4 * D.pitch;   // scalar stores: the images are rare, and a
+#pragma unroll                                                 // vector store would pin its values to aligned registers
+                for (int q = 0; q < 4; ++q) gp[q] = v[q];
+            }
+        }
+}
+
+
 // Fill the two ghost layers of buffer (n & 1): periodic wrap, zero-gradient copy
 // of u and u_1..u_4, or the mirror image (normal momentum negated in u and all
 // populations, u_1 <-> u_2 across an x-wall, u_3 <-> u_4 across a y-wall); a

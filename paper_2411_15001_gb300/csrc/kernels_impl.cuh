@@ -69,11 +69,6 @@ const void *simple_kernel_fn<VLBM_T>(int limiter) {
     }
 }
 
-template <>
-const void *ghosts_kernel_fn<VLBM_T>() {
-    return (const void *)k_ghosts<VLBM_T>;
-}
-
 namespace {
 template <int LIM, bool PROBE = false>
 cudaError_t fused_one(const FusedBatchArgs<VLBM_T> &B, int grid, cudaStream_t s) {

@@ -84,7 +84,8 @@ inline StepArgs<T> args_of(const vlbm_state *s) {
 
 // VLBM_KERNEL_AUTO. FP32: below this many cells a grid has too few row-marching
 // work items to fill the GPU and the one-thread-per-cell kernel is faster (PP on a
-// GB300: 45 vs 56 us at 512^2, 141 vs 101 us at 1024^2). FP64: every face's theta_p
+// GB300, a vortex with density bumps: 11.8 vs 20.4 us per step at 256^2, 27.3 vs
+// 35.4 us at 512^2, about even at 640^2, 93 vs 67 us at 1024^2). FP64: every face's theta_p
 // solve makes the step FP64-bound, where the one-thread-per-cell kernel's many warps
 // per SM win at every size measured (0.62 vs 1.50 ms at 512^2, 9.4 vs 10.3 ms at 2048^2).
 constexpr long long kAutoFusedMinCells = 1ll << 19;

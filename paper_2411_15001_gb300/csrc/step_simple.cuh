@@ -205,9 +205,21 @@ __global__ void __launch_bounds__(256) k_step_simple(StepArgs<T> A) {
     if (i < A.nx && j < A.ny) {
         T nv[kNPlane];
         cell_step<T, LIM>(L, i, j, k, Sponge(A.sponge, A.nx, A.ny, A.bc), nv, mon.fp64);
-        const long long d = cidx(A, i, j);
+        T *base = out + cidx(A, i, j);
 #pragma unroll
-        for (int q = 0; q < kNPlane; ++q) out[d + qoff(A, q)] = nv[q];
+        for (int g = 0; g < kNGroup; ++g)
+            st_group(base + qoff(A, 4 * g), nv[4 * g], nv[4 * g + 1], nv[4 * g + 2], nv[4 * g + 3]);
+        // the new state's ghost frame: images of the cells next to a side (prescribed
+        // ghosts are written before the step that reads them)
+        if (i < 2 || i >= A.nx - 2 || j < 2 || j >= A.ny - 2) {
+            Geo D;
+            D.pitch = A.pitch;
+            D.nx = A.nx;
+            D.ny = A.ny;
+            for (int q = 0; q < 4; ++q) D.bc[q] = A.bc[q];
+            D.sponge = A.sponge;
+            write_ghost_images(D, out, i, j, nv, &A.bd);
+        }
         mon.add_cell(nv, k.gamma, k.gm1);
     }
     block_publish(mon, C);

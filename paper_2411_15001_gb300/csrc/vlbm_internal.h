@@ -248,16 +248,15 @@ template <typename T> int fused_occupancy(int limiter);   // CTAs per SM of the 
 // Kernel function and dynamic shared memory of the fused kernel, for graph nodes.
 template <typename T> const void *fused_kernel_fn(int limiter, size_t *smem);
 // Kernel functions and launch shapes of the one-thread-per-cell step and of the
-// ghost-frame pass (for CUDA graph kernel nodes).
+// ghost-frame passes (for CUDA graph kernel nodes).
 template <typename T> const void *simple_kernel_fn(int limiter);
-template <typename T> const void *ghosts_kernel_fn();
 void simple_launch_shape(int nx, int ny, dim3 *grid, dim3 *block);
 void ghosts_launch_shape(int nx, int ny, dim3 *grid, dim3 *block);
 bool encode_state_tmap(CUtensorMap *out, void *base, const Layout &L);
 constexpr int kFusedBox = 128;                             // TMA box width (columns) = threads per CTA
 constexpr int kFusedHalo = 2;                              // box columns on either side of a strip
 constexpr int kFusedOut = kFusedBox - 2 * kFusedHalo;      // most output columns of a strip (124)
-constexpr int kFusedMinChunk = 16;                         // rows per work item, bounds
+constexpr int kFusedMinChunk = 4;                          // rows per work item, bounds
 constexpr int kFusedMaxChunk = 128;
 
 // Strips of a grid of nx columns: as few as hold kFusedOut columns each, of even widths
@@ -274,11 +273,14 @@ inline void strip_of(int nx, int s, int *x0, int *w) {
 // rows. Uniform order: bands of `hmax` rows. Guided order (guided self-scheduling,
 // Polychronopoulos & Kuck 1987): each band is as high as the work left -- strip-rows
 // of this grid and of the grids after it, `work_left`, which the call decreases --
-// divided by the CTA count, within [kFusedMinChunk, hmax]: the first items are
-// tall (few repeated halo rows), the last ones short (a CTA taking one near the end
-// of the step finishes soon after the others). Measured on the 4096^2 blast (3 CTAs
-// x 152 SMs): 6.6 % faster than the best uniform height; work left / (2 x CTAs) and
-// minimum heights of 8-32 rows were within 2.5 % of it.
+// divided by the CTA count (rounded up), within [kFusedMinChunk, hmax]: the first
+// items are tall (few repeated halo rows), the last ones short (a CTA taking one
+// near the end of the step finishes soon after the others), and a grid too small to
+// give every CTA a tall band is cut into about one band per CTA. Measured on the
+// 4096^2 blast (3 CTAs x 152 SMs): 6.6 % faster than the best uniform height; work
+// left / (2 x CTAs) was within 2.5 % of it; a minimum height of 4 rows instead of
+// 16 gains 0.7 % there and 1.8 x on a 256^2 grid (one wave of short bands instead
+// of a few CTAs marching 16 rows each).
 inline int append_items(WorkItem *out, int inst, int nx, int ny, int hmax, bool guided,
                         long long &work_left, long long ctas) {
     const int strips = strip_count(nx);
@@ -286,7 +288,8 @@ inline int append_items(WorkItem *out, int inst, int nx, int ny, int hmax, bool 
     for (int y = 0; y < ny;) {
         long long h = hmax;
         if (guided) {
-            h = work_left / (ctas > 0 ? ctas : 1);
+            const long long c = ctas > 0 ? ctas : 1;
+            h = (work_left + c - 1) / c;
             if (h < kFusedMinChunk) h = kFusedMinChunk;
             if (h > hmax) h = hmax;
         }
