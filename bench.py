@@ -50,6 +50,16 @@ def _peaks():
         return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
+# The 1024^2 LMP quadrant run (FP32 populations, to t = 0.25) is held to the spread
+# of the FP64 oracle itself under float-level noise, not to the stated 1e-3 L1 target:
+# tests/test_gpu_fullsize.py and tests/golden/quadrant1024_lmp_jitter.txt.
+ACCURACY_GAP_1024_LMP = (
+    "1024^2 four-quadrant Riemann problem, LMP, FP32 populations, t = 0.25: the stated L1(rho) "
+    "target of 1e-3 against FP64 is not met (measured about 4e-3); the FP64 oracle run under "
+    "2^-24 relative noise per step spreads 5.4e-3 from its own clean run (discontinuous data "
+    "amplifies rounding), and the test holds FP32 to 1.1 x that spread")
+
+
 # The sources the FP32 step kernel is compiled from (its translation unit and
 # headers): a committed ncu summary counts for the kernel while these are unchanged.
 STEP_KERNEL_SOURCES = ("common.cuh", "kernels_f32.cu", "kernels_impl.cuh", "physics.cuh", "step_fused.cuh",
@@ -377,6 +387,7 @@ def run_ours(args):
                                steps_total=args.warmup + args.steps,
                                positivity_violations=mon["bad_cells"] + mon["nonfinite_cells"],
                                first_bad_step=mon["first_bad_step"], status=mon["status"]),
+                "known_gaps": [ACCURACY_GAP_1024_LMP],
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
                 "roofline": roof, "full_run": full}
         if not args.no_batched:

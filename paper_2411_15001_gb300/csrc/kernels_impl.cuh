@@ -75,7 +75,7 @@ cudaError_t fused_one(const FusedBatchArgs<VLBM_T> &B, int grid, cudaStream_t s)
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
-    const size_t smem = sizeof(FusedSmem<VLBM_T>);
+    const size_t smem = sizeof(FusedSmem<VLBM_T, fused_lag(LIM)>);
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(k_step_fused<VLBM_T, LIM, PROBE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -89,7 +89,7 @@ cudaError_t fused_one(const FusedBatchArgs<VLBM_T> &B, int grid, cudaStream_t s)
 template <int LIM>
 int fused_blocks_per_sm() {
     int nb = 0;
-    const size_t smem = sizeof(FusedSmem<VLBM_T>);
+    const size_t smem = sizeof(FusedSmem<VLBM_T, fused_lag(LIM)>);
     cudaFuncSetAttribute(k_step_fused<VLBM_T, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_fused<VLBM_T, LIM>, kFB, smem) != cudaSuccess)
         nb = 1;
@@ -110,7 +110,7 @@ int fused_occupancy<VLBM_T>(int limiter) {
 
 template <>
 const void *fused_kernel_fn<VLBM_T>(int limiter, size_t *smem) {
-    *smem = sizeof(FusedSmem<VLBM_T>);
+    *smem = fused_lag(limiter) == 2 ? sizeof(FusedSmem<VLBM_T, 2>) : sizeof(FusedSmem<VLBM_T, 1>);
     fused_blocks_per_sm<VLBM_LIM_PP>();   // sets the dynamic shared memory attributes
     switch (limiter) {
         case VLBM_LIM_FIRST_ORDER: fused_blocks_per_sm<VLBM_LIM_FIRST_ORDER>(); return (const void *)k_step_fused<VLBM_T, VLBM_LIM_FIRST_ORDER>;

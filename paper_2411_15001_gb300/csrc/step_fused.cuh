@@ -14,14 +14,16 @@
 // grid's last item runs that grid's end-of-step reduction.
 //
 // Rows arrive by TMA (two boxes of 64 columns x 5 groups of 4 values per row, see the
-// state layout in vlbm_internal.h) into a 3-slot ring completed on mbarriers. Per row R (output row O = R - 2, the
-// radius-2 stencil of the LMP bounds, eq. LMP_minmax):
+// state layout in vlbm_internal.h) into a 3-slot ring completed on mbarriers. Per row R
+// (output row O = R - lag: lag 1 for PP and the fixed thetas, lag 2 for LMP / RLMP,
+// whose bounds have the radius-2 stencil of eq. LMP_minmax):
 //  P1  fluxes, Maxwellians, non-equilibrium parts d_k of row R; what x-neighbours
-//      need (u, f, d_1, d_2) goes to a 4-row shared ring, what only the own column
-//      needs (u, g, d_3, d_4) to a 4-row register history; rho* of y-face R - 1/2.
+//      need (u, f, d_1, d_2) goes to a shared ring of lag + 2 rows, what only the own
+//      column needs (u, g, d_3, d_4) to a register history; rho* of y-face R - 1/2.
 //  P2  density bounds of row R - 1 (LMP/RLMP).
-//  P3  theta of the x-faces of row R - 1 and of y-face R - 3/2 (Sec. 3.3-3.4);
-//      then u*, dF of the x-faces of row R and of y-face R - 1/2.
+//  P3  PP and the fixed thetas: u*, dF and theta of the x-face of row R and of y-face
+//      R - 1/2 (Sec. 3.3-3.4). LMP / RLMP: theta of the x-faces of row R - 1 and of
+//      y-face R - 3/2, their face states formed again there.
 // Barriers: S1 after P1 (the ring row R and the previous row's theta are
 // complete); the bounds a thread needs of its right neighbour (LMP / RLMP) it forms
 // itself from the shared rows.
@@ -39,14 +41,20 @@ namespace vlbm {
 constexpr int kFB = kFusedBox;     // threads per CTA = TMA box width (columns)
 constexpr int kFHalo = kFusedHalo; // box columns left (and right) of the strip
 constexpr int kRawSlots = 3;   // TMA row ring
-constexpr int kXSlots = 4;     // shared ring of per-row neighbour data
 
-template <typename T>
+// The output row of row iteration R is R - lag: 1 for PP and the fixed thetas, 2
+// for LMP / RLMP (the bounds of a cell need the row above it).
+__host__ __device__ constexpr int fused_lag(int limiter) {
+    return limiter == VLBM_LIM_LMP || limiter == VLBM_LIM_RLMP ? 2 : 1;
+}
+
+template <typename T, int LAG>
 struct FusedSmem {
+    static constexpr int kX = LAG + 2;          // rows R - LAG .. R in use, one being refilled
     T raw[kRawSlots][2][kNGroup][kFB / 2][4];   // [slot][half of the strip][group][column][component]
-    T X[kXSlots][16][kFB];     // u (0..3), f (4..7), d_1 (8..11), d_2 (12..15)
-    T rsx[2][kFB];             // rho* of x-face (b, b+1)
-    T thx[3][kFB];             // theta of x-face (b, b+1): PP by row R % 3, LMP / RLMP by (R - 1) & 1
+    T X[kX][16][kFB];          // u (0..3), f (4..7), d_1 (8..11), d_2 (12..15)
+    T rsx[LAG == 2 ? 2 : 1][kFB];   // LMP / RLMP: rho* of x-face (b, b+1), by row R & 1
+    T thx[2][kFB];             // theta of x-face (b, b+1): PP by row R & 1, LMP / RLMP by (R - 1) & 1
     unsigned long long bar[kRawSlots];
     int item;
     int abort;
@@ -59,7 +67,9 @@ struct Hist {
 
 template <typename T, int LIM>
 struct FusedCtx {
-    FusedSmem<T> &S;
+    static constexpr int kLag = fused_lag(LIM);
+    static constexpr int kX = kLag + 2;
+    FusedSmem<T, kLag> &S;
     const CUtensorMap *tmap;
     const Geo &D;
     const StepConsts<T> &k;
@@ -69,18 +79,22 @@ struct FusedCtx {
     uint32_t &nissued, &nconsumed;
     int xb, xpad, c, y0, y1, R1, wout;   // strip: box origin, padded origin, own column, rows, width
     // PP and the fixed thetas form the faces of row R (x-face c+1/2, y-face R-1/2) in
-    // row R and limit them there: only two thetas of y-faces cross rows. LMP / RLMP
-    // need the density bounds of both cells of a face, complete one row later, so
-    // they limit the faces of row R-1 in row R, recomputing the face states there.
+    // row R and limit them there, so row R - 1 is complete (output lag 1; one theta of
+    // a y-face crosses rows). LMP / RLMP need the density bounds of both cells of a
+    // face, complete one row later, so they limit the faces of row R-1 in row R,
+    // recomputing the face states there (output lag 2).
     static constexpr bool kRecompute = LIM == VLBM_LIM_LMP || LIM == VLBM_LIM_RLMP;
     T xs_us[4], xs_df[4];   // LMP / RLMP: x-face (c+1/2) of row R-1
     T ys_us[4], ys_df[4];   // LMP / RLMP: y-face between rows R-2 and R-1
     T rsy_prev;             // rho* of the y-face between rows R-2 and R-1
     T mu2, nu2;             // bounds of row R-2 (own column)
     T thy_prev;             // LMP / RLMP: theta of the y-face between rows R-3 and R-2
-    T ty1, ty2;             // PP: thetas of the y-faces (R-2, R-1) and (R-3, R-2)
-    Hist<T> h1, h2;         // rows R-1, R-2 of the own column
-    T p3n[4];               // u_3 of row R-2 after the step (pulled from row R-3)
+    T ty1;                  // PP: theta of the y-face (R-2, R-1)
+    Hist<T> h1, h2;         // rows R-1, R-2 of the own column (h2: LMP / RLMP)
+    T p3n[4];               // u_3 of the next output row after the step (pulled from the one below)
+
+    // Slot of row R (>= -2) in the shared ring X.
+    static __device__ __forceinline__ int xslot(int R) { return (R + 2 * kX) % kX; }
 
     // The grid's descriptor (the tensor map is its first member).
     __device__ __forceinline__ const InstDesc<T> *desc() const {
@@ -105,7 +119,7 @@ struct FusedCtx {
             h1.d4[q] = h2.d4[q] = T(0);
             p3n[q] = T(0);
         }
-        rsy_prev = mu2 = nu2 = thy_prev = ty1 = ty2 = T(0);
+        rsy_prev = mu2 = nu2 = thy_prev = ty1 = T(0);
     }
 
     // P1 of row R (see the file comment); returns rho* of the y-face R - 1/2. f and d1
@@ -120,7 +134,7 @@ struct FusedCtx {
         euler_fluxes(u, k.gm1, f, g);
         maxwell_pm(u, f, k, M1, M2);
         maxwell_pm(u, g, k, M3, M4);
-        const int xs = R & 3;
+        const int xs = xslot(R);
         // each population group is read right where its non-equilibrium part is formed
         ld_group(&S.raw[slot][b >> 6][1][b & 63][0], pv);
 #pragma unroll
@@ -151,7 +165,7 @@ struct FusedCtx {
     // neighbour's from the shared ring.
     __device__ __forceinline__ void row_faces(int R, const Hist<T> &h0, T rsy_new, int br, const T f[4],
                                               const T d1[4], T xus[4], T xdf[4], T yus[4], T ydf[4]) const {
-        const int xs = R & 3;
+        const int xs = xslot(R);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             xus[q] = face_star(h0.u[q], f[q], S.X[xs][q][br], S.X[xs][4 + q][br], k);
@@ -161,11 +175,11 @@ struct FusedCtx {
         }
     }
 
-    // PP and the fixed thetas: theta of the x-face (c, c+1) of row R and of the y-face
-    // (R - 1, R) of the own column, from their face states, with the sponge layer;
-    // stored / shifted into the slots P4 of the next rows reads.
-    __device__ __forceinline__ void row_thetas(int R, const T xus[4], const T xdf[4], const T yus[4],
-                                               const T ydf[4]) {
+    // PP and the fixed thetas: theta of the x-face (c, c+1) of row R (stored in the
+    // shared slot R & 1 for the neighbours) and of the y-face (R - 1, R) of the own
+    // column (returned), from their face states, with the sponge layer.
+    __device__ __forceinline__ T row_thetas(int R, const T xus[4], const T xdf[4], const T yus[4],
+                                            const T ydf[4]) {
         T tx, ty;
         // theta is needed for the x-faces of columns kFHalo-1 .. kFHalo+wout-1 and the
         // y-faces of the strip's own columns, inside the grid. The other threads hold
@@ -193,9 +207,8 @@ struct FusedCtx {
             if (c0 || sp.cell(c + 1, R)) tx = T(0);        // x-face (c, c+1) of row R
             if (c0 || sp.cell(c, R - 1)) ty = T(0);        // y-face (R-1, R) of column c
         }
-        S.thx[R % 3][b] = tx;
-        ty2 = ty1;
-        ty1 = ty;
+        S.thx[R & 1][b] = tx;
+        return ty;
     }
 
     // LMP density bounds (eq. LMP_minmax): min / max of rho of a cell and rho* of its
@@ -220,7 +233,7 @@ struct FusedCtx {
     // operations on the same values as that column's own thread, so the same bits,
     // without a barrier to publish them.
     __device__ __forceinline__ void bounds_right(int R, int br, T &mu, T &nu) const {
-        const int rp = (R - 1) & 1, x0 = (R - 2) & 3, x1 = (R - 1) & 3, x2 = R & 3;
+        const int rp = (R - 1) & 1, x0 = xslot(R - 2), x1 = xslot(R - 1), x2 = xslot(R);
         const T r1 = S.X[x1][0][br], m1 = S.X[x1][2][br];
         const T syp = face_star(S.X[x0][0][br], S.X[x0][2][br], r1, m1, k);
         const T syn = face_star(r1, m1, S.X[x2][0][br], S.X[x2][2][br], k);
@@ -241,15 +254,15 @@ struct FusedCtx {
         const int bl = b > 0 ? b - 1 : 0, br = b < kFB - 1 ? b + 1 : b;
         if constexpr (kRecompute) {
             bounds(R, rsy_new, bl, mu2, nu2);
-            const int xs = R & 3;
+            const int xs = xslot(R);
             S.rsx[R & 1][b] = face_star(h0.u[0], S.X[xs][4][b], S.X[xs][0][br], S.X[xs][4][br], k);
+            h2 = h1;
         } else {
             T xus[4], xdf[4], yus[4], ydf[4];
             row_faces(R, h0, rsy_new, br, fo, d1o, xus, xdf, yus, ydf);
-            row_thetas(R, xus, xdf, yus, ydf);
+            ty1 = row_thetas(R, xus, xdf, yus, ydf);
         }
         rsy_prev = rsy_new;
-        h2 = h1;
         h1 = h0;
         return true;
     }
@@ -271,7 +284,7 @@ struct FusedCtx {
             tx = ty = T(0);
         } else {
             {
-                const int xp = (R - 1) & 3;
+                const int xp = xslot(R - 1);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     xs_us[q] = face_star(h1.u[q], S.X[xp][4 + q][b], S.X[xp][q][br], S.X[xp][4 + q][br], k);
@@ -304,12 +317,11 @@ struct FusedCtx {
         T fo[4], d1o[4];
         // ---------------------------------------------------------------- P1
         const T rsy_new = p1(R, h0, fo, d1o);
-        const int xs = R & 3;
         const int bl = b > 0 ? b - 1 : 0, br = b < kFB - 1 ? b + 1 : b;
         __syncthreads();                                                  // S1
         if (S.abort) return false;
         if (b == 0 && R + kRawSlots <= R1) issue(R + kRawSlots);
-        T tw, te, ts, tn;   // thetas of the west, east, south and north faces of row R - 2
+        T tw, te, ts, tn;   // thetas of the west, east, south and north faces of row O
         if constexpr (kRecompute) {
             // -------------------------------------------------------- P2
             T mu1, nu1, muR, nuR, tx, ty;
@@ -321,6 +333,7 @@ struct FusedCtx {
             mu2 = mu1;
             nu2 = nu1;
             // rho* of the x-face (b, b+1) of row R, for the next row's density bounds
+            const int xs = xslot(R);
             S.rsx[R & 1][b] = face_star(h0.u[0], S.X[xs][4][b], S.X[xs][0][br], S.X[xs][4][br], k);
             tw = S.thx[(R - 2) & 1][bl];
             te = S.thx[(R - 2) & 1][b];
@@ -329,37 +342,41 @@ struct FusedCtx {
             thy_prev = ty;
         } else {
             // -------------------------------------------------------- P3
-            tw = S.thx[(R - 2) % 3][bl];
-            te = S.thx[(R - 2) % 3][b];
-            ts = ty2;
-            tn = ty1;
             T xus[4], xdf[4], yus[4], ydf[4];
             row_faces(R, h0, rsy_new, br, fo, d1o, xus, xdf, yus, ydf);
-            row_thetas(R, xus, xdf, yus, ydf);
+            const T ty = row_thetas(R, xus, xdf, yus, ydf);
+            tw = S.thx[(R - 1) & 1][bl];
+            te = S.thx[(R - 1) & 1][b];
+            ts = ty1;
+            tn = ty;
+            ty1 = ty;
         }
         rsy_prev = rsy_new;
-        // No barrier before P4: it reads theta of row R-2's x-faces (written two rows
-        // (PP) or one row (LMP / RLMP) ago) and the ring rows of R-2, ordered by this
-        // row's S1; every slot this row's P3 writes is read only after the next row's
-        // S1, and every slot the next row overwrites is read here before this thread
-        // reaches that S1 (PP: the theta slot R % 3 was last read by P4 of row R - 1).
+        // No barrier before P4: it reads theta of row O's x-faces (written one row ago)
+        // and the ring row O, ordered by this row's S1; every slot this row's P3 writes
+        // is read only after the next row's S1, and every slot the next row overwrites
+        // is read here before this thread reaches that S1.
         // ---------------------------------------------------------------- P4
-        const int O = R - 2;
-        const int xo = O & 3;
+        // row O and the row above it: in the register history (LMP / RLMP: h2, h1;
+        // PP and the fixed thetas: h1 and the row just loaded)
+        const int O = R - kLag;
+        const int xo = xslot(O);
+        const Hist<T> &hc = kRecompute ? h2 : h1;
+        const Hist<T> &hn = kRecompute ? h1 : h0;
         T nv[kNPlane];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const T M1W = maxwell_plus(S.X[xo][q][bl], S.X[xo][4 + q][bl], k);
             const T M2E = maxwell_minus(S.X[xo][q][br], S.X[xo][4 + q][br], k);
-            const T M4N = maxwell_minus(h1.u[q], h1.g[q], k);
+            const T M4N = maxwell_minus(hn.u[q], hn.g[q], k);
             nv[4 + q] = blend_pop(M1W, S.X[xo][8 + q][bl], tw);
             nv[8 + q] = blend_pop(M2E, S.X[xo][12 + q][br], te);
             nv[12 + q] = p3n[q];
-            nv[16 + q] = blend_pop(M4N, h1.d4[q], tn);
-            nv[q] = blend_u(nv[4 + q], nv[8 + q], nv[12 + q], nv[16 + q], h2.u[q], tw, S.X[xo][12 + q][b],
-                            te, S.X[xo][8 + q][b], ts, h2.d4[q], tn, h2.d3[q], k);
+            nv[16 + q] = blend_pop(M4N, hn.d4[q], tn);
+            nv[q] = blend_u(nv[4 + q], nv[8 + q], nv[12 + q], nv[16 + q], hc.u[q], tw, S.X[xo][12 + q][b],
+                            te, S.X[xo][8 + q][b], ts, hc.d4[q], tn, hc.d3[q], k);
             // u_3 of row O + 1 after the step, pulled from row O with theta of y-face O + 1/2
-            p3n[q] = blend_pop(maxwell_plus(h2.u[q], h2.g[q], k), h2.d3[q], tn);
+            p3n[q] = blend_pop(maxwell_plus(hc.u[q], hc.g[q], k), hc.d3[q], tn);
         }
         if (O >= y0 && O < y1 && b >= kFHalo && b < kFHalo + wout && c < D.nx) {
             T *base = out + sidx(D.pitch, 0, c, O);
@@ -370,15 +387,15 @@ struct FusedCtx {
             mon.add_cell(nv, k.gamma, k.gm1);
         }
         // shift the register history
-        h2 = h1;
+        if constexpr (kRecompute) h2 = h1;
         h1 = h0;
         return true;
     }
 };
 
 // Wait (bounded) for this CTA's loads still in flight before it exits.
-template <typename T>
-__device__ void drain_loads(FusedSmem<T> &S, uint32_t nissued, uint32_t nconsumed) {
+template <typename SM>
+__device__ void drain_loads(SM &S, uint32_t nissued, uint32_t nconsumed) {
     if (threadIdx.x == 0) {
         while (nconsumed < nissued) {
             const int slot = nconsumed % kRawSlots;
@@ -395,7 +412,8 @@ template <typename T, int LIM, bool PROBE = false>
 __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
     k_step_fused(FusedBatchArgs<T> B) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    FusedSmem<T> &S = *reinterpret_cast<FusedSmem<T> *>(smem_raw);
+    constexpr int kLag = fused_lag(LIM);
+    FusedSmem<T, kLag> &S = *reinterpret_cast<FusedSmem<T, kLag> *>(smem_raw);
     const int b = threadIdx.x;
     // TMA destinations must be 128-byte aligned; dynamic shared memory follows
     // the static block of the reductions, so check rather than assume.
@@ -445,15 +463,16 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         X.xb = (it.xw & 0xffffff) - kFHalo;
         X.xpad = X.xb + kOX;
         X.c = X.xb + b;
-        // LMP / RLMP start at row y0 - 2 (the bounds of row y0 - 1 need rho* of the
-        // y-face y0 - 3/2), the others at y0 - 1
-        const int R0 = X.y0 - (FusedCtx<T, LIM>::kRecompute ? 2 : 1);
-        X.R1 = X.y1 + 1;
+        // rows y0 - lag .. y1 + lag - 1 (output rows y0 - 1 .. y1 - 1): LMP / RLMP start
+        // at row y0 - 2 (the bounds of row y0 - 1 need rho* of the y-face y0 - 3/2),
+        // the others at y0 - 1; rows before y0 + lag - 1 only load and form faces
+        const int R0 = X.y0 - kLag;
+        X.R1 = X.y1 + kLag - 1;
         if (b == 0)
             for (int r = R0; r < R0 + kRawSlots && r <= X.R1; ++r) X.issue(r);
         X.reset_state();
         int R = R0;
-        for (; R < X.y0 + 1 && ok; ++R) ok = X.row_warm(R);
+        for (; R < X.y0 + kLag - 1 && ok; ++R) ok = X.row_warm(R);
         for (; R <= X.R1 && ok; ++R) ok = X.row(R);
         if (!ok) break;
         // the item's monitors go to its grid; the CTA finishing the grid's last item
