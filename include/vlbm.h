@@ -350,11 +350,13 @@ VLBM_API const char *vlbm_batch_last_error(const vlbm_batch *b);
  * and a step whose lambda^n is set by the prescribed states hands nothing to the
  * cells.
  *
- * Memory: checkpoints of the state every ckpt_every steps, a segment buffer of
- * ckpt_every + 1 states for the recomputation, and two cotangent buffers, all in
- * caller-owned d_scratch of vlbm_adjoint_scratch_bytes (256-byte aligned). Cost:
- * one forward run, one recomputation of every step but the last of each
- * segment, and one adjoint kernel per step. */
+ * Memory: checkpoints of the state every ckpt_every steps, two segment buffers of
+ * ckpt_every + 1 states for the recomputation (the recomputation of one segment
+ * runs on a second stream of the library's, overlapping the adjoint steps of the
+ * segment after it), and two cotangent buffers, all in caller-owned d_scratch of
+ * vlbm_adjoint_scratch_bytes (256-byte aligned). Cost: one forward run, one
+ * recomputation of every step but the last of each segment, and one adjoint kernel
+ * per step. */
 VLBM_API size_t vlbm_adjoint_scratch_bytes(const vlbm_state *s, int64_t nsteps, int32_t ckpt_every);
 
 /* How vlbm_adjoint treats a dynamic kinetic speed (see above); the mode applies

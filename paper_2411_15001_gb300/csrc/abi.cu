@@ -591,6 +591,11 @@ void vlbm_destroy(vlbm_state *s) {
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     if (s->graph) cudaGraphDestroy(s->graph);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+    if (s->aux_ready) {
+        DeviceGuard g(s->device);
+        for (int i = 0; i < kAuxEvents; ++i) cudaEventDestroy(s->aux_ev[i]);
+        cudaStreamDestroy(s->aux_stream);
+    }
     delete s;
 }
 

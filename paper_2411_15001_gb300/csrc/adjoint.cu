@@ -5,10 +5,12 @@
 // Rollout: the state's own step kernel advances n = 0 .. N-1; the state and its
 // control block are copied to checkpoint c before step c k.
 // Reverse sweep, one segment [s, e] = [c k, min(c k + k, N) - 1] at a time, last
-// segment first: the checkpoint is restored into slot 1 of a segment buffer and
+// segment first: the checkpoint is restored into slot 1 of segment buffer c % 2 and
 // the same step kernel recomputes the states s+1 .. e into slots 2 .. e-s+1
 // (reading slot j, writing slot j+1, with the control block in scratch); then the
-// adjoint kernel maps the cotangent of s^{m+1} to that of s^m for m = e .. s.
+// adjoint kernel maps the cotangent of s^{m+1} to that of s^m for m = e .. s. The
+// recomputation of segment c - 1 runs on a second stream while the adjoint steps of
+// segment c run on the state's stream.
 // Finally the transpose of the initialisation u_k^0 = M_k(u_0) folds the
 // population cotangents into the conserved planes.
 // a^n is held as the forward run produced it: a constant when the state was made
@@ -149,10 +151,12 @@ size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 struct Plan {
     int64_t nckpt;        // checkpoints at steps 0, k, 2k, ...
     size_t ckpt_stride;   // state buffer + control block
-    size_t seg_off;       // k + 1 state slots (slot 0 is only ever a TMA window start)
-    size_t segctl_off;    // control block of the recomputation
-    size_t desc_off;      // 2 k InstDesc of the row-marching kernel (by parity of n)
-    size_t khist_off;     // the step constants (a^n) and the time t^n of each step of a segment
+    // Two segment buffers: the recomputation of one segment overlaps the adjoint
+    // steps of the segment after it (see reverse). Each holds
+    size_t seg_off[2];    // k + 1 state slots (slot 0 is only ever a TMA window start),
+    size_t segctl_off[2]; // the control block of the recomputation,
+    size_t desc_off[2];   // 2 k InstDesc of the row-marching kernel (by parity of n),
+    size_t khist_off[2];  // the step constants (a^n) and the time t^n of each step.
     size_t cot_off;       // two cotangent buffers of nx x ny cells (grouped, kidx)
     size_t cot_bytes;
     size_t red_off;       // the dL/da hand-over slots
@@ -167,14 +171,16 @@ Plan plan_of(const vlbm_state *s, int64_t nsteps, int32_t every) {
     p.nckpt = nsteps > 0 ? (nsteps + every - 1) / every : 1;
     p.ckpt_stride = round256(buf) + kCtlBytes;
     size_t off = (size_t)p.nckpt * p.ckpt_stride;
-    p.seg_off = off;
-    off += (size_t)(every + 1) * round256(buf);
-    p.segctl_off = off;
-    off += kCtlBytes;
-    p.desc_off = off;
-    off += (size_t)2 * every * 512;
-    p.khist_off = off;
-    off += round256((size_t)every * kConstSlot);
+    for (int q = 0; q < 2; ++q) {
+        p.seg_off[q] = off;
+        off += (size_t)(every + 1) * round256(buf);
+        p.segctl_off[q] = off;
+        off += kCtlBytes;
+        p.desc_off[q] = off;
+        off += (size_t)2 * every * 512;
+        p.khist_off[q] = off;
+        off += round256((size_t)every * kConstSlot);
+    }
     p.cot_bytes = round256((size_t)kNPlane * s->grid.nx * s->grid.ny * s->L.elem);
     p.cot_off = off;
     off += 2 * p.cot_bytes;
@@ -190,8 +196,8 @@ Plan plan_of(const vlbm_state *s, int64_t nsteps, int32_t every) {
     return p;
 }
 
-char *slot_ptr(char *scratch, const Plan &p, const vlbm_state *s, int64_t j) {
-    return scratch + p.seg_off + (size_t)j * round256(s->L.buf_bytes);
+char *slot_ptr(char *scratch, const Plan &p, const vlbm_state *s, int q, int64_t j) {
+    return scratch + p.seg_off[q] + (size_t)j * round256(s->L.buf_bytes);
 }
 
 int check_scratch(vlbm_state *s, void *scratch, size_t bytes, const Plan &p) {
@@ -211,7 +217,7 @@ int check_scratch(vlbm_state *s, void *scratch, size_t bytes, const Plan &p) {
 // 20 (n & 1) .. 20 (n & 1) + 19 of its TMA window, so the window starts
 // (n & 1) slots before the slot it reads.
 template <typename T>
-bool build_recompute_descs(vlbm_state *s, char *scratch, const Plan &p, int32_t every,
+bool build_recompute_descs(vlbm_state *s, char *scratch, const Plan &p, int32_t every, int q,
                            std::vector<unsigned char> &host) {
     host.assign((size_t)2 * every * 512, 0);
     InstDesc<T> base;
@@ -219,10 +225,10 @@ bool build_recompute_descs(vlbm_state *s, char *scratch, const Plan &p, int32_t 
     for (int par = 0; par < 2; ++par) {
         for (int j = 0; j + 1 < every; ++j) {   // the last state of a segment is not stepped
             InstDesc<T> d = base;
-            char *in = slot_ptr(scratch, p, s, j + 1);
+            char *in = slot_ptr(scratch, p, s, q, j + 1);
             if (!encode_state_tmap(&d.tmap, in - (size_t)par * round256(s->L.buf_bytes), s->L)) return false;
-            d.buf0 = d.buf1 = (T *)slot_ptr(scratch, p, s, j + 2);
-            d.ctl = (DevCtl *)(scratch + p.segctl_off);
+            d.buf0 = d.buf1 = (T *)slot_ptr(scratch, p, s, q, j + 2);
+            d.ctl = (DevCtl *)(scratch + p.segctl_off[q]);
             memcpy(host.data() + ((size_t)par * every + j) * 512, &d, sizeof d);
         }
     }
@@ -234,33 +240,35 @@ bool build_recompute_descs(vlbm_state *s, char *scratch, const Plan &p, int32_t 
 // block's t and a, for the recomputation step and for the adjoint step that read
 // that state.
 template <typename T>
-cudaError_t dirichlet_slot(vlbm_state *s, char *scratch, const Plan &p, int64_t m, int64_t j) {
+cudaError_t dirichlet_slot(vlbm_state *s, char *scratch, const Plan &p, int q, int64_t m, int64_t j,
+                           cudaStream_t st) {
     if (!s->bd.has_dir) return cudaSuccess;
     StepArgs<T> A = args_of<T>(s);
-    T *in = (T *)slot_ptr(scratch, p, s, j + 1), *out = (T *)slot_ptr(scratch, p, s, j + 2);
+    T *in = (T *)slot_ptr(scratch, p, s, q, j + 1), *out = (T *)slot_ptr(scratch, p, s, q, j + 2);
     A.buf0 = (m & 1) ? out : in;
     A.buf1 = (m & 1) ? in : out;
-    A.ctl = (DevCtl *)(scratch + p.segctl_off);
+    A.ctl = (DevCtl *)(scratch + p.segctl_off[q]);
     A.bd.ctl = A.ctl;
-    return launch_dirichlet_ghosts<T>(A, s->stream);
+    return launch_dirichlet_ghosts<T>(A, st);
 }
 
 template <typename T>
-cudaError_t recompute_step(vlbm_state *s, char *scratch, const Plan &p, int32_t every, int64_t m, int64_t j) {
-    cudaError_t e0 = dirichlet_slot<T>(s, scratch, p, m, j);
+cudaError_t recompute_step(vlbm_state *s, char *scratch, const Plan &p, int32_t every, int q, int64_t m, int64_t j,
+                           cudaStream_t st) {
+    cudaError_t e0 = dirichlet_slot<T>(s, scratch, p, q, m, j, st);
     if (e0 != cudaSuccess) return e0;
     if (use_fused(s)) {
         FusedBatchArgs<T> B = batch_args_of<T>(s);
-        B.insts = (const InstDesc<T> *)(scratch + p.desc_off + ((size_t)(m & 1) * every + j) * 512);
-        return launch_step_fused<T>(B, s->limiter, s->fused_grid, s->stream);
+        B.insts = (const InstDesc<T> *)(scratch + p.desc_off[q] + ((size_t)(m & 1) * every + j) * 512);
+        return launch_step_fused<T>(B, s->limiter, s->fused_grid, st);
     }
     StepArgs<T> A = args_of<T>(s);
-    T *in = (T *)slot_ptr(scratch, p, s, j + 1), *out = (T *)slot_ptr(scratch, p, s, j + 2);
+    T *in = (T *)slot_ptr(scratch, p, s, q, j + 1), *out = (T *)slot_ptr(scratch, p, s, q, j + 2);
     A.buf0 = (m & 1) ? out : in;
     A.buf1 = (m & 1) ? in : out;
-    A.ctl = (DevCtl *)(scratch + p.segctl_off);
+    A.ctl = (DevCtl *)(scratch + p.segctl_off[q]);
     A.bd.ctl = A.ctl;
-    return launch_step_simple<T>(A, s->stream);   // writes the new state's ghost frame too
+    return launch_step_simple<T>(A, st);   // writes the new state's ghost frame too
 }
 
 int rollout(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const Plan &p) {
@@ -285,16 +293,58 @@ int rollout(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     return VLBM_OK;
 }
 
+// The second stream of the reverse sweep and its events (made on first use, on the
+// state's device; destroyed with the state).
+static cudaError_t aux_stream(vlbm_state *s) {
+    if (s->aux_ready) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->aux_stream, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i < kAuxEvents; ++i)
+        e = cudaEventCreateWithFlags(&s->aux_ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) s->aux_ready = true;
+    return e;
+}
+
+// Recomputation of segment c (steps s0 .. e0) into segment buffer q on stream st:
+// the checkpoint into slot 1, then the step kernel for steps s0 .. e0 - 1, with the
+// constants (and times) of every step recorded for the adjoint steps.
+template <typename T>
+cudaError_t recompute_segment(vlbm_state *s, char *scratch, const Plan &p, int64_t nsteps, int32_t every, int64_t c,
+                              int q, cudaStream_t st) {
+    const size_t buf = s->L.buf_bytes;
+    const bool fixed_a = s->a_fixed > 0.0;
+    const bool diff_a = !fixed_a && s->adj_mode == VLBM_ADJOINT_DIFF_A;
+    DevCtl *segctl = (DevCtl *)(scratch + p.segctl_off[q]);
+    char *khist = scratch + p.khist_off[q];
+    const int64_t s0 = c * every;
+    const int64_t e0 = (s0 + every < nsteps ? s0 + every : nsteps) - 1;
+    const char *ck = scratch + (size_t)c * p.ckpt_stride;
+    cudaError_t e = cudaMemcpyAsync(slot_ptr(scratch, p, s, q, 1), ck, buf, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(segctl, ck + round256(buf), sizeof(DevCtl), cudaMemcpyDeviceToDevice, st);
+    for (int64_t m = s0; e == cudaSuccess && m <= e0; ++m) {
+        if (!fixed_a)
+            e = cudaMemcpyAsync(khist + (m - s0) * kConstSlot, ctl_consts<T>(segctl), sizeof(StepConsts<T>),
+                                cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && diff_a)
+            e = cudaMemcpyAsync(khist + (m - s0) * kConstSlot + kSlotTime, &segctl->t, sizeof(double),
+                                cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && m < e0) e = recompute_step<T>(s, scratch, p, every, q, m, m - s0, st);
+    }
+    if (e == cudaSuccess) e = dirichlet_slot<T>(s, scratch, p, q, e0, e0 - s0, st);   // the segment's last state
+    return e;
+}
+
+// Reverse sweep, last segment first. The recomputation of segment c - 1 (on the
+// second stream, into the other segment buffer) overlaps the adjoint steps of
+// segment c (on the state's stream): at small grids neither fills the GPU. Events
+// order each segment's adjoint steps after its recomputation, and the
+// recomputation into a buffer after the adjoint steps that last read it.
 template <typename T>
 int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const Plan &p, const void *dLduN,
             void *dLdu0) {
-    const size_t buf = s->L.buf_bytes;
     const bool fixed_a = s->a_fixed > 0.0;
     const bool diff_a = !fixed_a && s->adj_mode == VLBM_ADJOINT_DIFF_A;
     ARed *red = (ARed *)(scratch + p.red_off);
     T *cot[2] = {(T *)(scratch + p.cot_off), (T *)(scratch + p.cot_off + p.cot_bytes)};
-    DevCtl *segctl = (DevCtl *)(scratch + p.segctl_off);
-    char *khist = scratch + p.khist_off;
     {
         const dim3 blk(32, 8), grd((s->grid.nx + 31) / 32, (s->grid.ny + 7) / 8);
         k_adjoint_seed<T><<<grd, blk, 0, s->stream>>>((const T *)dLduN, s->grid.nx, s->grid.ny, cot[0]);
@@ -305,13 +355,22 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
         if (e == cudaSuccess) e = cudaMemsetAsync(&red->idx, 0xff, sizeof(unsigned int), s->stream);
     }
     if (e != cudaSuccess) return cuda_fail(s, e, "cotangent seed");
-    std::vector<unsigned char> descs;
+    std::vector<unsigned char> descs[2];
     if (use_fused(s)) {
-        if (!build_recompute_descs<T>(s, scratch, p, every, descs))
-            return fail(s, VLBM_E_CUDA, "TMA descriptor of a recomputation slot");
-        e = cudaMemcpyAsync(scratch + p.desc_off, descs.data(), descs.size(), cudaMemcpyHostToDevice, s->stream);
-        if (e != cudaSuccess) return cuda_fail(s, e, "descriptor upload");
+        for (int q = 0; q < 2; ++q) {
+            if (!build_recompute_descs<T>(s, scratch, p, every, q, descs[q]))
+                return fail(s, VLBM_E_CUDA, "TMA descriptor of a recomputation slot");
+            e = cudaMemcpyAsync(scratch + p.desc_off[q], descs[q].data(), descs[q].size(), cudaMemcpyHostToDevice,
+                                s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "descriptor upload");
+        }
     }
+    e = aux_stream(s);
+    if (e != cudaSuccess) return cuda_fail(s, e, "second stream of the reverse sweep");
+    cudaStream_t aux = s->aux_stream;
+    cudaEvent_t ev_fork = s->aux_ev[0], ev_rec[2] = {s->aux_ev[1], s->aux_ev[2]},
+                ev_adj[2] = {s->aux_ev[3], s->aux_ev[4]};
+    bool adj_used[2] = {false, false};   // an adjoint step has read buffer q (ev_adj[q] recorded)
     int cur = 0;
     AdjArgs<T> A;
     A.pitch = s->L.pitch;
@@ -326,26 +385,30 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
     A.sponge = s->sponge;
     A.lmp = (T *)(scratch + p.lmp_off);
     T *pad = (T *)(scratch + p.pad_off);
-    for (int64_t c = nsteps > 0 ? p.nckpt - 1 : -1; c >= 0; --c) {
+    const int64_t clast = nsteps > 0 ? p.nckpt - 1 : -1;
+    // the second stream starts after everything the state's stream holds so far
+    e = cudaEventRecord(ev_fork, s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev_fork, 0);
+    if (e == cudaSuccess && clast >= 0) {
+        e = recompute_segment<T>(s, scratch, p, nsteps, every, clast, (int)(clast & 1), aux);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_rec[clast & 1], aux);
+    }
+    for (int64_t c = clast; e == cudaSuccess && c >= 0; --c) {
+        const int q = (int)(c & 1);
+        DevCtl *segctl = (DevCtl *)(scratch + p.segctl_off[q]);
+        char *khist = scratch + p.khist_off[q];
         const int64_t s0 = c * every;
         const int64_t e0 = (s0 + every < nsteps ? s0 + every : nsteps) - 1;
-        const char *ck = scratch + (size_t)c * p.ckpt_stride;
-        e = cudaMemcpyAsync(slot_ptr(scratch, p, s, 1), ck, buf, cudaMemcpyDeviceToDevice, s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(segctl, ck + round256(buf), sizeof(DevCtl), cudaMemcpyDeviceToDevice, s->stream);
-        for (int64_t m = s0; e == cudaSuccess && m <= e0; ++m) {
-            if (!fixed_a)
-                e = cudaMemcpyAsync(khist + (m - s0) * kConstSlot, ctl_consts<T>(segctl), sizeof(StepConsts<T>),
-                                    cudaMemcpyDeviceToDevice, s->stream);
-            if (e == cudaSuccess && diff_a)
-                e = cudaMemcpyAsync(khist + (m - s0) * kConstSlot + kSlotTime, &segctl->t, sizeof(double),
-                                    cudaMemcpyDeviceToDevice, s->stream);
-            if (e == cudaSuccess && m < e0) e = recompute_step<T>(s, scratch, p, every, m, m - s0);
+        e = cudaStreamWaitEvent(s->stream, ev_rec[q], 0);
+        if (e == cudaSuccess && c > 0) {   // segment c - 1 into the other buffer, once its readers are done
+            const int qn = q ^ 1;
+            if (adj_used[qn]) e = cudaStreamWaitEvent(aux, ev_adj[qn], 0);
+            if (e == cudaSuccess) e = recompute_segment<T>(s, scratch, p, nsteps, every, c - 1, qn, aux);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_rec[qn], aux);
         }
-        if (e == cudaSuccess) e = dirichlet_slot<T>(s, scratch, p, e0, e0 - s0);   // the segment's last state
-        if (e != cudaSuccess) return cuda_fail(s, e, "recomputation");
+        if (e != cudaSuccess) break;
         for (int64_t m = e0; m >= s0; --m) {
-            A.fwd = (const T *)slot_ptr(scratch, p, s, m - s0 + 1);
+            A.fwd = (const T *)slot_ptr(scratch, p, s, q, m - s0 + 1);
             A.cot_in = cot[cur];
             A.cot_out = A.ext ? pad : cot[cur ^ 1];
             A.k = fixed_a ? ctl_consts<T>(segctl) : (const StepConsts<T> *)(khist + (m - s0) * kConstSlot);
@@ -353,20 +416,29 @@ int reverse(vlbm_state *s, int64_t nsteps, int32_t every, char *scratch, const P
             if (e == cudaSuccess && A.ext)
                 e = fold_ghosts<T>(pad, A.pad, s, cot[cur ^ 1], s->stream, A.k,
                                    (const double *)(khist + (m - s0) * kConstSlot + kSlotTime), A.abar);
-            if (e != cudaSuccess) return cuda_fail(s, e, "adjoint step launch");
+            if (e != cudaSuccess) break;
             cur ^= 1;
             if (diff_a && m > 0) {   // a^m came from lambda of s^m (a^0 waits for the init map)
                 e = hand_over_abar<T>(A.fwd, s->L, s->gamma, s->alpha, red, cot[cur], true, &segctl->lam_bc,
                                       s->stream);
-                if (e != cudaSuccess) return cuda_fail(s, e, "kinetic-speed cotangent launch");
+                if (e != cudaSuccess) break;
             }
         }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_adj[q], s->stream);
+        adj_used[q] = true;
     }
+    // join: whatever the second stream still holds comes before the state's next work
+    cudaError_t ej = cudaEventRecord(ev_fork, aux);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s->stream, ev_fork, 0);
+    if (e == cudaSuccess) e = ej;
+    if (e != cudaSuccess) return cuda_fail(s, e, "reverse sweep");
+    const size_t buf = s->L.buf_bytes;
     const char *ck0 = scratch;
+    DevCtl *segctl0 = (DevCtl *)(scratch + p.segctl_off[0]);
     e = launch_adjoint_init<T>((const T *)ck0, s->L, ctl_consts<T>((const DevCtl *)(ck0 + round256(buf))), cot[cur],
                                (T *)dLdu0, diff_a ? &red->abar : nullptr, s->stream);
     if (e == cudaSuccess && diff_a)
-        e = hand_over_abar<T>((const T *)ck0, s->L, s->gamma, s->alpha, red, (T *)dLdu0, false, &segctl->lam_bc,
+        e = hand_over_abar<T>((const T *)ck0, s->L, s->gamma, s->alpha, red, (T *)dLdu0, false, &segctl0->lam_bc,
                               s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "initialisation adjoint launch");
     return VLBM_OK;

@@ -9,6 +9,8 @@
 #include "../../include/vlbm.h"
 #include "vlbm_internal.h"
 
+constexpr int kAuxEvents = 5;   // events of the reverse sweep's two streams
+
 struct vlbm_state {
     vlbm_grid grid;
     int precision, limiter, kernel;
@@ -40,6 +42,10 @@ struct vlbm_state {
     int64_t roll_steps;
     int32_t roll_every;
     int adj_mode;       // VLBM_ADJOINT_HOLD_A or VLBM_ADJOINT_DIFF_A
+    // the reverse sweep's second stream (recomputation) and its events, made on first use
+    bool aux_ready;
+    cudaStream_t aux_stream;
+    cudaEvent_t aux_ev[kAuxEvents];
     char err[256];
 };
 
