@@ -264,7 +264,7 @@ typedef struct vlbm_batch vlbm_batch;
 #define VLBM_ORDER_INDEX 1   /* work items in grid index order */
 #define VLBM_ORDER_GUIDED 2  /* as LPT, rows cut into bands of decreasing height: each
                                 band's height is the rows x strips left in all grids over
-                                the CTA count, within [16, chunk] (guided self-scheduling;
+                                the CTA count, within [4, chunk] (guided self-scheduling;
                                 a single vlbm_state always uses it, with chunk 128) */
 
 /* Work decomposition: rows per work item (the largest band under GUIDED), CTAs
@@ -307,7 +307,7 @@ VLBM_API int vlbm_batch_monitors(vlbm_batch *b, int32_t i, vlbm_monitor_t *out);
 VLBM_API int vlbm_batch_get_tuning(const vlbm_batch *b, vlbm_batch_tuning *t);
 VLBM_API int vlbm_batch_set_tuning(vlbm_batch *b, const vlbm_batch_tuning *t);
 
-/* Autotuner: times every decomposition (chunk 16/32/64/128 rows x 1..max CTAs per SM
+/* Autotuner: times every decomposition (chunk 32/64/128/256 rows x 1..max CTAs per SM
  * x the three item orders) over trial_steps steps each with CUDA events, keeps the
  * fastest and returns it with its time per step. The decomposition does not
  * change any cell's arithmetic, so the trial steps are real steps: the grids

@@ -477,7 +477,7 @@ int vlbm_batch_autotune(vlbm_batch *b, int32_t trial_steps, vlbm_batch_tuning *b
     BDeviceGuard g(b->device);
     const int maxc = b->precision == VLBM_FP64 ? fused_occupancy<double>(b->limiter)
                                                : fused_occupancy<float>(b->limiter);
-    const int chunks[] = {16, 32, 64, 128};
+    const int chunks[] = {32, 64, 128, 256};
     const int orders[] = {VLBM_ORDER_LPT, VLBM_ORDER_INDEX, VLBM_ORDER_GUIDED};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
