@@ -90,7 +90,8 @@ extern "C" {
 #define VLBM_FP32 1
 
 /* Kernel choice. VLBM_KERNEL_AUTO takes the row-marching kernel for FP32 grids of at
- * least 2^19 cells and the one-thread-per-cell kernel otherwise (where it is faster). */
+ * least 2^19 cells and FP64 grids of at least 2^22 cells, the one-thread-per-cell
+ * kernel otherwise (where it is faster). */
 #define VLBM_KERNEL_AUTO 0
 #define VLBM_KERNEL_SIMPLE 1    /* one thread per cell, radius-2 gather from L2 */
 #define VLBM_KERNEL_FUSED 2     /* row-marching TMA kernel, one pass per step */

@@ -91,15 +91,19 @@ inline StepArgs<T> args_of(const vlbm_state *s) {
 // VLBM_KERNEL_AUTO. FP32: below this many cells a grid has too few row-marching
 // work items to fill the GPU and the one-thread-per-cell kernel is faster (PP on a
 // GB300, a vortex with density bumps: 11.8 vs 20.4 us per step at 256^2, 27.3 vs
-// 35.4 us at 512^2, about even at 640^2, 93 vs 67 us at 1024^2). FP64: every face's theta_p
-// solve makes the step FP64-bound, where the one-thread-per-cell kernel's many warps
-// per SM win at every size measured (0.62 vs 1.50 ms at 512^2, 9.4 vs 10.3 ms at 2048^2).
+// 35.4 us at 512^2, about even at 640^2, 93 vs 67 us at 1024^2). FP64: every face's
+// theta_p solve makes the step FP64-pipe bound, where the one-thread-per-cell
+// kernel's many warps per SM win on small grids (0.63 vs 0.77 ms at 512^2, 2.39 vs
+// 2.55 ms at 1024^2) and the row-marching kernel on large ones (9.53 vs 8.00 ms at
+// 2048^2).
 constexpr long long kAutoFusedMinCells = 1ll << 19;
+constexpr long long kAutoFusedMinCellsFp64 = 1ll << 22;
 
 inline bool use_fused(const vlbm_state *s) {
     if (!s->have_tmap || s->kernel == VLBM_KERNEL_SIMPLE) return false;
     if (s->kernel == VLBM_KERNEL_FUSED) return true;
-    return s->precision == VLBM_FP32 && (long long)s->grid.nx * s->grid.ny >= kAutoFusedMinCells;
+    const long long cells = (long long)s->grid.nx * s->grid.ny;
+    return cells >= (s->precision == VLBM_FP32 ? kAutoFusedMinCells : kAutoFusedMinCellsFp64);
 }
 
 // Arguments of the row-marching kernel for this grid (descriptor block of the workspace).
