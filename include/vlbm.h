@@ -245,7 +245,8 @@ VLBM_API int vlbm_save(const vlbm_state *s, void *d_dst);
 VLBM_API int vlbm_load(vlbm_state *s, const void *d_src);
 
 /* Kernel timing. While enabled, every step records a CUDA event pair around its
- * collide + limit + stream kernel (not the ghost-frame kernel) on the state's
+ * collide + limit + stream kernel (not the pass that writes prescribed ghosts
+ * before it, on grids with a prescribed part) on the state's
  * stream. vlbm_profile_read waits for the stream and returns the summed kernel
  * time in milliseconds and the number of timed launches since the last enable. */
 VLBM_API int vlbm_profile(vlbm_state *s, int32_t enable);
