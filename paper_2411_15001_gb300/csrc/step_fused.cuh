@@ -60,6 +60,8 @@ struct FusedSmem {
     int abort;
 };
 
+// Register history of the own column; u is kept only for the row just loaded (rows
+// before it read theirs back from the shared ring).
 template <typename T>
 struct Hist {
     T u[4], g[4], d3[4], d4[4];
@@ -109,11 +111,14 @@ struct FusedCtx {
         ++nissued;
     }
 
-    __device__ __forceinline__ void reset_state() {
+    // The history before row R0 (the item's first): a neutral row. The own column's u of
+    // earlier rows is read back from the shared ring (the same values P1 stored there),
+    // so the ring slot of row R0 - 1 gets u = 1 in the own column.
+    __device__ __forceinline__ void reset_state(int R0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             xs_us[q] = xs_df[q] = ys_us[q] = ys_df[q] = T(0);
-            h1.u[q] = h2.u[q] = T(1);
+            S.X[xslot(R0 - 1)][q][b] = T(1);
             h1.g[q] = h2.g[q] = T(0);
             h1.d3[q] = h2.d3[q] = T(0);
             h1.d4[q] = h2.d4[q] = T(0);
@@ -157,7 +162,7 @@ struct FusedCtx {
             h0.u[q] = u[q];
             h0.g[q] = g[q];
         }
-        return face_star(h1.u[0], h1.g[0], u[0], g[0], k);  // y-face R - 1/2
+        return face_star(S.X[xslot(R - 1)][0][b], h1.g[0], u[0], g[0], k);  // y-face R - 1/2
     }
 
     // Face states of the x-face (b, b+1) of row R and of the y-face R - 1/2 (PP and the
@@ -170,7 +175,7 @@ struct FusedCtx {
         for (int q = 0; q < 4; ++q) {
             xus[q] = face_star(h0.u[q], f[q], S.X[xs][q][br], S.X[xs][4 + q][br], k);
             xdf[q] = face_dflux(d1[q], S.X[xs][12 + q][br], k);
-            yus[q] = q == 0 ? rsy_new : face_star(h1.u[q], h1.g[q], h0.u[q], h0.g[q], k);
+            yus[q] = q == 0 ? rsy_new : face_star(S.X[xslot(R - 1)][q][b], h1.g[q], h0.u[q], h0.g[q], k);
             ydf[q] = face_dflux(h1.d3[q], h0.d4[q], k);
         }
     }
@@ -225,7 +230,7 @@ struct FusedCtx {
     // Bounds of row R - 1, own column.
     __device__ __forceinline__ void bounds(int R, T rsy_new, int bl, T &mu, T &nu) const {
         const int rp = (R - 1) & 1;
-        minmax5(h1.u[0], S.rsx[rp][bl], S.rsx[rp][b], rsy_prev, rsy_new, mu, nu);
+        minmax5(S.X[xslot(R - 1)][0][b], S.rsx[rp][bl], S.rsx[rp][b], rsy_prev, rsy_new, mu, nu);
     }
 
     // Bounds of row R - 1 of the column to the right (br), from the shared rows R - 2 ..
@@ -287,9 +292,10 @@ struct FusedCtx {
                 const int xp = xslot(R - 1);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    xs_us[q] = face_star(h1.u[q], S.X[xp][4 + q][b], S.X[xp][q][br], S.X[xp][4 + q][br], k);
+                    xs_us[q] = face_star(S.X[xp][q][b], S.X[xp][4 + q][b], S.X[xp][q][br], S.X[xp][4 + q][br], k);
                     xs_df[q] = face_dflux(S.X[xp][8 + q][b], S.X[xp][12 + q][br], k);
-                    ys_us[q] = q == 0 ? rsy_prev : face_star(h2.u[q], h2.g[q], h1.u[q], h1.g[q], k);
+                    ys_us[q] = q == 0 ? rsy_prev
+                                      : face_star(S.X[xslot(R - 2)][q][b], h2.g[q], S.X[xp][q][b], h1.g[q], k);
                     ys_df[q] = face_dflux(h2.d3[q], h1.d4[q], k);
                 }
             }
@@ -368,15 +374,15 @@ struct FusedCtx {
         for (int q = 0; q < 4; ++q) {
             const T M1W = maxwell_plus(S.X[xo][q][bl], S.X[xo][4 + q][bl], k);
             const T M2E = maxwell_minus(S.X[xo][q][br], S.X[xo][4 + q][br], k);
-            const T M4N = maxwell_minus(hn.u[q], hn.g[q], k);
+            const T M4N = maxwell_minus(kRecompute ? S.X[xslot(R - 1)][q][b] : h0.u[q], hn.g[q], k);
             nv[4 + q] = blend_pop(M1W, S.X[xo][8 + q][bl], tw);
             nv[8 + q] = blend_pop(M2E, S.X[xo][12 + q][br], te);
             nv[12 + q] = p3n[q];
             nv[16 + q] = blend_pop(M4N, hn.d4[q], tn);
-            nv[q] = blend_u(nv[4 + q], nv[8 + q], nv[12 + q], nv[16 + q], hc.u[q], tw, S.X[xo][12 + q][b],
+            nv[q] = blend_u(nv[4 + q], nv[8 + q], nv[12 + q], nv[16 + q], S.X[xo][q][b], tw, S.X[xo][12 + q][b],
                             te, S.X[xo][8 + q][b], ts, hc.d4[q], tn, hc.d3[q], k);
             // u_3 of row O + 1 after the step, pulled from row O with theta of y-face O + 1/2
-            p3n[q] = blend_pop(maxwell_plus(hc.u[q], hc.g[q], k), hc.d3[q], tn);
+            p3n[q] = blend_pop(maxwell_plus(S.X[xo][q][b], hc.g[q], k), hc.d3[q], tn);
         }
         if (O >= y0 && O < y1 && b >= kFHalo && b < kFHalo + wout && c < D.nx) {
             T *base = out + sidx(D.pitch, 0, c, O);
@@ -470,7 +476,7 @@ __global__ void __launch_bounds__(kFB, sizeof(T) == 4 ? 3 : 1)
         X.R1 = X.y1 + kLag - 1;
         if (b == 0)
             for (int r = R0; r < R0 + kRawSlots && r <= X.R1; ++r) X.issue(r);
-        X.reset_state();
+        X.reset_state(R0);
         int R = R0;
         for (; R < X.y0 + kLag - 1 && ok; ++R) ok = X.row_warm(R);
         for (; R <= X.R1 && ok; ++R) ok = X.row(R);
