@@ -269,8 +269,8 @@ typedef struct vlbm_batch vlbm_batch;
                                 the CTA count, within [4, chunk] (guided self-scheduling;
                                 a single vlbm_state always uses it, with chunk 128) */
 
-/* Work decomposition: rows per work item (the largest band under GUIDED), CTAs
- * per SM, item order; items and CTAs of the resulting launch (outputs). A new
+/* Work decomposition: rows per work item (the largest band under GUIDED; 4 to 1024),
+ * CTAs per SM (1 to 4), item order; items and CTAs of the resulting launch (outputs). A new
  * batch starts with GUIDED bands of at most 128 rows and as many CTAs per SM as
  * the kernel's occupancy allows. */
 typedef struct {
@@ -309,7 +309,7 @@ VLBM_API int vlbm_batch_monitors(vlbm_batch *b, int32_t i, vlbm_monitor_t *out);
 VLBM_API int vlbm_batch_get_tuning(const vlbm_batch *b, vlbm_batch_tuning *t);
 VLBM_API int vlbm_batch_set_tuning(vlbm_batch *b, const vlbm_batch_tuning *t);
 
-/* Autotuner: times every decomposition (chunk 32/64/128/256 rows x 1..max CTAs per SM
+/* Autotuner: times every decomposition (chunk 32/128/512/1024 rows x 1..max CTAs per SM
  * x the three item orders) over trial_steps steps each with CUDA events, keeps the
  * fastest and returns it with its time per step. The decomposition does not
  * change any cell's arithmetic, so the trial steps are real steps: the grids

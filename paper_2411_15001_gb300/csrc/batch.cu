@@ -458,7 +458,7 @@ int vlbm_batch_get_tuning(const vlbm_batch *b, vlbm_batch_tuning *t) {
 
 int vlbm_batch_set_tuning(vlbm_batch *b, const vlbm_batch_tuning *t) {
     if (!b || !t) return bfail(b, VLBM_E_INVAL, "bad argument");
-    if (t->chunk < kFusedMinChunk || t->chunk > 256 || t->ctas_per_sm < 1 || t->ctas_per_sm > 4 ||
+    if (t->chunk < kFusedMinChunk || t->chunk > 1024 || t->ctas_per_sm < 1 || t->ctas_per_sm > 4 ||
         (t->order != VLBM_ORDER_LPT && t->order != VLBM_ORDER_INDEX && t->order != VLBM_ORDER_GUIDED))
         return bfail(b, VLBM_E_INVAL, "tuning out of range");
     const int maxc = b->precision == VLBM_FP64 ? fused_occupancy<double>(b->limiter)
@@ -477,7 +477,7 @@ int vlbm_batch_autotune(vlbm_batch *b, int32_t trial_steps, vlbm_batch_tuning *b
     BDeviceGuard g(b->device);
     const int maxc = b->precision == VLBM_FP64 ? fused_occupancy<double>(b->limiter)
                                                : fused_occupancy<float>(b->limiter);
-    const int chunks[] = {32, 64, 128, 256};
+    const int chunks[] = {32, 128, 512, 1024};
     const int orders[] = {VLBM_ORDER_LPT, VLBM_ORDER_INDEX, VLBM_ORDER_GUIDED};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

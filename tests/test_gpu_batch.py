@@ -70,7 +70,8 @@ def test_autotune_keeps_results_exact():
     n = b.monitors(0)["n"]
     assert n > 0 and best["ms_per_step"] > 0 and best["items"] > 0
     for chunk, cps, order in ((16, 1, V.ORDER_LPT), (64, 3, V.ORDER_INDEX), (128, 3, V.ORDER_GUIDED),
-                              (16, 2, V.ORDER_GUIDED), (256, 3, V.ORDER_GUIDED), (4, 3, V.ORDER_LPT)):
+                              (16, 2, V.ORDER_GUIDED), (256, 3, V.ORDER_GUIDED), (4, 3, V.ORDER_LPT),
+                              (1024, 2, V.ORDER_INDEX)):
         b.set_tuning(chunk, cps, order)
         assert b.tuning()["order"] == order
         b.step(3)
