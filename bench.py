@@ -61,17 +61,42 @@ ACCURACY_GAP_1024_LMP = (
 
 
 # The sources the FP32 step kernel is compiled from (its translation unit and
-# headers): a committed ncu summary counts for the kernel while these are unchanged.
+# headers): a committed ncu summary counts for the kernel while their code (comments
+# aside) is unchanged.
 STEP_KERNEL_SOURCES = ("common.cuh", "kernels_f32.cu", "kernels_impl.cuh", "physics.cuh", "step_fused.cuh",
                        "step_simple.cuh", "tma.cuh", "vlbm_internal.h")
+
+
+def _code_only(text: str) -> str:
+    """C++ source without comments, blank lines and trailing spaces (a comment edit does
+    not change the kernel)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif text[i] == '"':                       # string literal: copied as is
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(text[i])
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).splitlines())
+    return "\n".join(line for line in lines if line)
 
 
 def _kernel_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2411_15001_gb300", "csrc")
     for name in STEP_KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

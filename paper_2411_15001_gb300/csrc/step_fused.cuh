@@ -19,7 +19,8 @@
 // whose bounds have the radius-2 stencil of eq. LMP_minmax):
 //  P1  fluxes, Maxwellians, non-equilibrium parts d_k of row R; what x-neighbours
 //      need (u, f, d_1, d_2) goes to a shared ring of lag + 2 rows, what only the own
-//      column needs (u, g, d_3, d_4) to a register history; rho* of y-face R - 1/2.
+//      column needs (g, d_3, d_4; its u is read back from the ring) to a register
+//      history; rho* of y-face R - 1/2.
 //  P2  density bounds of row R - 1 (LMP/RLMP).
 //  P3  PP and the fixed thetas: u*, dF and theta of the x-face of row R and of y-face
 //      R - 1/2 (Sec. 3.3-3.4). LMP / RLMP: theta of the x-faces of row R - 1 and of
@@ -92,7 +93,7 @@ struct FusedCtx {
     T mu2, nu2;             // bounds of row R-2 (own column)
     T thy_prev;             // LMP / RLMP: theta of the y-face between rows R-3 and R-2
     T ty1;                  // PP: theta of the y-face (R-2, R-1)
-    Hist<T> h1, h2;         // rows R-1, R-2 of the own column (h2: LMP / RLMP)
+    Hist<T> h1, h2;         // rows R-1, R-2 of the own column (h2: LMP / RLMP; their u unused)
     T p3n[4];               // u_3 of the next output row after the step (pulled from the one below)
 
     // Slot of row R (>= -2) in the shared ring X.
@@ -363,8 +364,8 @@ struct FusedCtx {
         // is read only after the next row's S1, and every slot the next row overwrites
         // is read here before this thread reaches that S1.
         // ---------------------------------------------------------------- P4
-        // row O and the row above it: in the register history (LMP / RLMP: h2, h1;
-        // PP and the fixed thetas: h1 and the row just loaded)
+        // row O and the row above it: g, d_3, d_4 in the register history (LMP / RLMP:
+        // h2, h1; PP and the fixed thetas: h1 and the row just loaded), u in the ring
         const int O = R - kLag;
         const int xo = xslot(O);
         const Hist<T> &hc = kRecompute ? h2 : h1;
