@@ -56,3 +56,15 @@ def test_single_process_without_a_group():
     b = _bench()
     assert b.max_over_ranks(2.5) == 2.5
     assert b.whole_job_mlups(1, 4096 * 4096, 1900, 1.0) == pytest.approx(4096 * 4096 * 1900 / 1e6)
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The ncu summary stays valid across comment edits of the kernel sources, not across
+    code edits (string literals are code)."""
+    b = _bench()
+    src = 'int a = 1;  // one\n/* block\n comment */\nconst char *s = "x // y";\n\n  a += 2;\n'
+    same = '// header\nint a = 1;\n\nconst char *s = "x // y"; /* trailing */\n  a += 2;   \n'
+    other = 'int a = 1;\nconst char *s = "x // z";\n  a += 2;\n'
+    assert b._code_only(src) == b._code_only(same)
+    assert b._code_only(src) != b._code_only(other)
+    assert b._code_only(src) != b._code_only(src.replace("a += 2", "a += 3"))
